@@ -1,0 +1,190 @@
+"""FP64 CPU oracle for the explicit forward-Euler phase-field / reaction-diffusion step.
+
+TEST INFRASTRUCTURE ONLY.  This package is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline / reference arm of ``bench.py``, and by
+nothing else.  It shares no code with the CUDA library and never calls it; the CUDA path
+never imports it.
+
+Every function is plain numpy in float64 and follows the paper's definitions directly:
+
+* grid layout: row-major with x fastest (Sec. 2.2.1 "Uniform Grid"); periodic sides
+  (the driver example, Fig. "driver_implementation" in Sec. 2.4, sets every edge
+  periodic), done here with ``np.roll``;
+* the second-order central Laplacian, 5 points in 2D and 7 points in 3D
+  (Sec. 2.2.2 "Finite Difference Stencils");
+* Model A (Allen-Cahn) and Model B (Cahn-Hilliard) equations of motion (Sec. 3,
+  the first two numbered equations), with the coefficient names of the model
+  definitions figure (Fig. "models_abc_definitions"): A uses c1 (linear) and c2 (cubic);
+  B uses c1, c2 and a mobility M multiplying the whole right-hand side;
+* Gray-Scott, which the paper names as a reaction-diffusion example (Sec. 1) but does not
+  write out, in its standard two-species form
+  du/dt = Du lap u - u v^2 + F (1 - u),  dv/dt = Dv lap v + u v^2 - (F + k) v;
+* the forward-Euler solver (Sec. 2.4.1): x^{n+1} = x^n + dt f(x^n), every field updated
+  from the same x^n, i.e. the paper's ``equation()`` then ``step()`` split (Sec. 2.2.4);
+* the discrete free energy whose gradient flow Model A is, and the discrete adjoint of
+  the Gray-Scott forward-Euler map (reverse-mode derivative of the time loop).
+
+Parity status: every function here is pinned by the tests in ``tests/test_oracle_*.py``
+(closed forms, brute force on tiny grids, invariants, complex-step derivatives).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MODELS = ("ac", "ch", "gs")
+
+
+def _f64(x):
+    a = np.asarray(x)
+    if np.iscomplexobj(a):
+        return a.astype(np.complex128)
+    return a.astype(np.float64)
+
+
+# ------------------------------------------------------------------ stencils (Sec. 2.2.2)
+
+def laplacian(phi, h: float = 1.0):
+    """Periodic second-order Laplacian: sum over axes of (phi[+1] + phi[-1] - 2 phi) / h^2.
+
+    5-point in 2D, 7-point in 3D (3-point in 1D).  Works for real or complex arrays.
+    """
+    phi = _f64(phi)
+    out = np.zeros_like(phi)
+    for ax in range(phi.ndim):
+        out += (np.roll(phi, 1, axis=ax) - phi) + (np.roll(phi, -1, axis=ax) - phi)
+    return out / (h * h)
+
+
+# ------------------------------------------------------------ right-hand sides (Sec. 3)
+
+def rhs_allen_cahn(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
+    """Model A: dphi/dt = lap phi + c1 phi - c2 phi^3."""
+    phi = _f64(phi)
+    return laplacian(phi, h) + c1 * phi - c2 * phi ** 3
+
+
+def chemical_potential(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
+    """Model B chemical potential mu = c2 phi^3 - c1 phi - lap phi."""
+    phi = _f64(phi)
+    return c2 * phi ** 3 - c1 * phi - laplacian(phi, h)
+
+
+def rhs_cahn_hilliard(phi, c1: float = 1.0, c2: float = 1.0, M: float = 1.0, h: float = 1.0):
+    """Model B: dphi/dt = M lap mu = -M lap^2 phi - M lap (c1 phi - c2 phi^3)."""
+    return M * laplacian(chemical_potential(phi, c1, c2, h), h)
+
+
+def rhs_gray_scott(u, v, Du: float, Dv: float, F: float, k: float, h: float = 1.0):
+    """Gray-Scott: (Du lap u - u v^2 + F (1-u),  Dv lap v + u v^2 - (F+k) v)."""
+    u = _f64(u)
+    v = _f64(v)
+    uvv = u * v * v
+    fu = Du * laplacian(u, h) - uvv + F * (1.0 - u)
+    fv = Dv * laplacian(v, h) + uvv - (F + k) * v
+    return fu, fv
+
+
+def rhs(model: str, fields, coeffs, h: float = 1.0):
+    """Right-hand side f(x) of ``model`` for the tuple of fields ``x``."""
+    if model == "ac":
+        return (rhs_allen_cahn(fields[0], *coeffs, h=h),)
+    if model == "ch":
+        return (rhs_cahn_hilliard(fields[0], *coeffs, h=h),)
+    if model == "gs":
+        return rhs_gray_scott(fields[0], fields[1], *coeffs, h=h)
+    raise ValueError(f"unknown model {model!r}")
+
+
+# ----------------------------------------------------------- forward Euler (Sec. 2.4.1)
+
+def euler_step(model: str, fields, coeffs, dt: float, h: float = 1.0):
+    """One explicit step x^{n+1} = x^n + dt f(x^n); all fields read x^n."""
+    fields = tuple(_f64(f) for f in fields)
+    f = rhs(model, fields, coeffs, h)
+    return tuple(x + dt * fx for x, fx in zip(fields, f))
+
+
+def run(model: str, fields, coeffs, dt: float, n_steps: int, h: float = 1.0):
+    """``n_steps`` forward-Euler steps from ``fields``."""
+    x = tuple(_f64(f) for f in fields)
+    for _ in range(int(n_steps)):
+        x = euler_step(model, x, coeffs, dt, h)
+    return x
+
+
+# ------------------------------------------------------------------------ reductions
+
+def mass(phi, h: float = 1.0) -> float:
+    """Discrete integral h^d * sum(phi)."""
+    phi = _f64(phi)
+    return float(h ** phi.ndim * phi.sum())
+
+
+def energy(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
+    """Discrete free energy E = h^d sum_x [ 1/2 sum_i ((phi_{x+e_i}-phi_x)/h)^2
+    - c1/2 phi^2 + c2/4 phi^4 ].
+
+    -dE/dphi_x / h^d equals the Model A right-hand side exactly, so Model A is the discrete
+    gradient flow of E and Model B its lap-weighted flow with mu = dE/dphi_x / h^d.
+    """
+    phi = _f64(phi)
+    grad2 = np.zeros_like(phi)
+    for ax in range(phi.ndim):
+        d = (np.roll(phi, -1, axis=ax) - phi) / h
+        grad2 += d * d
+    dens = 0.5 * grad2 - 0.5 * c1 * phi ** 2 + 0.25 * c2 * phi ** 4
+    return h ** phi.ndim * dens.sum()
+
+
+# --------------------------------------------------------- Gray-Scott discrete adjoint
+
+def gray_scott_loss(u, v, u_target, v_target) -> float:
+    """L = 1/2 sum over sites of (u - u*)^2 + (v - v*)^2."""
+    du = _f64(u) - _f64(u_target)
+    dv = _f64(v) - _f64(v_target)
+    return 0.5 * float((du * du).sum() + (dv * dv).sum())
+
+
+def gray_scott_adjoint_step(u, v, a, b, Du, Dv, F, k, dt, h=1.0):
+    """Reverse step of the forward-Euler Gray-Scott map x^{n+1} = x^n + dt f(x^n).
+
+    With (u, v) = x^n and (a, b) = lambda^{n+1} = dL/dx^{n+1}, returns lambda^n =
+    lambda^{n+1} + dt J(x^n)^T lambda^{n+1} and this step's contribution
+    dt (df/dtheta)(x^n)^T lambda^{n+1} to the gradient w.r.t. theta = (Du, Dv, F, k).
+    The periodic Laplacian is symmetric, so its transpose is itself.
+    """
+    u, v, a, b = (_f64(t) for t in (u, v, a, b))
+    a_new = a + dt * (Du * laplacian(a, h) - (v * v + F) * a + v * v * b)
+    b_new = b + dt * (Dv * laplacian(b, h) - 2.0 * u * v * a + (2.0 * u * v - F - k) * b)
+    g = np.array([
+        dt * float((a * laplacian(u, h)).sum()),            # d/dDu
+        dt * float((b * laplacian(v, h)).sum()),            # d/dDv
+        dt * float(((1.0 - u) * a - v * b).sum()),          # d/dF
+        -dt * float((v * b).sum()),                          # d/dk
+    ])
+    return a_new, b_new, g
+
+
+def gray_scott_adjoint(u0, v0, coeffs, dt, n_steps, dLdu_N, dLdv_N, h=1.0):
+    """Gradient of a final-state loss through ``n_steps`` forward-Euler Gray-Scott steps.
+
+    Stores the whole forward trajectory (no checkpointing), then runs the reverse steps
+    from n = N-1 down to 0.  Returns (dL/du0, dL/dv0, dL/d(Du, Dv, F, k)).
+    """
+    Du, Dv, F, k = coeffs
+    traj = [(_f64(u0), _f64(v0))]
+    for _ in range(int(n_steps)):
+        traj.append(euler_step("gs", traj[-1], coeffs, dt, h))
+    a, b = _f64(dLdu_N), _f64(dLdv_N)
+    g = np.zeros(4)
+    for n in range(int(n_steps) - 1, -1, -1):
+        u, v = traj[n]
+        a, b, gn = gray_scott_adjoint_step(u, v, a, b, Du, Dv, F, k, dt, h)
+        g += gn
+    return a, b, g
+
+
+def gray_scott_final_and_loss(u0, v0, coeffs, dt, n_steps, u_target, v_target, h=1.0):
+    """Forward run then loss; returns (u_N, v_N, L)."""
+    uN, vN = run("gs", (u0, v0), coeffs, dt, n_steps, h)
+    return uN, vN, gray_scott_loss(uN, vN, u_target, v_target)
