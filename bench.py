@@ -1,0 +1,316 @@
+"""Throughput of the forward-Euler step on GB300: lattice-site updates per second (GLUPS)
+and the fraction of the measured HBM roofline.
+
+Default workload: 3D Gray-Scott, periodic 256^3, two fields, h = 1, Du = 0.2, Dv = 0.1,
+F = 0.04, k = 0.06, dt = 0.5, 7-point Laplacian, u = 1, v = 0 with 20 seeded 8^3 cubes
+(u = 0.5, v = 0.25) and 1 % multiplicative noise.  One bench "step" = ``--substeps``
+forward-Euler time steps of the whole grid (pf_step).  The state (2 fields x 2 copies x
+64 MiB = 268 MB) is larger than the 129 MB L2, so no flush is needed between iterations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pf|reference]
+Under torchrun every rank runs its own replica (weak scaling, no data-path collective);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "lattice-site updates/s (GLUPS), % of measured HBM roofline"
+UNIT = "GLUPS"
+WORKLOAD = "gs3d_256"
+BYTES_PER_LUP = {"gs": 16.0, "ac": 8.0, "ch": 8.0}  # k = 1: read + write every field once
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def _dist_init(use_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clock sampling
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on the host: full 256^3 grid, one step at a time until
+    ``budget_s`` of CPU time has elapsed (at least one step)."""
+    import oracle
+    w = synthetic.WORKLOADS[WORKLOAD]
+    x = tuple(a.astype(np.float64) for a in synthetic.workload_init(WORKLOAD))
+    sites = x[0].size
+    n, t0 = 0, time.perf_counter()
+    while True:
+        x = oracle.euler_step(w["model"], x, w["coeffs"], w["dt"], w["h"])
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sites * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 numpy forward-Euler step(s) of the full 256^3 Gray-Scott grid "
+                      f"({dt:.1f} s, single-threaded)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    w = synthetic.WORKLOADS[WORKLOAD]
+    x = tuple(a.astype(np.float64) for a in synthetic.workload_init(WORKLOAD))
+    sites = x[0].size
+    for _ in range(args.warmup):
+        x = oracle.euler_step(w["model"], x, w["coeffs"], w["dt"], w["h"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = oracle.euler_step(w["model"], x, w["coeffs"], w["dt"], w["h"])
+    dt = time.perf_counter() - t0
+    value = sites * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gs3d_256: 3D Gray-Scott 256^3 periodic, 2 fields, dt=0.5, "
+                               "one bench step = 1 forward-Euler step (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed FP64 numpy steps of the full 256^3 grid"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_2109_02598_gb300 as pf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    w = synthetic.WORKLOADS[WORKLOAD]
+    x0 = synthetic.workload_init(WORKLOAD)
+    sites = x0[0].size
+    S = args.substeps
+    with torch.cuda.stream(stream):
+        g = pf.Grid(x0[0].shape, 2, w["h"], stream=stream).set_model(w["model"], w["coeffs"], w["dt"])
+        g.write_fields(x0)
+        tuning = g.tuning
+        launches_per_step = sum(1 for _ in _launch_schedule(S, tuning[2]))
+
+        # ---- device-resident timing
+        for _ in range(args.warmup):
+            g.step(S)
+        g.synchronize()
+        _barrier(world)
+        sampler = ClockSampler(local).start() if rank == 0 else None
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.step(S)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1)
+        ms = _max_over_ranks(ms, world, dev)
+        _barrier(world)
+
+        # ---- end to end through the public API with pinned host buffers
+        host_in = [torch.from_numpy(a).pin_memory() for a in x0]
+        host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+        for _ in range(max(1, args.warmup // 2)):
+            for i, h in enumerate(host_in):
+                g.write_field(i, h)
+            g.step(S)
+            for i, h in enumerate(host_out):
+                g.read_field(i, out=h.numpy())
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for i, h in enumerate(host_in):
+                g.write_field(i, h)
+            g.step(S)
+            for i, h in enumerate(host_out):
+                g.read_field(i, out=h.numpy())
+        torch.cuda.synchronize()
+        e2e_s = _max_over_ranks(time.perf_counter() - t0, world, dev)
+        g.close()
+
+    if rank != 0:
+        return
+    hbm, peak_kind = _peaks()
+    n_launch = args.steps * launches_per_step
+    lups = sites * S * args.steps * world
+    value = lups / (ms * 1e-3) / 1e9
+    launch_ms = ms / n_launch
+    k = tuning[2]
+    alg_bytes = BYTES_PER_LUP[w["model"]] * sites  # per launch: every field read and written once
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gs3d_256: 3D Gray-Scott 256^3 periodic, 2 fields, Du=0.2 Dv=0.1 "
+                               "F=0.04 k=0.06 dt=0.5 h=1, 7-point Laplacian, 20 seeded 8^3 cubes "
+                               "+ 1% noise",
+                   "substeps_per_step": S, "tile": list(tuning[:2]), "k": k,
+                   "l2": "inputs larger than L2 (268 MB ping-pong state vs 129 MB L2)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback",
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "kernel": "fe3d (7-point GS, z-streaming)",
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms},
+        "e2e": {"value": sites * S * args.steps * world / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(a.nbytes for a in x0)),
+                "d2h_bytes_per_step": int(sum(a.nbytes for a in x0))},
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    print(json.dumps(line), flush=True)
+
+
+def _launch_schedule(n, k):
+    left = n
+    while left > 0:
+        kk = k
+        while kk > left:
+            kk >>= 1
+        yield kk
+        left -= kk
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pf", choices=["pf", "reference"])
+    ap.add_argument("--substeps", type=int, default=100)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        rank, world, _ = _dist_init(False)
+        run_reference(args, rank, world)
+        return
+    rank, world, local = _dist_init(True)
+    run_gpu(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * pfgpu — explicit forward-Euler time step of phase-field (Allen-Cahn "Model A",
+ * Cahn-Hilliard "Model B") and reaction-diffusion (Gray-Scott) models on periodic
+ * 2D/3D grids, computed by hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * The method (arxiv 2109.02598, SymPhas):
+ *   - grid: a row-major array with x fastest (Sec. 2.2.1 "Uniform Grid"), periodic on
+ *     every side (driver example, Fig. "driver_implementation", Sec. 2.4);
+ *   - derivatives: the second-order central Laplacian, 5 points in 2D and 7 in 3D
+ *     (Sec. 2.2.2); Model B applies it twice (the 13-point bilaplacian of Sec. 2.2.2);
+ *   - equations of motion (Sec. 3):  Model A  dphi/dt = lap phi + c1 phi - c2 phi^3;
+ *     Model B  dphi/dt = M lap(c2 phi^3 - c1 phi - lap phi);  Gray-Scott (named in
+ *     Sec. 1, standard two-species form)  du/dt = Du lap u - u v^2 + F (1 - u),
+ *     dv/dt = Dv lap v + u v^2 - (F + k) v;
+ *   - solver: forward Euler (Sec. 2.4.1), x^{n+1} = x^n + dt f(x^n) with every field
+ *     read from x^n — the paper's equation()/step() pair (Sec. 2.2.4) fused into one
+ *     kernel per step (or per k steps with temporal blocking).
+ *
+ * Conventions for every call:
+ *   - returns PF_OK (0) or a negative PF_ERR_* code; pf_last_error() then gives a
+ *     message (thread-local, valid until the next failing call on that thread);
+ *   - field arrays exchanged with the caller are dense float32, C order
+ *     [nz][ny][nx] (3D) or [ny][nx] (2D), x fastest; the library copies them into its
+ *     own padded layout (row pitch rounded up to a multiple of 4 floats);
+ *   - pointers passed in are borrowed: the library never frees or retains them past the
+ *     call, except that device-to-device copies are enqueued on the grid's stream and
+ *     read the source when that stream reaches them;
+ *   - handles (pf_grid_t, pf_batch_t) and the device memory behind them are owned by
+ *     the library and released by pf_destroy / pf_batch_destroy;
+ *   - all device work is enqueued on the CUDA stream given at creation (NULL = the
+ *     legacy default stream); calls that hand data to host memory synchronize it.
+ *   No call traps, aborts or waits without bound; bad arguments are rejected with
+ *   PF_ERR_INVALID_ARG before any device work is enqueued.
+ */
+#ifndef PFGPU_H
+#define PFGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define PF_OK 0
+#define PF_ERR_INVALID_ARG (-1) /* bad handle, size, index, model or coefficient count */
+#define PF_ERR_OOM (-2)         /* device or pinned-host allocation failed */
+#define PF_ERR_CUDA (-3)        /* a CUDA runtime/driver call failed (message has the name) */
+#define PF_ERR_UNSTABLE_DT (-4) /* dt beyond the linear forward-Euler stability bound */
+#define PF_ERR_NONFINITE (-5)   /* a reduction found NaN/Inf: the state blew up */
+#define PF_ERR_STATE (-6)       /* call out of order (no model set, no forward pass, ...) */
+
+/* ---------------------------------------------------------------- models */
+#define PF_MODEL_AC 1 /* Allen-Cahn, 1 field, coeffs {c1, c2}          (Sec. 3, Model A) */
+#define PF_MODEL_CH 2 /* Cahn-Hilliard, 1 field, coeffs {c1, c2, M}    (Sec. 3, Model B) */
+#define PF_MODEL_GS 3 /* Gray-Scott, 2 fields (u, v), coeffs {Du, Dv, F, k}   (Sec. 1) */
+
+/* ---------------------------------------------------------------- reductions */
+#define PF_REDUCE_MASS 1   /* h^d * sum_x phi_x of one field                         */
+#define PF_REDUCE_ENERGY 2 /* discrete free energy of field 0 (AC and CH only):
+                              h^d sum_x [1/2 sum_i ((phi_{x+e_i}-phi_x)/h)^2
+                                         - c1/2 phi^2 + c2/4 phi^4]                  */
+
+typedef struct pf_grid_s* pf_grid_t;
+typedef struct pf_batch_s* pf_batch_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int pf_version(void);
+
+/* Message of the last failing call on this thread ("" if none). Owned by the library. */
+const char* pf_last_error(void);
+
+/* ----------------------------------------------------------------- single grid */
+
+/* Create a periodic grid (the paper's Grid/System, Sec. 2.2.1 and 2.2.5).
+ *   dim      2 or 3;
+ *   n        n[0] = nx, n[1] = ny, n[2] = nz (ignored for dim 2); each in [1, 2^30];
+ *   n_fields 1 or 2 (Gray-Scott needs 2);
+ *   h        grid spacing, > 0;
+ *   stream   cudaStream_t to enqueue all work on (NULL = legacy default stream);
+ *   out      receives the handle.
+ * Allocates two device copies of every field (ping-pong), zero-filled.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_CUDA. */
+int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stream,
+                   pf_grid_t* out);
+
+/* Release the grid and its device memory (synchronizes its stream first). NULL is a no-op. */
+void pf_destroy(pf_grid_t g);
+
+/* Choose the equation of motion and its coefficients (Sec. 3; see PF_MODEL_*).
+ *   coeffs/n_coeffs  AC {c1, c2}, CH {c1, c2, M}, GS {Du, Dv, F, k} (exact count);
+ *   dt               time step, > 0;
+ *   force            0: reject dt beyond the linear stability bound of forward Euler
+ *                    (PF_ERR_UNSTABLE_DT, nothing changed); 1: accept it.
+ * The kernels use the coefficients rounded once to float32.
+ * Errors: PF_ERR_INVALID_ARG (model, count, field count, non-finite), PF_ERR_UNSTABLE_DT. */
+int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, double dt,
+                 int force);
+
+/* Copy field `field` in from `src` (dense float32 as above; host memory if
+ * src_on_device == 0, else device memory). Host copies complete before return;
+ * device copies are enqueued on the grid's stream.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
+int pf_write_field(pf_grid_t g, int field, const float* src, int src_on_device);
+
+/* Copy field `field` out to `dst` (dense float32). Host destinations are complete on
+ * return (the stream is synchronized); device destinations are enqueued.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
+int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device);
+
+/* Advance the state by n_steps forward-Euler steps (Sec. 2.4.1), asynchronously on the
+ * grid's stream. Uses temporal blocking of depth k (pf_set_tuning) where the model and
+ * dimension support it; the result is bitwise the same for every k and tile shape.
+ * n_steps == 0 is a no-op. Errors: PF_ERR_STATE (no model), PF_ERR_INVALID_ARG (n < 0),
+ * PF_ERR_CUDA. */
+int pf_step(pf_grid_t g, int64_t n_steps);
+
+/* Deterministic reduction of the current state into *out (see PF_REDUCE_*): warp
+ * shuffles to per-block partial sums in FP64, then one fixed-order FP64 sum.
+ * Synchronizes the stream. Errors: PF_ERR_INVALID_ARG, PF_ERR_STATE (energy without an
+ * AC/CH model), PF_ERR_CUDA, PF_ERR_NONFINITE (*out is still written). */
+int pf_reduce(pf_grid_t g, int what, int field, double* out);
+
+/* Kernel tuning: tile_x, tile_y (2D tile, or xy tile of the 3D z-streaming kernel) and
+ * k_steps (temporal-blocking depth, 2D only). 0 for any value = library default.
+ * Unsupported combinations are rejected with PF_ERR_INVALID_ARG.
+ * Supported: 2D tiles 64x16, 128x16, 32x32, 128x32; k in {1, 2, 4} (CH: {1, 2});
+ * 3D tiles 32x16, 64x8 (k = 1). */
+int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
+
+/* The tuning in effect (after defaults are resolved). */
+int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps);
+
+/* Time every supported (tile, k) for this grid and model on `probe_launches` launches
+ * each (CUDA events), keep the fastest and report it. The state is not changed: probe
+ * launches read the current buffer and write the spare one.
+ * Errors: PF_ERR_STATE (no model), PF_ERR_CUDA. */
+int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps);
+
+/* Block until all work enqueued on the grid's stream is done. */
+int pf_synchronize(pf_grid_t g);
+
+/* Current device addresses of field `field` in the padded layout, and that layout:
+ * row pitch and plane stride in floats. For zero-copy interop only; the addresses
+ * change after every pf_step (ping-pong). */
+int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFGPU_H */

@@ -1,0 +1,10 @@
+"""GB300-native explicit forward-Euler step for phase-field (Allen-Cahn, Cahn-Hilliard)
+and reaction-diffusion (Gray-Scott) models on periodic 2D/3D grids (arxiv 2109.02598).
+
+The compute path is libpfgpu.so (hand-written CUDA for sm_103a behind the C ABI of
+``include/pfgpu.h``); this package only marshals arguments to it.
+"""
+from ._lib import PfError, load  # noqa: F401
+from .grid import Grid  # noqa: F401
+
+__all__ = ["Grid", "PfError", "load"]

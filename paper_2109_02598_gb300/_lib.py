@@ -1,0 +1,100 @@
+"""ctypes loader for libpfgpu.so (the C ABI of include/pfgpu.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libpfgpu.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pfgpu.h")
+
+PF_OK = 0
+PF_ERR_INVALID_ARG = -1
+PF_ERR_OOM = -2
+PF_ERR_CUDA = -3
+PF_ERR_UNSTABLE_DT = -4
+PF_ERR_NONFINITE = -5
+PF_ERR_STATE = -6
+
+PF_MODEL_AC = 1
+PF_MODEL_CH = 2
+PF_MODEL_GS = 3
+MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS}
+MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2}
+
+PF_REDUCE_MASS = 1
+PF_REDUCE_ENERGY = 2
+
+_c_int64_p = ctypes.POINTER(ctypes.c_int64)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pf_version": (ctypes.c_int, []),
+    "pf_last_error": (ctypes.c_char_p, []),
+    "pf_create_grid": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_double,
+                                      _vp, ctypes.POINTER(_vp)]),
+    "pf_destroy": (None, [_vp]),
+    "pf_set_model": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int]),
+    "pf_write_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pf_reduce": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _c_double_p]),
+    "pf_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pf_get_tuning": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
+    "pf_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p]),
+    "pf_synchronize": (ctypes.c_int, [_vp]),
+    "pf_field_view": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), _c_int64_p,
+                                     _c_int64_p]),
+}
+
+
+class PfError(RuntimeError):
+    """A libpfgpu call returned a negative status."""
+
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once) and declare its signatures. Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libpfgpu.so not found at {path}: build it with __graft_entry__.build() "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc: int) -> int:
+    if rc != PF_OK:
+        msg = load().pf_last_error()
+        raise PfError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/pfgpu.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z0-9_]+)\s*\(", text)))

@@ -1,0 +1,412 @@
+// C ABI of libpfgpu: grid handles, model selection, field I/O, stepping, reductions and
+// tuning.  Declarations and contracts are in include/pfgpu.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "pf_grid.h"
+#include "pf_internal.h"
+
+namespace pf {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s: %s", (int)e, cudaGetErrorName(e), what,
+            cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
+}
+
+int invalid(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return PF_ERR_INVALID_ARG;
+}
+
+int model_fields(int model) {
+  switch (model) {
+    case PF_MODEL_AC: return 1;
+    case PF_MODEL_CH: return 1;
+    case PF_MODEL_GS: return 2;
+  }
+  return 0;
+}
+
+int model_ncoeffs(int model) {
+  switch (model) {
+    case PF_MODEL_AC: return 2;
+    case PF_MODEL_CH: return 3;
+    case PF_MODEL_GS: return 4;
+  }
+  return 0;
+}
+
+// Linear forward-Euler stability: dt * |largest eigenvalue of the linearised right-hand
+// side| <= 2, with the periodic Laplacian's spectrum in [-4d/h^2, 0] and, for AC/CH, the
+// cubic term linearised about |phi| <= 1 (slope between -c1 and 3 c2 - c1).
+double stable_dt_limit(int model, int dim, double h, const double* c) {
+  const double lmax = 4.0 * dim / (h * h);
+  switch (model) {
+    case PF_MODEL_AC: {
+      const double s = lmax + std::fmax(0.0, 3.0 * c[1] - c[0]);
+      return s > 0 ? 2.0 / s : INFINITY;
+    }
+    case PF_MODEL_CH: {
+      const double s = c[2] * lmax * (lmax + std::fmax(0.0, 3.0 * c[1] - c[0]));
+      return s > 0 ? 2.0 / s : INFINITY;
+    }
+    case PF_MODEL_GS: {
+      const double s = std::fmax(c[0], c[1]) * lmax + c[2] + c[3];
+      return s > 0 ? 2.0 / s : INFINITY;
+    }
+  }
+  return 0.0;
+}
+
+ModelParams make_params(int model, const double* c, double dt, double h) {
+  ModelParams m{};
+  m.dt = (float)dt;
+  m.inv_h2 = (float)(1.0 / (h * h));
+  switch (model) {
+    case PF_MODEL_AC:
+      m.a0 = (float)c[0];
+      m.a1 = (float)c[1];
+      break;
+    case PF_MODEL_CH:
+      m.a0 = (float)c[0];
+      m.a1 = (float)c[1];
+      m.a2 = (float)(dt * c[2]);
+      break;
+    case PF_MODEL_GS:
+      m.a0 = (float)c[0];
+      m.a1 = (float)c[1];
+      m.a2 = (float)c[2];
+      m.a3 = (float)(c[2] + c[3]);
+      break;
+  }
+  return m;
+}
+
+Geom grid_geom(const pf_grid_s* g) {
+  Geom q{};
+  q.dim = g->dim;
+  q.nx = g->nx;
+  q.ny = g->ny;
+  q.nz = g->nz;
+  q.pitch = g->pitch;
+  q.plane = g->plane;
+  return q;
+}
+
+int resolve_tuning(pf_grid_s* g) {
+  if (g->dim == 2) {
+    if (g->tile < 0) g->tile = 1;  // 128 x 16
+    if (g->k <= 0) g->k = 1;
+    if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
+  } else {
+    if (g->tile < 0) g->tile = 0;  // 32 x 16
+    g->k = 1;
+  }
+  return PF_OK;
+}
+
+// One launch advancing `k` steps from buffer `src` into buffer `dst`.
+cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst) {
+  FieldPtrs in{};
+  FieldOut out{};
+  for (int f = 0; f < g->nf; ++f) {
+    in.f[f] = g->buf[src][f];
+    out.f[f] = g->buf[dst][f];
+  }
+  const Geom q = grid_geom(g);
+  if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, g->stream);
+  return launch_fe3d(g->model, tile, q, in, out, g->params, g->stream);
+}
+
+int check_grid(pf_grid_s* g) {
+  if (g == nullptr || g->magic != kGridMagic) return invalid("invalid grid handle");
+  return PF_OK;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" {
+
+int pf_version(void) { return 10000; }
+
+const char* pf_last_error(void) { return g_err; }
+
+int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stream,
+                   pf_grid_t* out) {
+  if (out == nullptr) return invalid("out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return invalid("dim must be 2 or 3 (got %d)", dim);
+  if (n == nullptr) return invalid("n is NULL");
+  const int64_t nz = dim == 3 ? n[2] : 1;
+  const int64_t lim = (int64_t)1 << 30;
+  if (n[0] < 1 || n[1] < 1 || nz < 1 || n[0] > lim || n[1] > lim || nz > lim)
+    return invalid("grid sizes must be in [1, 2^30] (got %lld x %lld x %lld)",
+                   (long long)n[0], (long long)n[1], (long long)nz);
+  if (n_fields < 1 || n_fields > PF_MAX_FIELDS)
+    return invalid("n_fields must be 1 or 2 (got %d)", n_fields);
+  if (!(h > 0.0) || !std::isfinite(h)) return invalid("h must be finite and > 0");
+  const int64_t pitch = (n[0] + 3) / 4 * 4;
+  const int64_t plane = pitch * n[1];
+  const int64_t elems = plane * nz;
+  if (elems > ((int64_t)1 << 36)) return invalid("grid too large");
+  pf_grid_s* g = new (std::nothrow) pf_grid_s();
+  if (g == nullptr) return PF_ERR_OOM;
+  g->magic = kGridMagic;
+  g->dim = dim;
+  g->nx = (int)n[0];
+  g->ny = (int)n[1];
+  g->nz = (int)nz;
+  g->nf = n_fields;
+  g->h = h;
+  g->stream = (cudaStream_t)stream;
+  g->pitch = pitch;
+  g->plane = plane;
+  g->field_elems = elems;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->base, sizeof(float) * elems * 2 * n_fields);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->base, 0, sizeof(float) * elems * 2 * n_fields, g->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&g->red_partials, sizeof(double) * (kReduceBlocks + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->red_host, sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "pf_create_grid allocation");
+    pf_destroy(g);
+    return rc;
+  }
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < n_fields; ++f) g->buf[b][f] = g->base + (b * n_fields + f) * elems;
+  g->cur = 0;
+  g->tile = -1;
+  g->k = 0;
+  resolve_tuning(g);
+  *out = g;
+  return PF_OK;
+}
+
+void pf_destroy(pf_grid_t g) {
+  if (g == nullptr || g->magic != kGridMagic) return;
+  cudaStreamSynchronize(g->stream);
+  pf::adjoint_release(g);
+  if (g->base) cudaFree(g->base);
+  if (g->red_partials) cudaFree(g->red_partials);
+  if (g->red_host) cudaFreeHost(g->red_host);
+  g->magic = 0;
+  delete g;
+}
+
+int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, double dt,
+                 int force) {
+  if (int rc = check_grid(g)) return rc;
+  if (model_fields(model) == 0) return invalid("unknown model %d", model);
+  if (model_fields(model) != g->nf)
+    return invalid("model %d needs %d field(s); grid has %d", model, model_fields(model), g->nf);
+  if (coeffs == nullptr || n_coeffs != model_ncoeffs(model))
+    return invalid("model %d takes exactly %d coefficients (got %d)", model,
+                   model_ncoeffs(model), n_coeffs);
+  for (int i = 0; i < n_coeffs; ++i)
+    if (!std::isfinite(coeffs[i])) return invalid("coefficient %d is not finite", i);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("dt must be finite and > 0");
+  const double lim = stable_dt_limit(model, g->dim, g->h, coeffs);
+  if (dt > lim && !force) {
+    set_error("dt = %g exceeds the forward-Euler stability limit %g for this model and grid "
+              "(pass force=1 to accept)", dt, lim);
+    return PF_ERR_UNSTABLE_DT;
+  }
+  g->model = model;
+  for (int i = 0; i < n_coeffs; ++i) g->coeffs[i] = coeffs[i];
+  g->dt = dt;
+  g->params = make_params(model, coeffs, dt, g->h);
+  g->model_set = 1;
+  resolve_tuning(g);
+  return PF_OK;
+}
+
+int pf_write_field(pf_grid_t g, int field, const float* src, int src_on_device) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  if (src == nullptr) return invalid("src is NULL");
+  const size_t w = sizeof(float) * g->nx;
+  PF_CUDA_TRY(cudaMemcpy2DAsync(g->buf[g->cur][field], sizeof(float) * g->pitch, src, w, w,
+                                (size_t)g->ny * g->nz,
+                                src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                g->stream));
+  if (!src_on_device) PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PF_OK;
+}
+
+int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  if (dst == nullptr) return invalid("dst is NULL");
+  const size_t w = sizeof(float) * g->nx;
+  PF_CUDA_TRY(cudaMemcpy2DAsync(dst, w, g->buf[g->cur][field], sizeof(float) * g->pitch, w,
+                                (size_t)g->ny * g->nz,
+                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                g->stream));
+  if (!dst_on_device) PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PF_OK;
+}
+
+int pf_step(pf_grid_t g, int64_t n_steps) {
+  if (int rc = check_grid(g)) return rc;
+  if (!g->model_set) {
+    set_error("pf_step: no model set (call pf_set_model first)");
+    return PF_ERR_STATE;
+  }
+  if (n_steps < 0) return invalid("n_steps must be >= 0");
+  int64_t left = n_steps;
+  while (left > 0) {
+    int k = g->k;
+    while (k > left) k >>= 1;  // k in {4, 2, 1}
+    PF_CUDA_TRY(launch_step(g, g->tile, k, g->cur, 1 - g->cur));
+    g->cur = 1 - g->cur;
+    left -= k;
+  }
+  return PF_OK;
+}
+
+int pf_reduce(pf_grid_t g, int what, int field, double* out) {
+  if (int rc = check_grid(g)) return rc;
+  if (out == nullptr) return invalid("out is NULL");
+  if (what != PF_REDUCE_MASS && what != PF_REDUCE_ENERGY) return invalid("unknown reduction %d", what);
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  double c1 = 0, c2 = 0;
+  if (what == PF_REDUCE_ENERGY) {
+    if (!g->model_set || (g->model != PF_MODEL_AC && g->model != PF_MODEL_CH)) {
+      set_error("energy needs an Allen-Cahn or Cahn-Hilliard model");
+      return PF_ERR_STATE;
+    }
+    c1 = g->coeffs[0];
+    c2 = g->coeffs[1];
+  }
+  PF_CUDA_TRY(launch_reduce(what, grid_geom(g), g->buf[g->cur][field], c1, c2, g->h,
+                            g->red_partials, g->red_partials + kReduceBlocks, g->stream));
+  PF_CUDA_TRY(cudaMemcpyAsync(g->red_host, g->red_partials + kReduceBlocks, sizeof(double),
+                              cudaMemcpyDeviceToHost, g->stream));
+  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  *out = *g->red_host;
+  if (!std::isfinite(*out)) {
+    set_error("reduction is not finite (%g): the state has blown up", *out);
+    return PF_ERR_NONFINITE;
+  }
+  return PF_OK;
+}
+
+int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
+  if (int rc = check_grid(g)) return rc;
+  int tile = -1;
+  if (tile_x == 0 && tile_y == 0) {
+    tile = -1;
+  } else if (g->dim == 2) {
+    tile = tile2d_id(tile_x, tile_y);
+    if (tile < 0) return invalid("unsupported 2D tile %dx%d", tile_x, tile_y);
+  } else {
+    tile = tile3d_id(tile_x, tile_y);
+    if (tile < 0) return invalid("unsupported 3D tile %dx%d", tile_x, tile_y);
+  }
+  if (k_steps < 0) return invalid("k_steps must be >= 0");
+  if (g->dim == 3 && k_steps > 1) return invalid("3D grids support k = 1 only");
+  if (k_steps > 0 && g->dim == 2) {
+    const int model = g->model_set ? g->model : PF_MODEL_AC;
+    if (!fe2d_supported(model, k_steps))
+      return invalid("temporal blocking depth %d unsupported for this model", k_steps);
+  }
+  g->tile = tile;
+  g->k = k_steps;
+  return resolve_tuning(g);
+}
+
+int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps) {
+  if (int rc = check_grid(g)) return rc;
+  int tx, ty;
+  if (g->dim == 2)
+    tile2d_shape(g->tile, &tx, &ty);
+  else
+    tile3d_shape(g->tile, &tx, &ty);
+  if (tile_x) *tile_x = tx;
+  if (tile_y) *tile_y = ty;
+  if (k_steps) *k_steps = g->k;
+  return PF_OK;
+}
+
+int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps) {
+  if (int rc = check_grid(g)) return rc;
+  if (!g->model_set) {
+    set_error("pf_autotune: no model set");
+    return PF_ERR_STATE;
+  }
+  if (probe_launches < 1) probe_launches = 3;
+  cudaEvent_t e0, e1;
+  PF_CUDA_TRY(cudaEventCreate(&e0));
+  PF_CUDA_TRY(cudaEventCreate(&e1));
+  float best = INFINITY;
+  int best_tile = g->tile, best_k = g->k;
+  const int ntiles = g->dim == 2 ? kNumTiles2D : kNumTiles3D;
+  static const int ks[3] = {1, 2, 4};
+  int rc = PF_OK;
+  for (int t = 0; t < ntiles && rc == PF_OK; ++t) {
+    for (int ki = 0; ki < 3 && rc == PF_OK; ++ki) {
+      const int k = ks[ki];
+      if (g->dim == 3 && k > 1) continue;
+      if (g->dim == 2 && !fe2d_supported(g->model, k)) continue;
+      cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
+      for (int i = 0; i < probe_launches && e == cudaSuccess; ++i)
+        e = launch_step(g, t, k, g->cur, 1 - g->cur);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "pf_autotune probe");
+        break;
+      }
+      const float per_step = ms / (probe_launches * k);
+      if (per_step < best) {
+        best = per_step;
+        best_tile = t;
+        best_k = k;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PF_OK) return rc;
+  g->tile = best_tile;
+  g->k = best_k;
+  return pf_get_tuning(g, tile_x, tile_y, k_steps);
+}
+
+int pf_synchronize(pf_grid_t g) {
+  if (int rc = check_grid(g)) return rc;
+  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PF_OK;
+}
+
+int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  if (dev_ptr) *dev_ptr = g->buf[g->cur][field];
+  if (pitch) *pitch = g->pitch;
+  if (plane) *plane = g->plane;
+  return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// 2D forward-Euler step with temporal blocking (Sec. 2.4.1 solver, Sec. 2.2.2 stencils,
+// Sec. 3 models) — one fused kernel per k steps.
+//
+// A CTA owns a TX x TY output tile.  It stages the tile plus a periodic halo of
+// H = k * R sites (R = 1 for AC/GS, 2 for CH) in shared memory, runs k forward-Euler
+// sub-steps there on a region that shrinks by R per sub-step (halo sites are recomputed
+// redundantly instead of exchanged), and writes only the last sub-step to HBM.  HBM
+// traffic per site and step is therefore 2 * NF * 4 / k bytes.  Model B computes the
+// chemical potential mu on the region one ring wider than the phi update and never
+// stores it to HBM (the paper's provisional variable, Sec. 2.3.2, kept on chip).
+//
+// The tile body is a device function so the batched runner (many grids, one launch)
+// executes exactly the same arithmetic.
+#include "pf_fe2d_tile.cuh"
+#include "pf_internal.h"
+
+namespace pf {
+
+namespace {
+
+template <int MODEL, int K, int TX, int TY>
+__global__ void __launch_bounds__(kNT2) fe2d_kernel(FieldPtrs in, FieldOut out, Geom g,
+                                                    ModelParams m) {
+  extern __shared__ __align__(16) float sm[];
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * TY;
+  fe2d_tile<MODEL, K, TX, TY>(in, out, g.nx, g.ny, g.pitch, x0, y0, m, sm);
+}
+
+template <int MODEL, int K, int TX, int TY>
+cudaError_t launch_one(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
+                       cudaStream_t s) {
+  using C = Cfg2<MODEL, K, TX, TY>;
+  const size_t smem = sizeof(float) * C::SMEM_FLOATS;
+  static bool attr_done = false;  // per instantiation; idempotent if raced
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(fe2d_kernel<MODEL, K, TX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
+  fe2d_kernel<MODEL, K, TX, TY><<<grid, kNT2, smem, s>>>(in, out, g, m);
+  return cudaGetLastError();
+}
+
+template <int MODEL, int K>
+cudaError_t launch_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
+                        const ModelParams& m, cudaStream_t s) {
+  switch (tile_id) {
+    case 0: return launch_one<MODEL, K, 64, 16>(g, in, out, m, s);
+    case 1: return launch_one<MODEL, K, 128, 16>(g, in, out, m, s);
+    case 2: return launch_one<MODEL, K, 32, 32>(g, in, out, m, s);
+    case 3: return launch_one<MODEL, K, 128, 32>(g, in, out, m, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+void tile2d_shape(int tile_id, int* tx, int* ty) {
+  static const int s[kNumTiles2D][2] = {{64, 16}, {128, 16}, {32, 32}, {128, 32}};
+  *tx = s[tile_id][0];
+  *ty = s[tile_id][1];
+}
+
+int tile2d_id(int tx, int ty) {
+  for (int i = 0; i < kNumTiles2D; ++i) {
+    int a, b;
+    tile2d_shape(i, &a, &b);
+    if (a == tx && b == ty) return i;
+  }
+  return -1;
+}
+
+bool fe2d_supported(int model, int k) {
+  if (model == PF_MODEL_CH) return k == 1 || k == 2;
+  return k == 1 || k == 2 || k == 4;
+}
+
+cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs in,
+                        FieldOut out, const ModelParams& m, cudaStream_t s) {
+  if (tile_id < 0 || tile_id >= kNumTiles2D || !fe2d_supported(model, k))
+    return cudaErrorInvalidValue;
+  switch (model) {
+    case PF_MODEL_AC:
+      if (k == 1) return launch_tile<PF_MODEL_AC, 1>(tile_id, g, in, out, m, s);
+      if (k == 2) return launch_tile<PF_MODEL_AC, 2>(tile_id, g, in, out, m, s);
+      return launch_tile<PF_MODEL_AC, 4>(tile_id, g, in, out, m, s);
+    case PF_MODEL_GS:
+      if (k == 1) return launch_tile<PF_MODEL_GS, 1>(tile_id, g, in, out, m, s);
+      if (k == 2) return launch_tile<PF_MODEL_GS, 2>(tile_id, g, in, out, m, s);
+      return launch_tile<PF_MODEL_GS, 4>(tile_id, g, in, out, m, s);
+    case PF_MODEL_CH:
+      if (k == 1) return launch_tile<PF_MODEL_CH, 1>(tile_id, g, in, out, m, s);
+      return launch_tile<PF_MODEL_CH, 2>(tile_id, g, in, out, m, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pf

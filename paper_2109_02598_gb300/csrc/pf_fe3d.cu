@@ -1,0 +1,248 @@
+// 3D forward-Euler step, z-streaming (Sec. 2.4.1 solver, Sec. 2.2.2 7-point stencil,
+// Sec. 3 models).  General kernel for any grid size: a CTA owns a TX x TY column of the
+// xy plane and a chunk of tz planes; it streams through z keeping a ring of three
+// planes (z-1, z, z+1) with a periodic xy halo in shared memory, so every input value is
+// fetched from HBM once per CTA plus the halo.  Model B keeps three phi planes (halo 2)
+// and three mu planes (halo 1); mu is computed on chip and never stored.
+#include "pf_internal.h"
+
+namespace pf {
+
+namespace {
+
+constexpr int kNT3 = 256;
+
+template <int MODEL, int TX, int TY>
+struct Cfg3 {
+  static constexpr int NF = ModelTraits<MODEL>::NF;
+  static constexpr int R = ModelTraits<MODEL>::R;
+  // phi planes (halo R)
+  static constexpr int W = TX + 2 * R;
+  static constexpr int HT = TY + 2 * R;
+  static constexpr int PL = W * HT;
+  // mu planes (Model B only, halo 1)
+  static constexpr int W1 = TX + 2;
+  static constexpr int HT1 = TY + 2;
+  static constexpr int PL1 = W1 * HT1;
+  static constexpr int SMEM_FLOATS = 3 * NF * PL + (MODEL == PF_MODEL_CH ? 3 * PL1 : 0);
+};
+
+// Stage plane z (periodic) of every field into ring slot `slot`.
+template <class C>
+__device__ __forceinline__ void load_plane3d(const FieldPtrs& in, const Geom& g, int x0,
+                                             int y0, int z, int slot, float* sm) {
+  const int64_t zoff = (int64_t)wrap_index(z, g.nz) * g.plane;
+  for (int i = threadIdx.x; i < C::PL; i += kNT3) {
+    const int r = i / C::W;
+    const int c = i - r * C::W;
+    const int gy = wrap_index(y0 - C::R + r, g.ny);
+    const int gx = wrap_index(x0 - C::R + c, g.nx);
+    const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
+#pragma unroll
+    for (int f = 0; f < C::NF; ++f) sm[(slot * C::NF + f) * C::PL + i] = __ldg(in.f[f] + off);
+  }
+}
+
+// AC and Gray-Scott (stencil radius 1).
+template <int MODEL, int TX, int TY>
+__global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut out, Geom g,
+                                                       ModelParams m, int tz) {
+  using C = Cfg3<MODEL, TX, TY>;
+  constexpr int W = C::W;
+  constexpr int PL = C::PL;
+  extern __shared__ __align__(16) float sm[];
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * tz;
+  const int z1 = min(z0 + tz, g.nz);
+  load_plane3d<C>(in, g, x0, y0, z0 - 1, 0, sm);
+  load_plane3d<C>(in, g, x0, y0, z0, 1, sm);
+  int sb = 0, sc = 1, sa = 2;
+  for (int z = z0; z < z1; ++z) {
+    load_plane3d<C>(in, g, x0, y0, z + 1, sa, sm);
+    __syncthreads();
+    const int64_t zoff = (int64_t)z * g.plane;
+    for (int i = threadIdx.x; i < TX * TY; i += kNT3) {
+      const int rr = i / TX;
+      const int r = 1 + rr;
+      const int c = 1 + (i - rr * TX);
+      const int p = r * W + c;
+      const int gx = x0 + c - 1;
+      const int gy = y0 + r - 1;
+      float val[C::NF];
+      if constexpr (MODEL == PF_MODEL_AC) {
+        const float* cp = sm + sc * PL;
+        const float pc = cp[p];
+        const float l = lap3d(pc, cp[p - 1], cp[p + 1], cp[p - W], cp[p + W], sm[sb * PL + p],
+                              sm[sa * PL + p], m.inv_h2);
+        val[0] = ac_update(pc, l, m);
+      } else {
+        const float* cu = sm + (sc * 2) * PL;
+        const float* cv = cu + PL;
+        const float u = cu[p], v = cv[p];
+        const float lu = lap3d(u, cu[p - 1], cu[p + 1], cu[p - W], cu[p + W],
+                               sm[(sb * 2) * PL + p], sm[(sa * 2) * PL + p], m.inv_h2);
+        const float lv = lap3d(v, cv[p - 1], cv[p + 1], cv[p - W], cv[p + W],
+                               sm[(sb * 2 + 1) * PL + p], sm[(sa * 2 + 1) * PL + p], m.inv_h2);
+        gs_update(u, v, lu, lv, m, val[0], val[1]);
+      }
+      if (gx < g.nx && gy < g.ny) {
+        const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
+#pragma unroll
+        for (int f = 0; f < C::NF; ++f) out.f[f][off] = val[f];
+      }
+    }
+    __syncthreads();
+    const int t = sb;
+    sb = sc;
+    sc = sa;
+    sa = t;
+  }
+}
+
+// Model B: mu planes computed on chip from phi planes.
+template <int TX, int TY>
+__device__ __forceinline__ void ch_mu_plane(const float* phb, const float* phc,
+                                            const float* pha, float* mu,
+                                            const ModelParams& m) {
+  using C = Cfg3<PF_MODEL_CH, TX, TY>;
+  constexpr int W = C::W;
+  for (int i = threadIdx.x; i < C::PL1; i += kNT3) {
+    const int r1 = i / C::W1;
+    const int c1 = i - r1 * C::W1;
+    const int p = (r1 + 1) * W + (c1 + 1);  // position in the phi plane (halo 2)
+    const float pc = phc[p];
+    const float l = lap3d(pc, phc[p - 1], phc[p + 1], phc[p - W], phc[p + W], phb[p], pha[p],
+                          m.inv_h2);
+    mu[i] = ch_mu(pc, l, m);
+  }
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(kNT3) fe3d_ch_kernel(FieldPtrs in, FieldOut out, Geom g,
+                                                       ModelParams m, int tz) {
+  using C = Cfg3<PF_MODEL_CH, TX, TY>;
+  constexpr int W = C::W;
+  constexpr int PL = C::PL;
+  constexpr int W1 = C::W1;
+  constexpr int PL1 = C::PL1;
+  extern __shared__ __align__(16) float sm[];
+  float* ph = sm;           // 3 phi slots, slot(p) = (p - z0 + 6) % 3
+  float* mu = sm + 3 * PL;  // 3 mu slots, same slot rule
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * tz;
+  const int z1 = min(z0 + tz, g.nz);
+  auto slot = [&](int p) { return (p - z0 + 6) % 3; };
+  // prologue: mu(z0-1) from phi(z0-2..z0), then mu(z0) from phi(z0-1..z0+1)
+  load_plane3d<C>(in, g, x0, y0, z0 - 2, slot(z0 - 2), ph);
+  load_plane3d<C>(in, g, x0, y0, z0 - 1, slot(z0 - 1), ph);
+  load_plane3d<C>(in, g, x0, y0, z0, slot(z0), ph);
+  __syncthreads();
+  ch_mu_plane<TX, TY>(ph + slot(z0 - 2) * PL, ph + slot(z0 - 1) * PL, ph + slot(z0) * PL,
+                      mu + slot(z0 - 1) * PL1, m);
+  __syncthreads();
+  load_plane3d<C>(in, g, x0, y0, z0 + 1, slot(z0 + 1), ph);
+  __syncthreads();
+  ch_mu_plane<TX, TY>(ph + slot(z0 - 1) * PL, ph + slot(z0) * PL, ph + slot(z0 + 1) * PL,
+                      mu + slot(z0) * PL1, m);
+  __syncthreads();
+  for (int z = z0; z < z1; ++z) {
+    load_plane3d<C>(in, g, x0, y0, z + 2, slot(z + 2), ph);
+    __syncthreads();
+    ch_mu_plane<TX, TY>(ph + slot(z) * PL, ph + slot(z + 1) * PL, ph + slot(z + 2) * PL,
+                        mu + slot(z + 1) * PL1, m);
+    __syncthreads();
+    const float* mb = mu + slot(z - 1) * PL1;
+    const float* mc = mu + slot(z) * PL1;
+    const float* ma = mu + slot(z + 1) * PL1;
+    const float* pc = ph + slot(z) * PL;
+    const int64_t zoff = (int64_t)z * g.plane;
+    for (int i = threadIdx.x; i < TX * TY; i += kNT3) {
+      const int rr = i / TX;
+      const int cc = i - rr * TX;
+      const int q = (rr + 1) * W1 + (cc + 1);  // mu plane position
+      const float l = lap3d(mc[q], mc[q - 1], mc[q + 1], mc[q - W1], mc[q + W1], mb[q], ma[q],
+                            m.inv_h2);
+      const float v = ch_update(pc[(rr + 2) * W + (cc + 2)], l, m);
+      const int gx = x0 + cc;
+      const int gy = y0 + rr;
+      if (gx < g.nx && gy < g.ny) out.f[0][zoff + (int64_t)gy * g.pitch + gx] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <class KernelT>
+cudaError_t set_smem(KernelT k, size_t bytes, bool* done) {
+  if (*done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *done = true;
+  return e;
+}
+
+int choose_tz(const Geom& g, int tiles_xy) {
+  // enough CTAs for several waves on 152 SMs, but chunks long enough that the two
+  // extra prologue planes stay a small fraction
+  int tz = g.nz;
+  while (tz > 16 && (int64_t)tiles_xy * ((g.nz + tz - 1) / tz) < 4 * 152) tz = (tz + 1) / 2;
+  return tz;
+}
+
+template <int MODEL, int TX, int TY>
+cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
+                    cudaStream_t s) {
+  using C = Cfg3<MODEL, TX, TY>;
+  const size_t smem = sizeof(float) * C::SMEM_FLOATS;
+  static bool done = false;
+  const int bx = (g.nx + TX - 1) / TX, by = (g.ny + TY - 1) / TY;
+  const int tz = choose_tz(g, bx * by);
+  dim3 grid(bx, by, (g.nz + tz - 1) / tz);
+  if constexpr (MODEL == PF_MODEL_CH) {
+    cudaError_t e = set_smem(fe3d_ch_kernel<TX, TY>, smem, &done);
+    if (e != cudaSuccess) return e;
+    fe3d_ch_kernel<TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+  } else {
+    cudaError_t e = set_smem(fe3d_r1_kernel<MODEL, TX, TY>, smem, &done);
+    if (e != cudaSuccess) return e;
+    fe3d_r1_kernel<MODEL, TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODEL>
+cudaError_t launch3_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
+                         const ModelParams& m, cudaStream_t s) {
+  if (tile_id == 0) return launch3<MODEL, 32, 16>(g, in, out, m, s);
+  return launch3<MODEL, 64, 8>(g, in, out, m, s);
+}
+
+}  // namespace
+
+void tile3d_shape(int tile_id, int* tx, int* ty) {
+  static const int s[kNumTiles3D][2] = {{32, 16}, {64, 8}};
+  *tx = s[tile_id][0];
+  *ty = s[tile_id][1];
+}
+
+int tile3d_id(int tx, int ty) {
+  for (int i = 0; i < kNumTiles3D; ++i) {
+    int a, b;
+    tile3d_shape(i, &a, &b);
+    if (a == tx && b == ty) return i;
+  }
+  return -1;
+}
+
+cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
+                        const ModelParams& m, cudaStream_t s) {
+  if (tile_id < 0 || tile_id >= kNumTiles3D) return cudaErrorInvalidValue;
+  switch (model) {
+    case PF_MODEL_AC: return launch3_tile<PF_MODEL_AC>(tile_id, g, in, out, m, s);
+    case PF_MODEL_CH: return launch3_tile<PF_MODEL_CH>(tile_id, g, in, out, m, s);
+    case PF_MODEL_GS: return launch3_tile<PF_MODEL_GS>(tile_id, g, in, out, m, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pf

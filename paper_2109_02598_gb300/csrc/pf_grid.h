@@ -1,0 +1,61 @@
+// The grid handle behind pf_grid_t (the paper's Grid + System + Model state,
+// Sec. 2.2.1 and 2.2.5): geometry, the two ping-pong copies of every field in the padded
+// device layout, the model coefficients and the kernel tuning.
+#pragma once
+
+#include "pf_internal.h"
+
+namespace pf {
+
+constexpr uint32_t kGridMagic = 0x50464744u;  // "PFGD"
+
+struct AdjointState {
+  int64_t n_steps = 0;       // steps of the recorded forward pass
+  int64_t interval = 0;      // checkpoint interval C
+  int64_t n_ckpt = 0;        // checkpoints stored (states 0, C, 2C, ...)
+  float* ckpt = nullptr;     // n_ckpt * nf * field_elems floats
+  float* seg = nullptr;      // (C + 1) * nf * field_elems floats: one recomputed segment
+  float* lam = nullptr;      // 2 * nf * field_elems floats: adjoint ping-pong
+  double* gpart = nullptr;   // per-CTA parameter-gradient partials (4 per CTA)
+  double* gout = nullptr;    // 4 final sums (device)
+  double* ghost = nullptr;   // 4 final sums (pinned host)
+  int64_t gpart_cap = 0;     // CTAs the partial buffer holds
+  double coeffs[4] = {0, 0, 0, 0};
+  double dt = 0;
+  int ready = 0;             // a forward pass is recorded
+};
+
+}  // namespace pf
+
+struct pf_grid_s {
+  uint32_t magic = 0;
+  int dim = 0;
+  int nx = 0, ny = 0, nz = 1;
+  int nf = 0;
+  double h = 1.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t pitch = 0, plane = 0, field_elems = 0;
+  float* base = nullptr;
+  float* buf[2][PF_MAX_FIELDS] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int cur = 0;
+  int model = 0;
+  double coeffs[4] = {0, 0, 0, 0};
+  double dt = 0;
+  int model_set = 0;
+  pf::ModelParams params{};
+  int tile = -1;  // kernel tile id (2D or 3D table)
+  int k = 0;      // temporal-blocking depth
+  double* red_partials = nullptr;  // kReduceBlocks partials + 1 result
+  double* red_host = nullptr;      // pinned
+  pf::AdjointState adj;
+};
+
+namespace pf {
+void adjoint_release(pf_grid_s* g);
+int invalid(const char* fmt, ...);
+int check_grid(pf_grid_s* g);
+Geom grid_geom(const pf_grid_s* g);
+ModelParams make_params(int model, const double* c, double dt, double h);
+cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst);
+}  // namespace pf

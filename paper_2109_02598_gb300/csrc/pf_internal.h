@@ -1,0 +1,65 @@
+// Host-side declarations shared by the translation units of libpfgpu (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "pf_model.cuh"
+#include "pfgpu.h"
+
+#define PF_MAX_FIELDS 2
+
+namespace pf {
+
+// Geometry of one field in the padded device layout: [nz][ny][pitch] floats, x fastest,
+// pitch = nx rounded up to a multiple of 4 (16-byte rows); padding is never read as data.
+struct Geom {
+  int dim;
+  int nx, ny, nz;  // nz == 1 for 2D
+  int64_t pitch;   // floats per row
+  int64_t plane;   // floats per z-plane (pitch * ny)
+};
+
+struct FieldPtrs {
+  const float* f[PF_MAX_FIELDS];
+};
+struct FieldOut {
+  float* f[PF_MAX_FIELDS];
+};
+
+// Thread-local error reporting (pf_last_error).
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PF_CUDA_TRY(call)                                  \
+  do {                                                     \
+    cudaError_t pf_e_ = (call);                            \
+    if (pf_e_ != cudaSuccess) return pf::cuda_fail(pf_e_, #call); \
+  } while (0)
+
+// ---- 2D tiled forward-Euler kernel (temporal blocking depth k) -------------------
+// Tile ids: 0 = 64x16, 1 = 128x16, 2 = 32x32, 3 = 128x32.
+constexpr int kNumTiles2D = 4;
+void tile2d_shape(int tile_id, int* tx, int* ty);
+int tile2d_id(int tx, int ty);  // -1 if unsupported
+bool fe2d_supported(int model, int k);
+cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs in,
+                        FieldOut out, const ModelParams& m, cudaStream_t s);
+
+// ---- 3D z-streaming forward-Euler kernel (k = 1) --------------------------------
+// Tile ids: 0 = 32x16, 1 = 64x8.
+constexpr int kNumTiles3D = 2;
+void tile3d_shape(int tile_id, int* tx, int* ty);
+int tile3d_id(int tx, int ty);
+cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
+                        const ModelParams& m, cudaStream_t s);
+
+// ---- reductions -------------------------------------------------------------------
+// Writes one double to d_out. d_partials must hold kReduceBlocks doubles.
+constexpr int kReduceBlocks = 512;
+cudaError_t launch_reduce(int what, const Geom& g, const float* field, double c1, double c2,
+                          double h, double* d_partials, double* d_out, cudaStream_t s);
+
+}  // namespace pf

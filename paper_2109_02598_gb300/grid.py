@@ -1,0 +1,171 @@
+"""Python face of a pfgpu grid (argument marshalling over the C ABI of include/pfgpu.h).
+
+A ``Grid`` is the paper's Grid/System/Model triple (Sec. 2.2.1, 2.2.5): a periodic 2D or
+3D grid of one or two float32 fields, an equation of motion with its coefficients
+(Sec. 3) and the forward-Euler solver (Sec. 2.4.1).  Shapes follow numpy order,
+``(ny, nx)`` or ``(nz, ny, nx)``, x fastest (Sec. 2.2.1).  PyTorch supplies the CUDA
+stream and device tensors; all arithmetic runs in libpfgpu's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import MODEL_FIELDS, MODEL_IDS, check
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("pfgpu needs a CUDA device (there is no CPU fallback)")
+    return torch
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Grid:
+    """A periodic grid with ``n_fields`` float32 fields living on the GPU."""
+
+    def __init__(self, shape, n_fields: int = 1, h: float = 1.0, stream=None):
+        torch = _torch()
+        self._lib = _lib.load()
+        self.shape = tuple(int(s) for s in shape)
+        if len(self.shape) not in (2, 3):
+            raise ValueError("shape must be (ny, nx) or (nz, ny, nx)")
+        self.dim = len(self.shape)
+        self.n_fields = int(n_fields)
+        self.h = float(h)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nx, ny = self.shape[-1], self.shape[-2]
+        nz = self.shape[0] if self.dim == 3 else 1
+        n = (ctypes.c_int64 * 3)(nx, ny, nz)
+        handle = ctypes.c_void_p()
+        check(self._lib.pf_create_grid(self.dim, n, self.n_fields, self.h,
+                                       ctypes.c_void_p(_stream_handle(self.stream)),
+                                       ctypes.byref(handle)))
+        self._h = handle
+        self.model = None
+
+    # ---------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def sites(self) -> int:
+        return int(np.prod(self.shape))
+
+    # ---------------------------------------------------------------- model
+    def set_model(self, model: str, coeffs, dt: float, force: bool = False):
+        """model in {"ac", "ch", "gs"}; coeffs AC (c1, c2), CH (c1, c2, M), GS (Du, Dv, F, k)."""
+        c = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
+        check(self._lib.pf_set_model(self._h, MODEL_IDS[model], c, len(coeffs), float(dt),
+                                     1 if force else 0))
+        self.model = model
+        self.coeffs = tuple(float(x) for x in coeffs)
+        self.dt = float(dt)
+        return self
+
+    # ---------------------------------------------------------------- fields
+    def write_field(self, field: int, data):
+        """Copy in a dense float32 array of ``shape``: numpy (host) or torch (host/CUDA)."""
+        if hasattr(data, "data_ptr"):
+            t = data.detach()
+            if tuple(t.shape) != self.shape:
+                raise ValueError(f"field shape {tuple(t.shape)} != grid shape {self.shape}")
+            torch = _torch()
+            t = t.to(torch.float32).contiguous()
+            check(self._lib.pf_write_field(self._h, field, ctypes.c_void_p(t.data_ptr()),
+                                           1 if t.is_cuda else 0))
+            if t.is_cuda:
+                self._keep = t  # the copy is enqueued; keep the source alive until synced
+                self.synchronize()
+                self._keep = None
+            return self
+        a = np.ascontiguousarray(data, dtype=np.float32)
+        if a.shape != self.shape:
+            raise ValueError(f"field shape {a.shape} != grid shape {self.shape}")
+        check(self._lib.pf_write_field(self._h, field, a.ctypes.data_as(ctypes.c_void_p), 0))
+        return self
+
+    def write_fields(self, fields):
+        for i, f in enumerate(fields):
+            self.write_field(i, f)
+        return self
+
+    def read_field(self, field: int, device: bool = False, out=None):
+        """Field ``field`` as a numpy array (default) or a CUDA torch tensor."""
+        if device or (out is not None and hasattr(out, "data_ptr")):
+            torch = _torch()
+            if out is None:
+                out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+            check(self._lib.pf_read_field(self._h, field, ctypes.c_void_p(out.data_ptr()),
+                                          1 if out.is_cuda else 0))
+            return out
+        a = np.empty(self.shape, dtype=np.float32) if out is None else out
+        check(self._lib.pf_read_field(self._h, field, a.ctypes.data_as(ctypes.c_void_p), 0))
+        return a
+
+    def read_fields(self, device: bool = False):
+        return tuple(self.read_field(i, device=device) for i in range(self.n_fields))
+
+    # ---------------------------------------------------------------- stepping
+    def step(self, n_steps: int = 1):
+        check(self._lib.pf_step(self._h, int(n_steps)))
+        return self
+
+    def synchronize(self):
+        check(self._lib.pf_synchronize(self._h))
+
+    # ---------------------------------------------------------------- reductions
+    def mass(self, field: int = 0) -> float:
+        out = ctypes.c_double()
+        check(self._lib.pf_reduce(self._h, _lib.PF_REDUCE_MASS, field, ctypes.byref(out)))
+        return out.value
+
+    def energy(self) -> float:
+        out = ctypes.c_double()
+        check(self._lib.pf_reduce(self._h, _lib.PF_REDUCE_ENERGY, 0, ctypes.byref(out)))
+        return out.value
+
+    # ---------------------------------------------------------------- tuning
+    def set_tuning(self, tile_x: int = 0, tile_y: int = 0, k: int = 0):
+        check(self._lib.pf_set_tuning(self._h, tile_x, tile_y, k))
+        return self
+
+    @property
+    def tuning(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pf_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def autotune(self, probe_launches: int = 5):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pf_autotune(self._h, probe_launches, ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)))
+        return a.value, b.value, c.value

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every function include/pfgpu.h declares, and rejects
+bad arguments before touching the GPU (these calls run on a machine without one)."""
+import ctypes
+
+import pytest
+
+from paper_2109_02598_gb300 import _lib
+from paper_2109_02598_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _lib.header_functions()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    # and the binding declares a signature for each of them
+    assert set(declared) <= set(_lib.SIGNATURES)
+
+
+def test_version(lib):
+    assert lib.pf_version() >= 10000
+
+
+def _err(lib):
+    return lib.pf_last_error().decode()
+
+
+def test_create_grid_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(16, 16, 16)
+    assert lib.pf_create_grid(4, n, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    assert "dim" in _err(lib)
+    assert lib.pf_create_grid(2, n, 3, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_create_grid(2, n, 1, 0.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    bad = (ctypes.c_int64 * 3)(0, 16, 16)
+    assert lib.pf_create_grid(2, bad, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_create_grid(2, n, 1, 1.0, None, None) == _lib.PF_ERR_INVALID_ARG
+
+
+def test_calls_on_null_handle_fail_cleanly(lib):
+    c = (ctypes.c_double * 2)(1.0, 1.0)
+    assert lib.pf_set_model(None, 1, c, 2, 0.05, 0) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_step(None, 1) == _lib.PF_ERR_INVALID_ARG
+    out = ctypes.c_double()
+    assert lib.pf_reduce(None, 1, 0, ctypes.byref(out)) == _lib.PF_ERR_INVALID_ARG
+    lib.pf_destroy(None)  # no-op
+
+
+def test_loader_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        saved = _lib._lib
+        _lib._lib = None
+        try:
+            _lib.load(str(tmp_path / "missing.so"))
+        finally:
+            _lib._lib = saved

@@ -1,0 +1,243 @@
+"""Parity of the CUDA forward-Euler step (through the C ABI) with the FP64 oracle.
+
+Bars (float32 kernels against the FP64 oracle from the same float32 initial array):
+  one step            relative L-inf  <= 1e-6   (||x_gpu - x_ora||_inf / ||x_ora||_inf)
+  1000 steps          relative L2     <= 1e-3
+Every tile shape and temporal-blocking depth must give bitwise-identical results.
+Shapes span several tiles with ragged tails, grids smaller than a tile, and the full
+workload sizes (one step, every site)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+COEFFS = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06)}
+DT = {"ac": 0.05, "ch": 0.01, "gs": 0.5}
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02598_gb300.build import build
+    build()
+    import paper_2109_02598_gb300 as pf
+    return pf
+
+
+def init_fields(model, shape, seed=0):
+    if model == "ac":
+        return (synthetic.allen_cahn_init(shape, seed=100 + seed, lo=-0.5, hi=0.5),)
+    if model == "ch":
+        return (synthetic.cahn_hilliard_init(shape, seed=200 + seed, amp=0.3),)
+    n_seeds = max(2, int(np.prod(shape)) // 2000)
+    return synthetic.gray_scott_init(shape, seed=300 + seed, n_seeds=n_seeds, side=4,
+                                     noise=0.05)
+
+
+def gpu_run(pf, model, fields, n, coeffs=None, dt=None, h=1.0, tuning=None):
+    coeffs = COEFFS[model] if coeffs is None else coeffs
+    dt = DT[model] if dt is None else dt
+    g = pf.Grid(fields[0].shape, n_fields=len(fields), h=h)
+    g.set_model(model, coeffs, dt, force=True)
+    if tuning is not None:
+        g.set_tuning(*tuning)
+    g.write_fields(fields)
+    g.step(n)
+    out = g.read_fields()
+    g.close()
+    return out
+
+
+def rel_linf(got, ref):
+    num = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(got, ref))
+    den = max(np.abs(r).max() for r in ref)
+    return num / den
+
+
+def rel_l2(got, ref):
+    num = np.sqrt(sum(((g.astype(np.float64) - r) ** 2).sum() for g, r in zip(got, ref)))
+    den = np.sqrt(sum((r ** 2).sum() for r in ref))
+    return num / den
+
+
+SHAPES_2D = [(37, 150), (64, 64), (5, 7), (1, 9), (130, 33)]
+SHAPES_3D = [(9, 20, 70), (4, 4, 4), (3, 17, 33), (17, 5, 130)]
+
+
+@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D)
+def test_single_step_parity(pf, model, shape):
+    x0 = init_fields(model, shape)
+    h = 0.9
+    ref = oracle.euler_step(model, x0, COEFFS[model], DT[model] * 0.5, h)
+    got = gpu_run(pf, model, x0, 1, dt=DT[model] * 0.5, h=h)
+    assert rel_linf(got, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+@pytest.mark.parametrize("shape", [(37, 150), (6, 11, 40)])
+def test_twenty_steps_parity(pf, model, shape):
+    x0 = init_fields(model, shape, seed=1)
+    ref = oracle.run(model, x0, COEFFS[model], DT[model], 20)
+    got = gpu_run(pf, model, x0, 20)
+    assert rel_linf(got, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+def test_tiles_and_temporal_blocking_are_bitwise_identical(pf, model):
+    x0 = init_fields(model, (70, 200), seed=2)
+    base = gpu_run(pf, model, x0, 12, tuning=(64, 16, 1))
+    ks = (1, 2) if model == "ch" else (1, 2, 4)
+    for tile in [(64, 16), (128, 16), (32, 32), (128, 32)]:
+        for k in ks:
+            got = gpu_run(pf, model, x0, 12, tuning=(tile[0], tile[1], k))
+            for a, b in zip(base, got):
+                assert np.array_equal(a, b), (tile, k)
+    # n not a multiple of k: remainder launches with smaller k
+    got = gpu_run(pf, model, x0, 12, tuning=(128, 16, 2 if model == "ch" else 4))
+    for a, b in zip(base, got):
+        assert np.array_equal(a, b)
+    # 3D tiles
+    y0 = init_fields(model, (12, 19, 70), seed=3)
+    b3 = gpu_run(pf, model, y0, 5, tuning=(32, 16, 1))
+    g3 = gpu_run(pf, model, y0, 5, tuning=(64, 8, 1))
+    for a, b in zip(b3, g3):
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- workload configurations
+
+def test_ac2d_128_1000_steps(pf):
+    w = synthetic.WORKLOADS["ac2d_128"]
+    x0 = synthetic.workload_init("ac2d_128")
+    ref = oracle.run("ac", x0, w["coeffs"], w["dt"], 1000, w["h"])
+    got = gpu_run(pf, "ac", x0, 1000, w["coeffs"], w["dt"], w["h"])
+    assert rel_l2(got, ref) <= 1e-3
+    one = gpu_run(pf, "ac", x0, 1, w["coeffs"], w["dt"], w["h"])
+    assert rel_linf(one, oracle.euler_step("ac", x0, w["coeffs"], w["dt"])) <= 1e-6
+
+
+def test_ch2d_1000_steps_256(pf):
+    # the 2048^2 recipe at 256^2 so the oracle finishes 1000 steps in seconds
+    w = synthetic.WORKLOADS["ch2d_2048"]
+    x0 = synthetic.workload_init("ch2d_2048", shape=(256, 256))
+    ref = oracle.run("ch", x0, w["coeffs"], w["dt"], 1000, w["h"])
+    got = gpu_run(pf, "ch", x0, 1000, w["coeffs"], w["dt"], w["h"])
+    assert rel_l2(got, ref) <= 1e-3
+
+
+def test_gs3d_1000_steps_48(pf):
+    w = synthetic.WORKLOADS["gs3d_256"]
+    x0 = synthetic.workload_init("gs3d_256", shape=(48, 48, 48))
+    ref = oracle.run("gs", x0, w["coeffs"], w["dt"], 1000, w["h"])
+    got = gpu_run(pf, "gs", x0, 1000, w["coeffs"], w["dt"], w["h"])
+    assert rel_l2(got, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("name", ["ch2d_2048", "gs3d_256"])
+def test_full_size_single_step(pf, name):
+    w = synthetic.WORKLOADS[name]
+    x0 = synthetic.workload_init(name)
+    ref = oracle.euler_step(w["model"], x0, w["coeffs"], w["dt"], w["h"])
+    got = gpu_run(pf, w["model"], x0, 1, w["coeffs"], w["dt"], w["h"])
+    assert rel_linf(got, ref) <= 1e-6
+
+
+def test_full_size_ch2d_mass_conserved(pf):
+    w = synthetic.WORKLOADS["ch2d_2048"]
+    (x0,) = synthetic.workload_init("ch2d_2048")
+    g = pf.Grid(x0.shape, 1, w["h"]).set_model("ch", w["coeffs"], w["dt"])
+    g.write_field(0, x0)
+    m0 = g.mass()
+    assert abs(m0 - oracle.mass(x0)) <= 1e-9 * np.abs(x0.astype(np.float64)).sum()
+    g.step(2000)
+    m1 = g.mass()
+    assert abs(m1 - m0) / x0.size <= 1e-6  # mean drift per site
+    phi = g.read_field(0)
+    assert np.isfinite(phi).all() and phi.std() > x0.std()  # spinodal growth happened
+    g.close()
+
+
+def test_full_size_gs3d_stays_bounded(pf):
+    w = synthetic.WORKLOADS["gs3d_256"]
+    x0 = synthetic.workload_init("gs3d_256")
+    g = pf.Grid(x0[0].shape, 2, w["h"]).set_model("gs", w["coeffs"], w["dt"])
+    g.write_fields(x0)
+    g.step(500)
+    u, v = g.read_fields()
+    assert np.isfinite(u).all() and np.isfinite(v).all()
+    assert u.min() >= -0.01 and u.max() <= 1.01 and v.min() >= -0.01 and v.max() <= 1.01
+    # far from the seeds the state is still the exact fixed point neighbourhood
+    g.close()
+
+
+# ---------------------------------------------------------------- invariants on the GPU
+
+def test_gs_fixed_point_is_bitwise(pf):
+    for shape in [(33, 70), (5, 9, 13)]:
+        u = np.ones(shape, np.float32)
+        v = np.zeros(shape, np.float32)
+        out = gpu_run(pf, "gs", (u, v), 25)
+        assert np.array_equal(out[0], u) and np.array_equal(out[1], v)
+
+
+def test_ac_energy_decreases(pf):
+    w = synthetic.WORKLOADS["ac2d_128"]
+    x0 = synthetic.workload_init("ac2d_128")
+    g = pf.Grid(x0[0].shape, 1, w["h"]).set_model("ac", w["coeffs"], w["dt"])
+    g.write_fields(x0)
+    e_prev = g.energy()
+    assert abs(e_prev - oracle.energy(x0[0])) <= 1e-10 * abs(e_prev)
+    for _ in range(100):
+        g.step(10)
+        e = g.energy()
+        assert e <= e_prev + 1e-6 * abs(e_prev)
+        e_prev = e
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(37, 150), (9, 20, 70)])
+def test_reductions_match_oracle(pf, shape):
+    (phi,) = init_fields("ac", shape, seed=5)
+    g = pf.Grid(shape, 1, 0.7).set_model("ac", (0.9, 1.1), 0.01)
+    g.write_field(0, phi)
+    assert abs(g.mass() - oracle.mass(phi, 0.7)) <= 1e-12 * oracle.mass(np.abs(phi), 0.7)
+    e = oracle.energy(phi, 0.9, 1.1, 0.7)
+    assert abs(g.energy() - e) <= 1e-12 * abs(e)
+    g.close()
+
+
+def test_device_tensor_io(pf):
+    import torch
+    shape = (40, 72)
+    (x0,) = init_fields("ac", shape, seed=6)
+    g = pf.Grid(shape, 1).set_model("ac", COEFFS["ac"], DT["ac"])
+    g.write_field(0, torch.from_numpy(x0).cuda())
+    g.step(3)
+    t = g.read_field(0, device=True)
+    assert t.is_cuda
+    ref = oracle.run("ac", (x0,), COEFFS["ac"], DT["ac"], 3)
+    assert rel_linf((t.cpu().numpy(),), ref) <= 1e-6
+    g.close()
+
+
+def test_errors_are_reported(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((16, 16), 1)
+    with pytest.raises(PfError, match="no model"):
+        g.step(1)
+    with pytest.raises(PfError, match="stability"):
+        g.set_model("ac", (1.0, 1.0), 1.0)
+    with pytest.raises(PfError):
+        g.set_model("gs", (0.2, 0.1, 0.04, 0.06), 0.5)  # needs 2 fields
+    g.set_model("ac", (1.0, 1.0), 2.0, force=True)
+    g.write_field(0, np.full((16, 16), 1e30, np.float32))
+    g.step(5)
+    with pytest.raises(PfError, match="not finite"):
+        g.mass()
+    g.close()
