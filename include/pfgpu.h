@@ -145,6 +145,31 @@ int pf_synchronize(pf_grid_t g);
  * change after every pf_step (ping-pong). */
 int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane);
 
+/* ------------------------------------------------------- reduction without allocation */
+
+/* Mass or free energy (PF_REDUCE_*) of one caller-owned device field, written to a
+ * caller-owned device double, with no memory allocated by the call.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory, such as a host framework that has reserved the whole device for its own
+ * allocator, or a latency-critical loop that cannot take cudaMalloc's implicit
+ * device-wide synchronisation.
+ *   what     PF_REDUCE_MASS or PF_REDUCE_ENERGY (energy uses c1, c2; mass ignores them);
+ *   dim, n   as in pf_create_grid; pitch = floats per row (>= nx); the field is float32
+ *            [nz][ny][pitch] on the current device, x fastest; entries beyond nx unread;
+ *   h        grid spacing (> 0);
+ *   out_dev  device address of one double that receives the result;
+ *   stream   cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * Scratch: a fixed 4 KiB device array (512 FP64 partial sums) inside the library, which every
+ * GPU that loads the library holds until the process exits; the partial count does not grow
+ * with the grid, so every grid within the size limits below fits. The first call on a device
+ * looks up the array's device address (make that call before any stream capture). All calls
+ * share the array and each overwrites all of it before reading it; calls that overlap on the
+ * GPU race and may return wrong sums.
+ * Errors: PF_ERR_INVALID_ARG (NULL pointers, sides outside [1, 2^30], pitch < nx, more than
+ * 2^36 floats), PF_ERR_CUDA. Calls no cudaMalloc, cudaFree or other allocating routine. */
+int pf_reduce_noalloc(int what, int dim, const int64_t* n, int64_t pitch, const float* field,
+                      double h, double c1, double c2, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,9 @@ SIGNATURES = {
     "pf_synchronize": (ctypes.c_int, [_vp]),
     "pf_field_view": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), _c_int64_p,
                                      _c_int64_p]),
+    "pf_reduce_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_int64_p, ctypes.c_int64,
+                                         _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         _vp, _vp]),
 }
 
 
