@@ -33,6 +33,7 @@ METRIC = "lattice-site updates/s (GLUPS), % of measured HBM roofline"
 UNIT = "GLUPS"
 WORKLOAD = "gs3d_256"
 BYTES_PER_LUP = {"gs": 16.0, "ac": 8.0, "ch": 8.0}  # k = 1: read + write every field once
+TMA_TILES = {(64, 16), (128, 8), (128, 16)}
 
 
 def _peaks():
@@ -92,7 +93,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -268,7 +269,9 @@ def run_gpu(args, rank, world, local):
                      "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback",
                      "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "kernel": "fe3d (7-point GS, z-streaming)",
+                     "kernel": ("fe3d_tma_kernel (TMA-staged z-streaming, 7-point GS)"
+                                if tuple(tuning[:2]) in TMA_TILES else
+                                "fe3d_r1_kernel (general z-streaming, 7-point GS)"),
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms},
         "e2e": {"value": sites * S * args.steps * world / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(a.nbytes for a in x0)),
@@ -297,7 +300,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pf", choices=["pf", "reference"])
-    ap.add_argument("--substeps", type=int, default=100)
+    ap.add_argument("--substeps", type=int, default=250)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

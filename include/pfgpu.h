@@ -49,6 +49,9 @@ extern "C" {
 #define PF_ERR_UNSTABLE_DT (-4) /* dt beyond the linear forward-Euler stability bound */
 #define PF_ERR_NONFINITE (-5)   /* a reduction found NaN/Inf: the state blew up */
 #define PF_ERR_STATE (-6)       /* call out of order (no model set, no forward pass, ...) */
+#define PF_ERR_TIMEOUT (-7)     /* a bounded wait inside a kernel ran out; the kernel stopped
+                                   early and the state is invalid (reported by the next
+                                   synchronising call) */
 
 /* ---------------------------------------------------------------- models */
 #define PF_MODEL_AC 1 /* Allen-Cahn, 1 field, coeffs {c1, c2}          (Sec. 3, Model A) */
@@ -125,7 +128,8 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out);
  * k_steps (temporal-blocking depth, 2D only). 0 for any value = library default.
  * Unsupported combinations are rejected with PF_ERR_INVALID_ARG.
  * Supported: 2D tiles 64x16, 128x16, 32x32, 128x32; k in {1, 2, 4} (CH: {1, 2});
- * 3D tiles 32x16, 64x8 (k = 1). */
+ * 3D tiles 32x16, 64x8 (general kernel, every model and size) and 64x16, 128x8, 128x16
+ * (TMA-staged kernel: AC and GS with nx % tile_x == 0 and ny % tile_y == 0); k = 1. */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
 
 /* The tuning in effect (after defaults are resolved). */

@@ -20,6 +20,7 @@ PF_ERR_CUDA = -3
 PF_ERR_UNSTABLE_DT = -4
 PF_ERR_NONFINITE = -5
 PF_ERR_STATE = -6
+PF_ERR_TIMEOUT = -7
 
 PF_MODEL_AC = 1
 PF_MODEL_CH = 2

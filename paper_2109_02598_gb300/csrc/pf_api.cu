@@ -108,14 +108,40 @@ Geom grid_geom(const pf_grid_s* g) {
   return q;
 }
 
+// Turn the requested tuning (or the defaults) into the tuning in effect for the current
+// model and grid.
 int resolve_tuning(pf_grid_s* g) {
   if (g->dim == 2) {
-    if (g->tile < 0) g->tile = 1;  // 128 x 16
-    if (g->k <= 0) g->k = 1;
+    g->tile = g->req_tile >= 0 ? g->req_tile : 1;  // 128 x 16
+    g->k = g->req_k > 0 ? g->req_k : 1;
     if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
   } else {
-    if (g->tile < 0) g->tile = 0;  // 32 x 16
+    const bool tma_ok = g->model_set && fe3d_tma_supported(g->model, 0, grid_geom(g));
+    g->tile = g->req_tile >= 0 ? g->req_tile : (tma_ok ? kFirstTmaTile3D : 0);
+    if (g->tile >= kFirstTmaTile3D &&
+        !(g->model_set && fe3d_tma_supported(g->model, g->tile - kFirstTmaTile3D, grid_geom(g))))
+      g->tile = tma_ok ? kFirstTmaTile3D : 0;
     g->k = 1;
+  }
+  return PF_OK;
+}
+
+bool tile_supported(pf_grid_s* g, int tile, int k) {
+  if (g->dim == 2) return fe2d_supported(g->model, k);
+  if (k != 1) return false;
+  if (tile < kFirstTmaTile3D) return true;
+  return fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g));
+}
+
+// A kernel that gave up on a bounded wait leaves a flag; report it (and clear it).
+int check_device_error(pf_grid_s* g) {
+  int flag = 0;
+  PF_CUDA_TRY(cudaMemcpyAsync(&flag, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (flag != 0) {
+    PF_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    set_error("a kernel's bounded wait for a TMA copy ran out; the state is invalid");
+    return PF_ERR_TIMEOUT;
   }
   return PF_OK;
 }
@@ -130,6 +156,7 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst) {
   }
   const Geom q = grid_geom(g);
   if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, g->stream);
+  if (tile >= kFirstTmaTile3D) return launch_fe3d_tma(g, tile - kFirstTmaTile3D, src, dst);
   return launch_fe3d(g->model, tile, q, in, out, g->params, g->stream);
 }
 
@@ -184,6 +211,8 @@ int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stre
   if (e == cudaSuccess) e = cudaMemsetAsync(g->base, 0, sizeof(float) * elems * 2 * n_fields, g->stream);
   if (e == cudaSuccess) e = cudaMalloc(&g->red_partials, sizeof(double) * (kReduceBlocks + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&g->red_host, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {
     int rc = cuda_fail(e, "pf_create_grid allocation");
@@ -193,8 +222,8 @@ int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stre
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < n_fields; ++f) g->buf[b][f] = g->base + (b * n_fields + f) * elems;
   g->cur = 0;
-  g->tile = -1;
-  g->k = 0;
+  g->req_tile = -1;
+  g->req_k = 0;
   resolve_tuning(g);
   *out = g;
   return PF_OK;
@@ -207,6 +236,7 @@ void pf_destroy(pf_grid_t g) {
   if (g->base) cudaFree(g->base);
   if (g->red_partials) cudaFree(g->red_partials);
   if (g->red_host) cudaFreeHost(g->red_host);
+  if (g->d_err) cudaFree(g->d_err);
   g->magic = 0;
   delete g;
 }
@@ -260,7 +290,7 @@ int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device) {
                                 (size_t)g->ny * g->nz,
                                 dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 g->stream));
-  if (!dst_on_device) PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (!dst_on_device) return check_device_error(g);
   return PF_OK;
 }
 
@@ -300,7 +330,7 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out) {
                             g->red_partials, g->red_partials + kReduceBlocks, g->stream));
   PF_CUDA_TRY(cudaMemcpyAsync(g->red_host, g->red_partials + kReduceBlocks, sizeof(double),
                               cudaMemcpyDeviceToHost, g->stream));
-  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (int rc = check_device_error(g)) return rc;
   *out = *g->red_host;
   if (!std::isfinite(*out)) {
     set_error("reduction is not finite (%g): the state has blown up", *out);
@@ -328,8 +358,12 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
   }
-  g->tile = tile;
-  g->k = k_steps;
+  if (g->dim == 3 && tile >= kFirstTmaTile3D &&
+      !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g))))
+    return invalid("3D tile %dx%d needs an AC/GS model and nx %% %d == 0, ny %% %d == 0",
+                   tile_x, tile_y, tile_x, tile_y);
+  g->req_tile = tile;
+  g->req_k = k_steps;
   return resolve_tuning(g);
 }
 
@@ -364,8 +398,7 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   for (int t = 0; t < ntiles && rc == PF_OK; ++t) {
     for (int ki = 0; ki < 3 && rc == PF_OK; ++ki) {
       const int k = ks[ki];
-      if (g->dim == 3 && k > 1) continue;
-      if (g->dim == 2 && !fe2d_supported(g->model, k)) continue;
+      if (!tile_supported(g, t, k)) continue;
       cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
       for (int i = 0; i < probe_launches && e == cudaSuccess; ++i)
@@ -389,15 +422,15 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != PF_OK) return rc;
-  g->tile = best_tile;
-  g->k = best_k;
+  g->req_tile = best_tile;
+  g->req_k = best_k;
+  resolve_tuning(g);
   return pf_get_tuning(g, tile_x, tile_y, k_steps);
 }
 
 int pf_synchronize(pf_grid_t g) {
   if (int rc = check_grid(g)) return rc;
-  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-  return PF_OK;
+  return check_device_error(g);
 }
 
 int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane) {

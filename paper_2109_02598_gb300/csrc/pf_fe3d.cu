@@ -220,7 +220,7 @@ cudaError_t launch3_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
 }  // namespace
 
 void tile3d_shape(int tile_id, int* tx, int* ty) {
-  static const int s[kNumTiles3D][2] = {{32, 16}, {64, 8}};
+  static const int s[kNumTiles3D][2] = {{32, 16}, {64, 8}, {64, 16}, {128, 8}, {128, 16}};
   *tx = s[tile_id][0];
   *ty = s[tile_id][1];
 }
@@ -236,7 +236,7 @@ int tile3d_id(int tx, int ty) {
 
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
                         const ModelParams& m, cudaStream_t s) {
-  if (tile_id < 0 || tile_id >= kNumTiles3D) return cudaErrorInvalidValue;
+  if (tile_id < 0 || tile_id >= kFirstTmaTile3D) return cudaErrorInvalidValue;
   switch (model) {
     case PF_MODEL_AC: return launch3_tile<PF_MODEL_AC>(tile_id, g, in, out, m, s);
     case PF_MODEL_CH: return launch3_tile<PF_MODEL_CH>(tile_id, g, in, out, m, s);

@@ -3,9 +3,25 @@
 // device layout, the model coefficients and the kernel tuning.
 #pragma once
 
+#include <cuda.h>
+
 #include "pf_internal.h"
 
 namespace pf {
+
+// TMA descriptors of one ping-pong buffer for the 3D kernel: the tile interior box, the
+// one-row halo box and the 4-wide column box, per field.
+struct Tma3dMaps {
+  CUtensorMap inner[PF_MAX_FIELDS];
+  CUtensorMap row[PF_MAX_FIELDS];
+  CUtensorMap side[PF_MAX_FIELDS];
+};
+
+struct TmaCache {
+  int tile = -1;  // TMA tile the maps were encoded for
+  bool valid[2] = {false, false};
+  Tma3dMaps maps[2];
+};
 
 constexpr uint32_t kGridMagic = 0x50464744u;  // "PFGD"
 
@@ -44,11 +60,15 @@ struct pf_grid_s {
   double dt = 0;
   int model_set = 0;
   pf::ModelParams params{};
-  int tile = -1;  // kernel tile id (2D or 3D table)
-  int k = 0;      // temporal-blocking depth
+  int tile = -1;      // kernel tile id in effect (2D or 3D table)
+  int k = 0;          // temporal-blocking depth in effect
+  int req_tile = -1;  // tile asked for by pf_set_tuning (-1 = library default)
+  int req_k = 0;      // depth asked for (0 = library default)
   double* red_partials = nullptr;  // kReduceBlocks partials + 1 result
   double* red_host = nullptr;      // pinned
   pf::AdjointState adj;
+  pf::TmaCache tma;
+  int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
 };
 
 namespace pf {
@@ -58,4 +78,11 @@ int check_grid(pf_grid_s* g);
 Geom grid_geom(const pf_grid_s* g);
 ModelParams make_params(int model, const double* c, double dt, double h);
 cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst);
+
+// ---- 3D TMA kernel (AC, GS): TMA tile ids 0 = 64x16, 1 = 128x8, 2 = 128x16
+constexpr int kNumTmaTiles3D = 3;
+void tma3d_tile_shape(int tma_tile, int* tx, int* ty);
+bool fe3d_tma_supported(int model, int tma_tile, const Geom& g);
+cudaError_t tma3d_maps(pf_grid_s* g, int tma_tile, int buf);
+cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst);
 }  // namespace pf

@@ -48,9 +48,11 @@ bool fe2d_supported(int model, int k);
 cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs in,
                         FieldOut out, const ModelParams& m, cudaStream_t s);
 
-// ---- 3D z-streaming forward-Euler kernel (k = 1) --------------------------------
-// Tile ids: 0 = 32x16, 1 = 64x8.
-constexpr int kNumTiles3D = 2;
+// ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
+// Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
+//           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0).
+constexpr int kNumTiles3D = 5;
+constexpr int kFirstTmaTile3D = 2;
 void tile3d_shape(int tile_id, int* tx, int* ty);
 int tile3d_id(int tx, int ty);
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,

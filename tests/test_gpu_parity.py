@@ -66,7 +66,9 @@ def rel_l2(got, ref):
 
 
 SHAPES_2D = [(37, 150), (64, 64), (5, 7), (1, 9), (130, 33)]
-SHAPES_3D = [(9, 20, 70), (4, 4, 4), (3, 17, 33), (17, 5, 130)]
+# the last three take the TMA-staged kernel for AC/GS (nx % 64 == 0, ny % 16 == 0)
+SHAPES_3D = [(9, 20, 70), (4, 4, 4), (3, 17, 33), (17, 5, 130), (5, 48, 192), (1, 16, 64),
+             (2, 32, 128)]
 
 
 @pytest.mark.parametrize("model", ["ac", "ch", "gs"])
@@ -102,12 +104,39 @@ def test_tiles_and_temporal_blocking_are_bitwise_identical(pf, model):
     got = gpu_run(pf, model, x0, 12, tuning=(128, 16, 2 if model == "ch" else 4))
     for a, b in zip(base, got):
         assert np.array_equal(a, b)
-    # 3D tiles
+    # 3D tiles: general kernel on a ragged grid
     y0 = init_fields(model, (12, 19, 70), seed=3)
     b3 = gpu_run(pf, model, y0, 5, tuning=(32, 16, 1))
     g3 = gpu_run(pf, model, y0, 5, tuning=(64, 8, 1))
     for a, b in zip(b3, g3):
         assert np.array_equal(a, b)
+    # 3D tiles on a grid the TMA kernel accepts: general and TMA kernels agree bitwise
+    y1 = init_fields(model, (12, 32, 128), seed=4)
+    b3 = gpu_run(pf, model, y1, 7, tuning=(32, 16, 1))
+    tiles = [(64, 8)] + ([] if model == "ch" else [(64, 16), (128, 8), (128, 16)])
+    for t in tiles:
+        got = gpu_run(pf, model, y1, 7, tuning=(t[0], t[1], 1))
+        for a, b in zip(b3, got):
+            assert np.array_equal(a, b), t
+
+
+def test_tma_tile_rejected_when_grid_does_not_divide(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((8, 20, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
+    with pytest.raises(PfError, match="ny"):
+        g.set_tuning(64, 16, 1)  # ny = 20 is not a multiple of 16
+    g.set_tuning(64, 8, 1)  # the general kernel takes any size
+    g.close()
+    h = pf.Grid((8, 32, 64), 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    with pytest.raises(PfError):
+        h.set_tuning(64, 16, 1)  # no TMA kernel for Model B
+    h.close()
+
+
+def test_default_tuning_picks_tma_for_the_3d_workload(pf):
+    g = pf.Grid((256, 256, 256), 2).set_model("gs", COEFFS["gs"], DT["gs"])
+    assert g.tuning == (64, 16, 1)
+    g.close()
 
 
 # ---------------------------------------------------------------- workload configurations
