@@ -116,11 +116,18 @@ int resolve_tuning(pf_grid_s* g) {
     g->k = g->req_k > 0 ? g->req_k : 1;
     if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
   } else {
-    const bool tma_ok = g->model_set && fe3d_tma_supported(g->model, 0, grid_geom(g));
-    g->tile = g->req_tile >= 0 ? g->req_tile : (tma_ok ? kFirstTmaTile3D : 0);
+    // default: the fastest TMA tile that divides the grid (measured on GS 256^3:
+    // 128x16 > 64x16 = 128x8), else the general kernel
+    int def = 0;
+    if (g->model_set) {
+      static const int pref[3] = {2, 0, 1};  // TMA tile ids 128x16, 64x16, 128x8
+      for (int i = 0; i < 3 && def == 0; ++i)
+        if (fe3d_tma_supported(g->model, pref[i], grid_geom(g))) def = kFirstTmaTile3D + pref[i];
+    }
+    g->tile = g->req_tile >= 0 ? g->req_tile : def;
     if (g->tile >= kFirstTmaTile3D &&
         !(g->model_set && fe3d_tma_supported(g->model, g->tile - kFirstTmaTile3D, grid_geom(g))))
-      g->tile = tma_ok ? kFirstTmaTile3D : 0;
+      g->tile = def;
     g->k = 1;
   }
   return PF_OK;

@@ -1,10 +1,15 @@
 // 3D forward-Euler step for the radius-1 models (Allen-Cahn, Gray-Scott) with TMA plane
 // staging (Sec. 2.4.1 solver, Sec. 2.2.2 7-point Laplacian, Sec. 3 / Sec. 1 models).
 //
-// Work: the grid is cut into TX x TY columns in the xy plane; a column has nz planes, and
-// the (column, plane) tasks are split evenly over a persistent grid of CTAs, so each CTA
-// streams one or two contiguous z-ranges.  Streaming a z-range keeps the z-neighbours in
-// registers: plane z's values become the "below" values of plane z+1.
+// Work: the grid is cut into TX x TY columns in the xy plane and every column into
+// nchunks z-chunks; one CTA streams one (column, chunk) item at a time, all columns of a
+// chunk side by side, so the halo rows and columns a tile shares with its neighbours are
+// fetched from HBM once and served from L2 to the second reader.  Even chunks stream up
+// in z and odd chunks down, so the plane two chunks share at their boundary is read by
+// both CTAs at the same moment too.  Streaming keeps the z-neighbours in registers: the
+// values of one plane become the "previous" values of the next (the 7-point sum pairs the
+// two z-neighbours in one addition, which is commutative, so the direction does not
+// change the result).
 //
 // Staging: per plane and field, five TMA boxes land in a ring of NS shared-memory stages:
 // the TX x TY interior, the rows above and below (wrapped in y), and 4-wide column boxes
@@ -45,7 +50,7 @@ struct CfgT {
 template <int MODEL, int TX, int TY, int NS>
 __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
     fe3d_tma_kernel(const __grid_constant__ Tma3dMaps maps, FieldOut out, Geom g,
-                    ModelParams m, int tiles_x, long long total_tasks, int* err_flag) {
+                    ModelParams m, int tiles_x, int nchunks, int chunk_len, int* err_flag) {
   using C = CfgT<MODEL, TX, TY, NS>;
   constexpr int NF = C::NF;
   constexpr int LX = C::LX;
@@ -63,10 +68,6 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
     mbar_fence_init();
   }
   __syncthreads();
-
-  const long long G = gridDim.x;
-  const long long t_begin = total_tasks * blockIdx.x / G;
-  const long long t_end = total_tasks * (blockIdx.x + 1) / G;
 
   uint32_t q_base = 0;     // sequence number of the next plane load of this CTA
   uint32_t q_issued = 0;   // (thread 0) loads issued so far
@@ -97,24 +98,29 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
     return mbar_wait_bounded(&bars[q % NS], (q / NS) & 1u, kWaitBudgetCycles);
   };
 
-  const int nz = g.nz;
-  for (long long task = t_begin; task < t_end;) {
-    const int col = (int)(task / nz);
-    const int z0 = (int)(task % nz);
-    const int z1 = (int)min((long long)nz, (long long)z0 + (t_end - task));
-    task += z1 - z0;
+  const int ncols = tiles_x * (g.ny / TY);
+  const int nitems = ncols * nchunks;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int col = item % ncols;
+    const int chunk = item / ncols;
+    const int zlo = chunk * chunk_len;
+    const int zhi = min(g.nz, zlo + chunk_len);
+    if (zlo >= zhi) continue;  // uniform over the CTA
+    const int dir = (chunk & 1) ? -1 : 1;
+    const int n = zhi - zlo;
+    const int zfirst = dir > 0 ? zlo : zhi - 1;
     const int x0 = (col % tiles_x) * TX;
     const int y0 = (col / tiles_x) * TY;
-    const int np = z1 - z0 + 2;  // planes z0-1 .. z1
+    const int np = n + 2;  // planes zfirst - dir, zfirst, ..., zfirst + n*dir
 
     if (__syncthreads_or(err)) break;
     if (tid == 0) {
       fence_proxy_async_smem();
       const int n0 = np < NS ? np : NS;
-      for (int i = 0; i < n0; ++i) issue(q_base + i, x0, y0, z0 - 1 + i);
+      for (int i = 0; i < n0; ++i) issue(q_base + i, x0, y0, zfirst + (i - 1) * dir);
       q_issued = q_base + n0;
     }
-    // prologue: centre values of planes z0-1 and z0
+    // prologue: centre values of the planes before and at zfirst
     float4 zm[NF], c[NF];
     err = !wait(q_base);
     if (!err) {
@@ -133,15 +139,15 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
 
     const int gy = y0 + ty;
     const int gx = x0 + 4 * tx4;
-    for (int z = z0; z < z1; ++z) {
-      const int i = z - z0;  // plane z has index i + 1 in this segment
+    for (int i = 0; i < n; ++i) {
+      const int z = zfirst + i * dir;  // output plane; its load index is i + 1
       if (__syncthreads_or(err)) break;
       if (tid == 0 && i + NS < np) {
         fence_proxy_async_smem();
-        issue(q_base + i + NS, x0, y0, z0 - 1 + i + NS);
+        issue(q_base + i + NS, x0, y0, zfirst + (i + NS - 1) * dir);
         q_issued = q_base + i + NS + 1;
       }
-      err = !wait(q_base + i + 2);  // plane z+1
+      err = !wait(q_base + i + 2);  // the plane after z in streaming order
       err = __any_sync(0xffffffffu, err);  // warp-uniform before the shuffles below
       if (err) continue;
       const float* sz = stage_ptr(q_base + i + 1);
@@ -214,11 +220,18 @@ cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out) {
   const Geom g = grid_geom(gr);
   const int tiles_x = g.nx / TX;
   const int tiles_y = g.ny / TY;
-  const long long total = (long long)tiles_x * tiles_y * g.nz;
-  long long grid = (long long)sms * occ;
-  if (grid > total) grid = total;
-  kern<<<(unsigned)grid, C::NT, C::SMEM, gr->stream>>>(maps, out, g, gr->params, tiles_x, total,
-                                                       gr->d_err);
+  const long long ncols = (long long)tiles_x * tiles_y;
+  const long long slots = (long long)sms * occ;
+  // as many z-chunks as keep every column of a chunk resident at once, chunks >= 4 planes
+  long long nchunks = slots / ncols;
+  if (nchunks > g.nz / 4) nchunks = g.nz / 4;
+  if (nchunks < 1) nchunks = 1;
+  const int chunk_len = (int)((g.nz + nchunks - 1) / nchunks);
+  nchunks = (g.nz + chunk_len - 1) / chunk_len;
+  const long long items = ncols * nchunks;
+  const long long grid = items < slots ? items : slots;
+  kern<<<(unsigned)grid, C::NT, C::SMEM, gr->stream>>>(maps, out, g, gr->params, tiles_x,
+                                                       (int)nchunks, chunk_len, gr->d_err);
   return cudaGetLastError();
 }
 
@@ -247,7 +260,7 @@ cudaError_t launch_fe3d_tma(pf_grid_s* gr, int tma_tile, int src, int dst) {
     switch (tma_tile) {
       case 0: return launch_tma<PF_MODEL_GS, 64, 16, 5>(gr, maps, out);
       case 1: return launch_tma<PF_MODEL_GS, 128, 8, 5>(gr, maps, out);
-      case 2: return launch_tma<PF_MODEL_GS, 128, 16, 4>(gr, maps, out);
+      case 2: return launch_tma<PF_MODEL_GS, 128, 16, 5>(gr, maps, out);
     }
   } else if (gr->model == PF_MODEL_AC) {
     switch (tma_tile) {
@@ -298,7 +311,7 @@ cudaError_t tma3d_maps(pf_grid_s* gr, int tma_tile, int buf) {
     if (r == CUDA_SUCCESS)
       r = encode(&mp.side[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box_side,
                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
   tc.valid[buf] = true;

@@ -135,6 +135,9 @@ def test_tma_tile_rejected_when_grid_does_not_divide(pf):
 
 def test_default_tuning_picks_tma_for_the_3d_workload(pf):
     g = pf.Grid((256, 256, 256), 2).set_model("gs", COEFFS["gs"], DT["gs"])
+    assert g.tuning == (128, 16, 1)
+    g.close()
+    g = pf.Grid((8, 48, 192), 2).set_model("gs", COEFFS["gs"], DT["gs"])
     assert g.tuning == (64, 16, 1)
     g.close()
 
