@@ -149,6 +149,52 @@ int pf_synchronize(pf_grid_t g);
  * change after every pf_step (ping-pong). */
 int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane);
 
+/* ----------------------------------------------------------------- batched runner */
+
+/* One independent periodic 2D Gray-Scott instance of a batch: its size and coefficients. */
+typedef struct {
+  int64_t nx, ny;       /* grid sides, each in [1, 2^20] */
+  double Du, Dv, F, k;  /* Gray-Scott coefficients (Sec. 1 names the model; standard form) */
+} pf_gs2d_spec;
+
+/* Create a batch of n independent 2D Gray-Scott grids of uneven sizes and coefficients
+ * that advance together: the GPU form of the paper's driver that runs a list of models
+ * (Sec. 2.4, the "simultaneous-configs" example). All instances share dt and h.
+ * Allocates one device buffer holding every instance twice (ping-pong), zero-filled.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_UNSTABLE_DT (any instance), PF_ERR_OOM, PF_ERR_CUDA. */
+int pf_batch_create(int n, const pf_gs2d_spec* specs, double dt, double h, void* stream,
+                    pf_batch_t* out);
+
+/* Release the batch (synchronizes its stream). NULL is a no-op. */
+void pf_batch_destroy(pf_batch_t b);
+
+/* Copy field `field` (0 = u, 1 = v) of instance `inst` in / out; dense float32 [ny][nx].
+ * Host transfers complete before return; device transfers are enqueued on the stream. */
+int pf_batch_write_field(pf_batch_t b, int inst, int field, const float* src, int on_device);
+int pf_batch_read_field(pf_batch_t b, int inst, int field, float* dst, int on_device);
+
+/* Tile (one of the 2D tiles of pf_set_tuning) and temporal depth k in {1, 2, 4} for every
+ * instance; 0 keeps the current value. */
+int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps);
+int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps);
+
+/* Time every (tile, k) on this batch (probe launches read the current state and write the
+ * spare copy, so the state is unchanged) and keep the fastest. */
+int pf_batch_autotune(pf_batch_t b, int probe_launches, int* tile_x, int* tile_y,
+                      int* k_steps);
+
+/* Advance every instance by n_steps forward-Euler steps in one CUDA-graph launch on the
+ * batch's stream (one kernel node per k steps, each over all instances' tiles). The graph
+ * is recorded on first use for a given (n_steps, tuning, starting buffer) and replayed
+ * afterwards. Each instance's result is bitwise the same as pf_step on a single grid. */
+int pf_batch_run(pf_batch_t b, int64_t n_steps);
+
+/* Block until the batch's stream is idle. */
+int pf_batch_synchronize(pf_batch_t b);
+
+/* Total lattice sites of all instances, and bytes of one state copy (with padding). */
+int pf_batch_info(pf_batch_t b, int64_t* sites, int64_t* bytes_per_copy);
+
 /* ------------------------------------------------------- reduction without allocation */
 
 /* Mass or free energy (PF_REDUCE_*) of one caller-owned device field, written to a

@@ -6,5 +6,6 @@ The compute path is libpfgpu.so (hand-written CUDA for sm_103a behind the C ABI 
 """
 from ._lib import PfError, load  # noqa: F401
 from .grid import Grid  # noqa: F401
+from .batch import Batch  # noqa: F401
 
-__all__ = ["Grid", "PfError", "load"]
+__all__ = ["Batch", "Grid", "PfError", "load"]

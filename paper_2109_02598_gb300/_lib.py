@@ -31,6 +31,12 @@ MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2}
 PF_REDUCE_MASS = 1
 PF_REDUCE_ENERGY = 2
 
+class GS2DSpec(ctypes.Structure):
+    """pf_gs2d_spec: one batched 2D Gray-Scott instance."""
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("Du", ctypes.c_double),
+                ("Dv", ctypes.c_double), ("F", ctypes.c_double), ("k", ctypes.c_double)]
+
+
 _c_int64_p = ctypes.POINTER(ctypes.c_int64)
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -55,6 +61,17 @@ SIGNATURES = {
     "pf_synchronize": (ctypes.c_int, [_vp]),
     "pf_field_view": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), _c_int64_p,
                                      _c_int64_p]),
+    "pf_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(GS2DSpec), ctypes.c_double,
+                                       ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+    "pf_batch_destroy": (None, [_vp]),
+    "pf_batch_write_field": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_batch_read_field": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pf_batch_get_tuning": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
+    "pf_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p]),
+    "pf_batch_run": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pf_batch_synchronize": (ctypes.c_int, [_vp]),
+    "pf_batch_info": (ctypes.c_int, [_vp, _c_int64_p, _c_int64_p]),
     "pf_reduce_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_int64_p, ctypes.c_int64,
                                          _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _vp, _vp]),

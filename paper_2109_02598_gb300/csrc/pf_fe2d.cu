@@ -27,6 +27,52 @@ __global__ void __launch_bounds__(kNT2) fe2d_kernel(FieldPtrs in, FieldOut out, 
   fe2d_tile<MODEL, K, TX, TY>(in, out, g.nx, g.ny, g.pitch, x0, y0, m, sm);
 }
 
+// Batched Gray-Scott: CTA b runs the same tile body on work-list entry b.
+template <int K, int TX, int TY>
+__global__ void __launch_bounds__(kNT2) batch_gs2d_kernel(const BatchInst* __restrict__ insts,
+                                                          const BatchTile* __restrict__ tiles,
+                                                          const float* in_base, float* out_base) {
+  extern __shared__ __align__(16) float sm[];
+  const BatchTile t = tiles[blockIdx.x];
+  const BatchInst I = insts[t.inst];
+  const int64_t plane = I.pitch * I.ny;
+  FieldPtrs in{};
+  FieldOut out{};
+  in.f[0] = in_base + I.off;
+  in.f[1] = in_base + I.off + plane;
+  out.f[0] = out_base + I.off;
+  out.f[1] = out_base + I.off + plane;
+  fe2d_tile<PF_MODEL_GS, K, TX, TY>(in, out, I.nx, I.ny, I.pitch, t.x0, t.y0, I.m, sm);
+}
+
+template <int K, int TX, int TY>
+cudaError_t launch_batch_one(const BatchInst* d_insts, const BatchTile* d_tiles, int ntiles,
+                             const float* in_base, float* out_base, cudaStream_t s) {
+  using C = Cfg2<PF_MODEL_GS, K, TX, TY>;
+  const size_t smem = sizeof(float) * C::SMEM_FLOATS;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(batch_gs2d_kernel<K, TX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  batch_gs2d_kernel<K, TX, TY><<<ntiles, kNT2, smem, s>>>(d_insts, d_tiles, in_base, out_base);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_batch_tile(int tile_id, const BatchInst* d_insts, const BatchTile* d_tiles,
+                              int ntiles, const float* in_base, float* out_base, cudaStream_t s) {
+  switch (tile_id) {
+    case 0: return launch_batch_one<K, 64, 16>(d_insts, d_tiles, ntiles, in_base, out_base, s);
+    case 1: return launch_batch_one<K, 128, 16>(d_insts, d_tiles, ntiles, in_base, out_base, s);
+    case 2: return launch_batch_one<K, 32, 32>(d_insts, d_tiles, ntiles, in_base, out_base, s);
+    case 3: return launch_batch_one<K, 128, 32>(d_insts, d_tiles, ntiles, in_base, out_base, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int MODEL, int K, int TX, int TY>
 cudaError_t launch_one(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
                        cudaStream_t s) {
@@ -57,7 +103,41 @@ cudaError_t launch_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
   return cudaErrorInvalidValue;
 }
 
+template <int K, int TX, int TY>
+cudaError_t prepare_one() {
+  using C = Cfg2<PF_MODEL_GS, K, TX, TY>;
+  return cudaFuncSetAttribute(batch_gs2d_kernel<K, TX, TY>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float) * C::SMEM_FLOATS));
+}
+
+template <int K>
+cudaError_t prepare_k() {
+  cudaError_t e = prepare_one<K, 64, 16>();
+  if (e == cudaSuccess) e = prepare_one<K, 128, 16>();
+  if (e == cudaSuccess) e = prepare_one<K, 32, 32>();
+  if (e == cudaSuccess) e = prepare_one<K, 128, 32>();
+  return e;
+}
+
 }  // namespace
+
+cudaError_t prepare_batch_gs2d() {
+  cudaError_t e = prepare_k<1>();
+  if (e == cudaSuccess) e = prepare_k<2>();
+  if (e == cudaSuccess) e = prepare_k<4>();
+  return e;
+}
+
+cudaError_t launch_batch_gs2d(int tile_id, int k, const BatchInst* d_insts,
+                              const BatchTile* d_tiles, int ntiles, const float* in_base,
+                              float* out_base, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (k == 1) return launch_batch_tile<1>(tile_id, d_insts, d_tiles, ntiles, in_base, out_base, s);
+  if (k == 2) return launch_batch_tile<2>(tile_id, d_insts, d_tiles, ntiles, in_base, out_base, s);
+  if (k == 4) return launch_batch_tile<4>(tile_id, d_insts, d_tiles, ntiles, in_base, out_base, s);
+  return cudaErrorInvalidValue;
+}
 
 void tile2d_shape(int tile_id, int* tx, int* ty) {
   static const int s[kNumTiles2D][2] = {{64, 16}, {128, 16}, {32, 32}, {128, 32}};

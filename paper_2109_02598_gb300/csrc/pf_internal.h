@@ -58,6 +58,22 @@ int tile3d_id(int tx, int ty);
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
                         const ModelParams& m, cudaStream_t s);
 
+// ---- batched 2D Gray-Scott (many independent grids, one launch per k steps) -------
+// Instance i: fields at buffer base + off (u) and base + off + pitch * ny (v).
+struct BatchInst {
+  int nx, ny;
+  int64_t pitch;  // floats per row
+  int64_t off;    // floats from the buffer base to field u
+  ModelParams m;  // per-instance coefficients
+};
+struct BatchTile {
+  int inst, x0, y0;
+};
+cudaError_t prepare_batch_gs2d();  // set kernel attributes (call before any capture)
+cudaError_t launch_batch_gs2d(int tile_id, int k, const BatchInst* d_insts,
+                              const BatchTile* d_tiles, int ntiles, const float* in_base,
+                              float* out_base, cudaStream_t s);
+
 // ---- reductions -------------------------------------------------------------------
 // Writes one double to d_out. d_partials must hold kReduceBlocks doubles.
 constexpr int kReduceBlocks = 512;

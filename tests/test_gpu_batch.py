@@ -1,0 +1,107 @@
+"""Batched 2D Gray-Scott through the C ABI: every instance against the FP64 oracle, and
+bitwise against the same grid stepped alone (the batch runs the same tile body)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+DT, DU, DV = 0.5, 0.2, 0.1
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02598_gb300.build import build
+    build()
+    import paper_2109_02598_gb300 as pf
+    return pf
+
+
+def make_specs(shapes, seed=7):
+    F = synthetic.uniform(seed, 20, len(shapes), 0.02, 0.06)
+    k = synthetic.uniform(seed, 21, len(shapes), 0.045, 0.07)
+    return [dict(ny=s[0], nx=s[1], Du=DU, Dv=DV, F=float(f), k=float(kk))
+            for s, f, kk in zip(shapes, F, k)]
+
+
+SHAPES = [(64, 64), (97, 130), (5, 7), (200, 33), (1, 9), (128, 256), (70, 70), (33, 300)]
+
+
+def init(shape, i):
+    return synthetic.gray_scott_init(shape, seed=500 + i, n_seeds=max(1, shape[0] * shape[1] // 1500),
+                                     side=4, noise=0.05)
+
+
+def test_batch_matches_oracle_and_single_grids(pf):
+    specs = make_specs(SHAPES)
+    b = pf.Batch(specs, DT)
+    x0 = [init(s, i) for i, s in enumerate(SHAPES)]
+    for i, (u, v) in enumerate(x0):
+        b.write(i, 0, u).write(i, 1, v)
+    n = 13
+    b.run(n)
+    for i, (s, sp) in enumerate(zip(SHAPES, specs)):
+        coeffs = (DU, DV, sp["F"], sp["k"])
+        got = (b.read(i, 0), b.read(i, 1))
+        ref = oracle.run("gs", x0[i], coeffs, DT, n)
+        err = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(got, ref))
+        assert err <= 2e-5 * max(np.abs(r).max() for r in ref), (i, s)
+        g = pf.Grid(s, 2).set_model("gs", coeffs, DT)
+        g.write_fields(x0[i]).step(n)
+        alone = g.read_fields()
+        g.close()
+        assert np.array_equal(got[0], alone[0]) and np.array_equal(got[1], alone[1]), (i, s)
+    b.close()
+
+
+def test_batch_tunings_replays_and_autotune_agree_bitwise(pf):
+    specs = make_specs(SHAPES, seed=8)
+    x0 = [init(s, i) for i, s in enumerate(SHAPES)]
+
+    def run(tuning, chunks):
+        b = pf.Batch(specs, DT)
+        for i, (u, v) in enumerate(x0):
+            b.write(i, 0, u).write(i, 1, v)
+        if tuning == "auto":
+            b.autotune(2)
+        else:
+            b.set_tuning(*tuning)
+        for c in chunks:
+            b.run(c)
+        out = [(b.read(i, 0), b.read(i, 1)) for i in range(len(SHAPES))]
+        b.close()
+        return out
+
+    base = run((64, 16, 1), [12])
+    for tuning, chunks in [((128, 16, 2), [12]), ((32, 32, 4), [5, 7]), ((128, 32, 4), [6, 6]),
+                           ((64, 16, 2), [3, 3, 3, 3]), ("auto", [12])]:
+        got = run(tuning, chunks)
+        for (a0, a1), (b0, b1) in zip(base, got):
+            assert np.array_equal(a0, b0) and np.array_equal(a1, b1), tuning
+
+
+def test_batch_workload_recipe_runs(pf):
+    specs = synthetic.batch_instances(n=64, seed=4)
+    full = [dict(n=s["n"], Du=DU, Dv=DV, F=s["F"], k=s["k"]) for s in specs]
+    b = pf.Batch(full, DT)
+    for i, s in enumerate(specs):
+        u, v = synthetic.batch_instance_init(s["n"], i)
+        b.write(i, 0, u).write(i, 1, v)
+    b.run(200)
+    for i in (0, 17, 63):
+        u, v = b.read(i, 0), b.read(i, 1)
+        assert np.isfinite(u).all() and np.isfinite(v).all()
+        assert u.min() >= -0.01 and u.max() <= 1.01
+    assert b.sites == sum(s["n"] ** 2 for s in specs)
+    b.close()
+
+
+def test_batch_rejects_unstable_dt(pf):
+    from paper_2109_02598_gb300 import PfError
+    with pytest.raises(PfError, match="stability"):
+        pf.Batch(make_specs([(16, 16)]), 5.0)
