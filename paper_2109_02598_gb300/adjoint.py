@@ -1,0 +1,89 @@
+"""Gradients of a final-state loss through the forward-Euler Gray-Scott time loop.
+
+``GrayScottAdjoint`` is a ``torch.autograd.Function`` over the library's adjoint entry points
+(``pf_adj_forward`` / ``pf_adj_backward`` in include/pfgpu.h): the forward pass advances
+(u0, v0) by n steps with sqrt(N) checkpointing, the backward pass runs the hand-written
+adjoint kernel and returns dL/du0, dL/dv0 and dL/d(Du, Dv, F, k).  Argument marshalling
+only; all arithmetic runs in libpfgpu's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import check
+from .grid import Grid, _torch
+
+
+def adjoint_forward(grid: Grid, n_steps: int, ckpt_interval: int = 0):
+    """pf_adj_forward on ``grid`` (Gray-Scott model and fields already set)."""
+    check(grid._lib.pf_adj_forward(grid.handle, int(n_steps), int(ckpt_interval)))
+
+
+def adjoint_backward(grid: Grid, dLdu_N, dLdv_N):
+    """pf_adj_backward with CUDA tensors; returns (dL/du0, dL/dv0, [dL/dDu, dDv, dF, dk])."""
+    torch = _torch()
+    gu = dLdu_N.detach().to(torch.float32).contiguous()
+    gv = dLdv_N.detach().to(torch.float32).contiguous()
+    du0 = torch.empty_like(gu)
+    dv0 = torch.empty_like(gv)
+    dth = (ctypes.c_double * 4)()
+    check(grid._lib.pf_adj_backward(grid.handle, ctypes.c_void_p(gu.data_ptr()),
+                                    ctypes.c_void_p(gv.data_ptr()), 1,
+                                    ctypes.c_void_p(du0.data_ptr()),
+                                    ctypes.c_void_p(dv0.data_ptr()), dth))
+    return du0, dv0, list(dth)
+
+
+class GrayScottAdjoint:
+    """``apply(u0, v0, theta, n_steps, dt, h=1.0, ckpt_interval=0) -> (u_N, v_N)``.
+
+    ``u0``, ``v0``: CUDA float32 tensors (ny, nx); ``theta``: tensor (Du, Dv, F, k).
+    Gradients flow to u0, v0 and theta.
+    """
+
+    _fn = None
+
+    @classmethod
+    def _function(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, u0, v0, theta, n_steps, dt, h, ckpt_interval):
+                    grid = Grid(tuple(u0.shape), 2, h)
+                    grid.set_model("gs", [float(t) for t in theta.detach().cpu().tolist()], dt)
+                    grid.write_field(0, u0)
+                    grid.write_field(1, v0)
+                    adjoint_forward(grid, n_steps, ckpt_interval)
+                    uN = grid.read_field(0, device=True)
+                    vN = grid.read_field(1, device=True)
+                    grid.synchronize()
+                    ctx.grid = grid
+                    ctx.theta_meta = (theta.dtype, theta.device)
+                    return uN, vN
+
+                @staticmethod
+                def backward(ctx, gu, gv):
+                    torch = _torch()
+                    grid = ctx.grid
+                    if gu is None:
+                        gu = torch.zeros(grid.shape, device="cuda")
+                    if gv is None:
+                        gv = torch.zeros(grid.shape, device="cuda")
+                    du0, dv0, dth = adjoint_backward(grid, gu, gv)
+                    dtype, device = ctx.theta_meta
+                    grid.close()
+                    ctx.grid = None
+                    return (du0, dv0, torch.tensor(dth, dtype=dtype, device=device),
+                            None, None, None, None)
+
+            cls._fn = _Fn
+        return cls._fn
+
+    @classmethod
+    def apply(cls, u0, v0, theta, n_steps: int, dt: float, h: float = 1.0,
+              ckpt_interval: int = 0):
+        return cls._function().apply(u0, v0, theta, int(n_steps), float(dt), float(h),
+                                     int(ckpt_interval))

@@ -1,7 +1,153 @@
-// Gray-Scott discrete adjoint with sqrt(N) checkpointing (filled in below).
+// Discrete adjoint of the forward-Euler Gray-Scott time loop with sqrt(N) checkpointing.
+//
+// Forward map (Sec. 2.4.1 solver; Gray-Scott in its standard form, Sec. 1):
+//   x^{n+1} = x^n + dt f(x^n; theta),  theta = (Du, Dv, F, k).
+// For a loss L(x^N) with lambda^N = dL/dx^N, reverse-mode differentiation of the loop gives
+//   lambda^n = lambda^{n+1} + dt J(x^n)^T lambda^{n+1},
+//   dL/dtheta = sum_n dt (df/dtheta)(x^n)^T lambda^{n+1},   dL/dx^0 = lambda^0.
+// With (u, v) = x^n and (a, b) = lambda^{n+1}, and the periodic Laplacian symmetric:
+//   a' = a + dt [Du lap a - (v^2 + F) a + v^2 b]
+//   b' = b + dt [Dv lap b - 2uv a + (2uv - F - k) b]
+//   dL/dDu += dt sum a lap u,  dL/dDv += dt sum b lap v,
+//   dL/dF  += dt sum [(1 - u) a - v b],  dL/dk += -dt sum v b.
+//
+// Memory/recompute: the forward pass stores x at every C-th step (C ~ sqrt(N)); the
+// backward pass walks the segments from last to first, recomputes the segment's states
+// from its checkpoint with the forward kernel, then runs the segment's adjoint steps.
+// Parameter-gradient partials are summed per CTA in FP64 (each CTA owns one slot, so the
+// order is fixed and the result deterministic) and added up in a fixed order at the end.
+#include <cmath>
+
+#include "pf_fe2d_tile.cuh"
 #include "pf_grid.h"
+#include "pf_internal.h"
 
 namespace pf {
+
+namespace {
+
+constexpr int kATX = 64, kATY = 16;  // adjoint tile
+constexpr int kAW = kATX + 2, kAH = kATY + 2, kAPL = kAW * kAH;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One reverse step on a 2D tile: stage u, v, a, b with a periodic halo of 1, update
+// (a, b) and add this tile's parameter-gradient terms to its FP64 slot.
+__global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs lam,
+                                                        FieldOut lam_out, Geom g,
+                                                        ModelParams m, double* gpart) {
+  __shared__ float su[kAPL], sv[kAPL], sa[kAPL], sb[kAPL];
+  __shared__ double red[4][kNT2 / 32];
+  const int x0 = blockIdx.x * kATX;
+  const int y0 = blockIdx.y * kATY;
+  for (int i = threadIdx.x; i < kAPL; i += kNT2) {
+    const int r = i / kAW;
+    const int c = i - r * kAW;
+    const int gy = wrap_index(y0 - 1 + r, g.ny);
+    const int gx = wrap_index(x0 - 1 + c, g.nx);
+    const int64_t off = (int64_t)gy * g.pitch + gx;
+    su[i] = __ldg(x.f[0] + off);
+    sv[i] = __ldg(x.f[1] + off);
+    sa[i] = __ldg(lam.f[0] + off);
+    sb[i] = __ldg(lam.f[1] + off);
+  }
+  __syncthreads();
+  float pDu = 0.f, pDv = 0.f, pF = 0.f, pk = 0.f;
+  for (int i = threadIdx.x; i < kATX * kATY; i += kNT2) {
+    const int rr = i / kATX;
+    const int cc = i - rr * kATX;
+    const int gx = x0 + cc;
+    const int gy = y0 + rr;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    const int p = (rr + 1) * kAW + (cc + 1);
+    const float u = su[p], v = sv[p], a = sa[p], b = sb[p];
+    const float la = lap2d(a, sa[p - 1], sa[p + 1], sa[p - kAW], sa[p + kAW], m.inv_h2);
+    const float lb = lap2d(b, sb[p - 1], sb[p + 1], sb[p - kAW], sb[p + kAW], m.inv_h2);
+    const float lu = lap2d(u, su[p - 1], su[p + 1], su[p - kAW], su[p + kAW], m.inv_h2);
+    const float lv = lap2d(v, sv[p - 1], sv[p + 1], sv[p - kAW], sv[p + kAW], m.inv_h2);
+    const float vv = __fmul_rn(v, v);
+    const float uv2 = __fmul_rn(2.0f, __fmul_rn(u, v));
+    // a' = a + dt [Du la - (v^2 + F) a + v^2 b]
+    float fa = __fmaf_rn(-__fadd_rn(vv, m.a2), a, __fmul_rn(vv, b));
+    fa = __fmaf_rn(m.a0, la, fa);
+    // b' = b + dt [Dv lb - 2uv a + (2uv - F - k) b]
+    float fb = __fmaf_rn(__fsub_rn(uv2, m.a3), b, -__fmul_rn(uv2, a));
+    fb = __fmaf_rn(m.a1, lb, fb);
+    const int64_t off = (int64_t)gy * g.pitch + gx;
+    lam_out.f[0][off] = __fmaf_rn(m.dt, fa, a);
+    lam_out.f[1][off] = __fmaf_rn(m.dt, fb, b);
+    pDu = __fmaf_rn(a, lu, pDu);
+    pDv = __fmaf_rn(b, lv, pDv);
+    pF = __fadd_rn(pF, __fsub_rn(__fmul_rn(__fsub_rn(1.0f, u), a), __fmul_rn(v, b)));
+    pk = __fsub_rn(pk, __fmul_rn(v, b));
+  }
+  double t[4] = {pDu, pDv, pF, pk};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    t[q] = warp_sum_d(t[q]);
+    if (lane == 0) red[q][wid] = t[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < kNT2 / 32; ++w) s += red[threadIdx.x][w];
+    double* slot = gpart + 4 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+    slot[threadIdx.x] += s;
+  }
+}
+
+// out[q] = sum over CTAs of gpart[4 * cta + q], in CTA order split over 256 threads.
+__global__ void __launch_bounds__(256) adj_final_kernel(const double* gpart, int64_t nctas,
+                                                        double* out) {
+  __shared__ double red[4][256 / 32];
+  double t[4] = {0, 0, 0, 0};
+  const int64_t per = (nctas + 255) / 256;
+  const int64_t c0 = per * threadIdx.x;
+  const int64_t c1 = c0 + per < nctas ? c0 + per : nctas;
+  for (int64_t c = c0; c < c1; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] += gpart[4 * c + q];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    t[q] = warp_sum_d(t[q]);
+    if (lane == 0) red[q][wid] = t[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < 256 / 32; ++w) s += red[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+}
+
+dim3 adj_grid(const Geom& g) { return dim3((g.nx + kATX - 1) / kATX, (g.ny + kATY - 1) / kATY, 1); }
+
+float* ckpt_field(pf_grid_s* g, int64_t i, int f) {
+  return g->adj.ckpt + (i * g->nf + f) * g->field_elems;
+}
+float* seg_field(pf_grid_s* g, int64_t j, int f) {
+  return g->adj.seg + (j * g->nf + f) * g->field_elems;
+}
+float* lam_field(pf_grid_s* g, int b, int f) {
+  return g->adj.lam + (b * g->nf + f) * g->field_elems;
+}
+
+int check_gs2d(pf_grid_s* g) {
+  if (!g->model_set || g->model != PF_MODEL_GS) {
+    set_error("the adjoint needs a Gray-Scott model");
+    return PF_ERR_STATE;
+  }
+  if (g->dim != 2) return invalid("the adjoint is implemented for 2D grids");
+  return PF_OK;
+}
+
+}  // namespace
 
 void adjoint_release(pf_grid_s* g) {
   AdjointState& a = g->adj;
@@ -15,3 +161,127 @@ void adjoint_release(pf_grid_s* g) {
 }
 
 }  // namespace pf
+
+using namespace pf;
+
+extern "C" {
+
+int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval) {
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_gs2d(g)) return rc;
+  if (n_steps < 1) return invalid("n_steps must be >= 1");
+  if (ckpt_interval < 0) return invalid("ckpt_interval must be >= 0");
+  int64_t C = ckpt_interval > 0 ? ckpt_interval : (int64_t)std::ceil(std::sqrt((double)n_steps));
+  if (C > n_steps) C = n_steps;
+  const int64_t n_ckpt = (n_steps + C - 1) / C;
+  AdjointState& a = g->adj;
+  const size_t state = sizeof(float) * g->nf * g->field_elems;
+  if (a.n_ckpt != n_ckpt || a.interval != C) {
+    // (re)allocate for this schedule
+    if (a.ckpt) cudaFree(a.ckpt);
+    if (a.seg) cudaFree(a.seg);
+    a.ckpt = nullptr;
+    a.seg = nullptr;
+    PF_CUDA_TRY(cudaMalloc(&a.ckpt, state * n_ckpt));
+    if (C > 1) PF_CUDA_TRY(cudaMalloc(&a.seg, state * (C - 1)));
+    a.n_ckpt = n_ckpt;
+    a.interval = C;
+  }
+  if (a.lam == nullptr) {
+    PF_CUDA_TRY(cudaMalloc(&a.lam, 2 * state));
+    PF_CUDA_TRY(cudaMemsetAsync(a.lam, 0, 2 * state, g->stream));
+  }
+  const dim3 grid = adj_grid(grid_geom(g));
+  const int64_t nctas = (int64_t)grid.x * grid.y;
+  if (a.gpart_cap < nctas) {
+    if (a.gpart) cudaFree(a.gpart);
+    a.gpart = nullptr;
+    PF_CUDA_TRY(cudaMalloc(&a.gpart, sizeof(double) * 4 * nctas));
+    a.gpart_cap = nctas;
+  }
+  if (a.gout == nullptr) PF_CUDA_TRY(cudaMalloc(&a.gout, sizeof(double) * 4));
+  if (a.ghost == nullptr) PF_CUDA_TRY(cudaMallocHost(&a.ghost, sizeof(double) * 4));
+  for (int64_t s = 0; s < n_ckpt; ++s) {
+    for (int f = 0; f < g->nf; ++f)
+      PF_CUDA_TRY(cudaMemcpyAsync(ckpt_field(g, s, f), g->buf[g->cur][f],
+                                  sizeof(float) * g->field_elems, cudaMemcpyDeviceToDevice,
+                                  g->stream));
+    const int64_t len = std::min(C, n_steps - s * C);
+    if (int rc = pf_step(g, len)) return rc;
+  }
+  for (int i = 0; i < 4; ++i) a.coeffs[i] = g->coeffs[i];
+  a.dt = g->dt;
+  a.n_steps = n_steps;
+  a.ready = 1;
+  return PF_OK;
+}
+
+int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int on_device,
+                    float* dLdu0, float* dLdv0, double* dtheta) {
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_gs2d(g)) return rc;
+  AdjointState& a = g->adj;
+  if (!a.ready) {
+    set_error("pf_adj_backward: no recorded forward pass (call pf_adj_forward first)");
+    return PF_ERR_STATE;
+  }
+  if (dLdu_N == nullptr || dLdv_N == nullptr) return invalid("dL/dx_N must not be NULL");
+  const Geom q = grid_geom(g);
+  const ModelParams m = make_params(PF_MODEL_GS, a.coeffs, a.dt, g->h);
+  const size_t w = sizeof(float) * g->nx;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const float* src[2] = {dLdu_N, dLdv_N};
+  for (int f = 0; f < 2; ++f)
+    PF_CUDA_TRY(cudaMemcpy2DAsync(lam_field(g, 0, f), sizeof(float) * g->pitch, src[f], w, w,
+                                  (size_t)g->ny, kin, g->stream));
+  const dim3 grid = adj_grid(q);
+  const int64_t nctas = (int64_t)grid.x * grid.y;
+  PF_CUDA_TRY(cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, g->stream));
+  int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
+  const int64_t C = a.interval;
+  for (int64_t s = a.n_ckpt - 1; s >= 0; --s) {
+    const int64_t s0 = s * C;
+    const int64_t len = std::min(C, a.n_steps - s0);
+    // states x^{s0} .. x^{s0+len-1}: slot 0 is the checkpoint, slots 1.. are recomputed
+    auto state = [&](int64_t j, int f) -> float* {
+      return j == 0 ? ckpt_field(g, s, f) : seg_field(g, j - 1, f);
+    };
+    for (int64_t j = 1; j < len; ++j) {
+      FieldPtrs in{};
+      FieldOut out{};
+      for (int f = 0; f < 2; ++f) {
+        in.f[f] = state(j - 1, f);
+        out.f[f] = state(j, f);
+      }
+      PF_CUDA_TRY(launch_fe2d(PF_MODEL_GS, 0, 1, q, in, out, m, g->stream));
+    }
+    for (int64_t j = len - 1; j >= 0; --j) {
+      FieldPtrs xs{}, li{};
+      FieldOut lo{};
+      for (int f = 0; f < 2; ++f) {
+        xs.f[f] = state(j, f);
+        li.f[f] = lam_field(g, lb, f);
+        lo.f[f] = lam_field(g, 1 - lb, f);
+      }
+      adj_gs2d_kernel<<<grid, kNT2, 0, g->stream>>>(xs, li, lo, q, m, a.gpart);
+      PF_CUDA_TRY(cudaGetLastError());
+      lb = 1 - lb;
+    }
+  }
+  adj_final_kernel<<<1, 256, 0, g->stream>>>(a.gpart, nctas, a.gout);
+  PF_CUDA_TRY(cudaGetLastError());
+  PF_CUDA_TRY(cudaMemcpyAsync(a.ghost, a.gout, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                              g->stream));
+  float* dst[2] = {dLdu0, dLdv0};
+  for (int f = 0; f < 2; ++f)
+    if (dst[f] != nullptr)
+      PF_CUDA_TRY(cudaMemcpy2DAsync(dst[f], w, lam_field(g, lb, f), sizeof(float) * g->pitch, w,
+                                    (size_t)g->ny, kout, g->stream));
+  PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (dtheta != nullptr)
+    for (int i = 0; i < 4; ++i) dtheta[i] = a.dt * a.ghost[i];
+  return PF_OK;
+}
+
+}  // extern "C"
