@@ -279,9 +279,93 @@ def run_gpu(args, rank, world, local):
         "gpu_launches": n_launch,
         "clocks": clocks,
     }
+    if not args.no_companions:
+        line["companions"] = companions(stream, hbm)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+def _time(stream, fn, reps=1):
+    """Device time (ms) of ``reps`` calls of ``fn`` on ``stream`` with CUDA events."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def companions(stream, hbm):
+    """The other workloads, each timed on the device: the 512-instance batched Gray-Scott
+    run against a plain 2D grid, the adjoint against the plain forward run at the same
+    size, and the Cahn-Hilliard 2048^2 and Allen-Cahn 128^2 steps."""
+    import torch
+    import paper_2109_02598_gb300 as pf
+    out = {}
+    with torch.cuda.stream(stream):
+        # ---- batched: 512 x 2D Gray-Scott, sides log-uniform in [64, 512], 2000 steps
+        specs = synthetic.batch_instances(512, seed=4)
+        b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5,
+                     stream=stream)
+        for i, q in enumerate(specs):
+            u, v = synthetic.batch_instance_init(q["n"], i)
+            b.write(i, 0, u).write(i, 1, v)
+        tuning = b.autotune(3)
+        b.run(2000)
+        ms = _time(stream, lambda: b.run(2000))
+        bglups = b.sites * 2000 / (ms * 1e-3) / 1e9
+        out["batched_gs2d_512x"] = {
+            "steps": 2000, "sites": b.sites, "ms": ms, "glups": bglups, "tuning": list(tuning),
+            "hbm_frac_k1_bytes": bglups * 16 / hbm, "launch": "one CUDA graph per 2000 steps"}
+        b.close()
+        # ---- plain 2D Gray-Scott of comparable state size (4096^2, 268 MB ping-pong)
+        u, v = synthetic.gray_scott_init((4096, 4096), seed=9, n_seeds=1024, side=8)
+        g = pf.Grid((4096, 4096), 2, stream=stream).set_model("gs", (0.2, 0.1, 0.04, 0.06), 0.5)
+        g.write_fields((u, v))
+        t2 = g.autotune(3)
+        g.step(20)
+        ms = _time(stream, lambda: g.step(200))
+        pglups = 4096 * 4096 * 200 / (ms * 1e-3) / 1e9
+        out["plain_gs2d_4096"] = {"glups": pglups, "tuning": list(t2)}
+        out["batched_gs2d_512x"]["vs_plain_gs2d_4096"] = bglups / pglups
+        g.close()
+        # ---- adjoint 512^2, 2000 steps, sqrt(N) checkpoints vs the plain forward run
+        w = synthetic.WORKLOADS["gs2d_adjoint_512"]
+        u0, v0 = synthetic.workload_init("gs2d_adjoint_512")
+        g = pf.Grid((512, 512), 2, stream=stream).set_model("gs", w["coeffs"], w["dt"])
+        g.write_fields((u0, v0))
+        g.step(10)
+        plain = _time(stream, lambda: g.step(2000))
+        g.write_fields((u0, v0))
+        fwd = _time(stream, lambda: pf.adjoint_forward(g, 2000))
+        uN = g.read_field(0, device=True)
+        vN = g.read_field(1, device=True)
+        gu, gv = uN * 0.01, vN * 0.01  # any dL/dx_N; cost does not depend on it
+        bwd = _time(stream, lambda: pf.adjoint_backward(g, gu, gv))
+        out["adjoint_gs2d_512"] = {
+            "steps": 2000, "checkpoint_interval": 45, "plain_forward_ms": plain,
+            "adjoint_forward_ms": fwd, "adjoint_backward_ms": bwd,
+            "ratio_vs_plain": (fwd + bwd) / plain}
+        g.close()
+        # ---- Cahn-Hilliard 2048^2 (L2-resident) and Allen-Cahn 128^2
+        for name, steps in (("ch2d_2048", 2000), ("ac2d_128", 1000)):
+            w = synthetic.WORKLOADS[name]
+            x0 = synthetic.workload_init(name)
+            g = pf.Grid(w["shape"], 1, stream=stream).set_model(w["model"], w["coeffs"], w["dt"])
+            g.write_fields(x0)
+            t = g.autotune(5)
+            g.step(steps // 10)
+            ms = _time(stream, lambda: g.step(steps))
+            sites = int(np.prod(w["shape"]))
+            out[name] = {"steps": steps, "glups": sites * steps / (ms * 1e-3) / 1e9,
+                         "tuning": list(t)}
+            g.close()
+    return out
 
 
 def _launch_schedule(n, k):
@@ -303,6 +387,8 @@ def main():
     ap.add_argument("--substeps", type=int, default=250)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-companions", action="store_true",
+                    help="skip the batched / adjoint / CH / AC measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         rank, world, _ = _dist_init(False)

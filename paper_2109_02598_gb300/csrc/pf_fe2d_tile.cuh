@@ -1,5 +1,14 @@
 // Tile body of the 2D forward-Euler kernel with temporal blocking; used by the plain
-// 2D kernel and by the batched runner so both execute identical arithmetic.
+// 2D kernel, the batched runner and the adjoint's recompute, so all execute identical
+// arithmetic.
+//
+// Shared-memory layout per field: HT rows of WS floats.  Staged column s of row r holds
+// the periodic value at (x0 - HP + s, y0 - H + r), where H = k R is the halo the k
+// sub-steps consume and HP = H rounded up to 4, so columns come in 16-byte-aligned groups
+// of four that match aligned groups in HBM.  Staging moves float4s (scalar loads with
+// periodic wrap only where a group crosses the grid edge), and every sub-step computes
+// four consecutive sites per thread from float4 rows: centre and y-neighbours as float4,
+// the two outer x-neighbours as scalars.
 #pragma once
 
 #include "pf_internal.h"
@@ -12,29 +21,59 @@ template <int MODEL, int K, int TX, int TY>
 struct Cfg2 {
   static constexpr int NF = ModelTraits<MODEL>::NF;
   static constexpr int R = ModelTraits<MODEL>::R;
-  static constexpr int H = K * R;          // halo width in sites
-  static constexpr int W = TX + 2 * H;     // staged region width
-  static constexpr int HT = TY + 2 * H;    // staged region height
-  static constexpr int PL = W * HT;        // floats per staged field
+  static constexpr int H = K * R;              // halo the k sub-steps consume (sites)
+  static constexpr int HP = (H + 3) / 4 * 4;   // staged halo, 16-byte aligned
+  static constexpr int WS = TX + 2 * HP;       // staged row width (floats)
+  static constexpr int HT = TY + 2 * H;        // staged rows
+  static constexpr int PL = WS * HT;           // floats per staged field
   static constexpr int NBUF = (K > 1) ? 2 : 1;
   static constexpr int MU = (MODEL == PF_MODEL_CH) ? PL : 0;
   static constexpr int SMEM_FLOATS = NF * NBUF * PL + MU;
+  static_assert(TX % 4 == 0, "tile width must be a multiple of 4");
 };
 
-// Stage rows [y0-H, y0+TY+H) x cols [x0-H, x0+TX+H) of every field (periodic wrap) into
-// buffer 0 of shared memory: sm[f * PL + r * W + c].
+// Stage rows [y0-H, y0+TY+H) x columns [x0-HP, x0+TX+HP) of every field into buffer 0.
 template <class C>
 __device__ __forceinline__ void load_region2d(const FieldPtrs& in, int nx, int ny,
                                               int64_t pitch, int x0, int y0, float* sm) {
-  for (int i = threadIdx.x; i < C::PL; i += kNT2) {
-    const int r = i / C::W;
-    const int c = i - r * C::W;
+  constexpr int CH4 = C::WS / 4;  // float4 groups per staged row
+  for (int i = threadIdx.x; i < C::HT * CH4; i += kNT2) {
+    const int r = i / CH4;
+    const int j = i - r * CH4;
     const int gy = wrap_index(y0 - C::H + r, ny);
-    const int gx = wrap_index(x0 - C::H + c, nx);
-    const int64_t off = (int64_t)gy * pitch + gx;
+    const int gx = x0 - C::HP + 4 * j;
+    const int64_t row = (int64_t)gy * pitch;
+    float* dst = sm + r * C::WS + 4 * j;
+    if (gx >= 0 && gx + 3 < nx) {
 #pragma unroll
-    for (int f = 0; f < C::NF; ++f) sm[f * C::PL + i] = __ldg(in.f[f] + off);
+      for (int f = 0; f < C::NF; ++f)
+        *reinterpret_cast<float4*>(dst + f * C::PL) =
+            __ldg(reinterpret_cast<const float4*>(in.f[f] + row + gx));
+    } else {
+      const int64_t o0 = row + wrap_index(gx, nx), o1 = row + wrap_index(gx + 1, nx);
+      const int64_t o2 = row + wrap_index(gx + 2, nx), o3 = row + wrap_index(gx + 3, nx);
+#pragma unroll
+      for (int f = 0; f < C::NF; ++f) {
+        const float* p = in.f[f];
+        *reinterpret_cast<float4*>(dst + f * C::PL) =
+            make_float4(__ldg(p + o0), __ldg(p + o1), __ldg(p + o2), __ldg(p + o3));
+      }
+    }
   }
+}
+
+// 2D Laplacians of four consecutive sites from a float4 row and its neighbours.
+__device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float inv_h2) {
+  const float4 c = *reinterpret_cast<const float4*>(s + p);
+  const float4 u = *reinterpret_cast<const float4*>(s + p - ws);
+  const float4 d = *reinterpret_cast<const float4*>(s + p + ws);
+  const float l = s[p - 1], r = s[p + 4];
+  float4 o;
+  o.x = lap2d(c.x, l, c.y, u.x, d.x, inv_h2);
+  o.y = lap2d(c.y, c.x, c.z, u.y, d.y, inv_h2);
+  o.z = lap2d(c.z, c.y, c.w, u.z, d.z, inv_h2);
+  o.w = lap2d(c.w, c.z, r, u.w, d.w, inv_h2);
+  return o;
 }
 
 // k forward-Euler sub-steps of one tile; the last one is written to `out` (sites beyond
@@ -44,7 +83,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
                                           int ny, int64_t pitch, int x0, int y0,
                                           const ModelParams& m, float* sm) {
   using C = Cfg2<MODEL, K, TX, TY>;
-  constexpr int W = C::W;
+  constexpr int WS = C::WS;
   constexpr int PL = C::PL;
   load_region2d<C>(in, nx, ny, pitch, x0, y0, sm);
   __syncthreads();
@@ -52,58 +91,75 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
   for (int s = 0; s < K; ++s) {
     const float* src = sm + (s & 1) * C::NF * PL;
     float* dst = sm + ((s + 1) & 1) * C::NF * PL;
+    float* mu = sm + C::NF * C::NBUF * PL;
     if constexpr (MODEL == PF_MODEL_CH) {
-      float* mu = sm + C::NF * C::NBUF * PL;
-      const int lm = C::R * s + 1;
-      const int mrows = C::HT - 2 * lm;
-      const int mcols = W - 2 * lm;
-      for (int i = threadIdx.x; i < mrows * mcols; i += kNT2) {
-        const int r = lm + i / mcols;
-        const int c = lm + (i - (i / mcols) * mcols);
-        const int p = r * W + c;
-        const float pc = src[p];
-        const float l = lap2d(pc, src[p - 1], src[p + 1], src[p - W], src[p + W], m.inv_h2);
-        mu[p] = ch_mu(pc, l, m);
+      // mu on the region one ring wider than this sub-step's phi update
+      const int rlo = C::R * s + 1, rhi = C::HT - rlo;
+      const int clo = (C::HP - C::H + C::R * s + 1) / 4, chi = (WS - (C::HP - C::H + C::R * s + 1) + 3) / 4;
+      const int nch = chi - clo;
+      for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
+        const int rr = i / nch;
+        const int r = rlo + rr;
+        const int p = r * WS + 4 * (clo + i - rr * nch);
+        const float4 c = *reinterpret_cast<const float4*>(src + p);
+        const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
+        *reinterpret_cast<float4*>(mu + p) =
+            make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
+                        ch_mu(c.w, l.w, m));
       }
       __syncthreads();
     }
     const bool last = (s == K - 1);
-    const int lo = C::R * (s + 1);
-    const int rows = C::HT - 2 * lo;
-    const int cols = W - 2 * lo;
-    for (int i = threadIdx.x; i < rows * cols; i += kNT2) {
-      const int rr = i / cols;
-      const int r = lo + rr;
-      const int c = lo + (i - rr * cols);
-      const int p = r * W + c;
-      float val[C::NF];
+    const int rlo = C::R * (s + 1), rhi = C::HT - rlo;
+    const int clo = last ? C::HP / 4 : (C::HP - C::H + C::R * (s + 1)) / 4;
+    const int chi = last ? (C::HP + TX) / 4 : (WS - (C::HP - C::H + C::R * (s + 1)) + 3) / 4;
+    const int nch = chi - clo;
+    for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
+      const int rr = i / nch;
+      const int r = rlo + rr;
+      const int j = clo + i - rr * nch;
+      const int p = r * WS + 4 * j;
+      float4 val[C::NF];
       if constexpr (MODEL == PF_MODEL_AC) {
-        const float pc = src[p];
-        const float l = lap2d(pc, src[p - 1], src[p + 1], src[p - W], src[p + W], m.inv_h2);
-        val[0] = ac_update(pc, l, m);
+        const float4 c = *reinterpret_cast<const float4*>(src + p);
+        const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
+        val[0] = make_float4(ac_update(c.x, l.x, m), ac_update(c.y, l.y, m),
+                             ac_update(c.z, l.z, m), ac_update(c.w, l.w, m));
       } else if constexpr (MODEL == PF_MODEL_CH) {
-        const float* mu = sm + C::NF * C::NBUF * PL;
-        const float l = lap2d(mu[p], mu[p - 1], mu[p + 1], mu[p - W], mu[p + W], m.inv_h2);
-        val[0] = ch_update(src[p], l, m);
+        const float4 c = *reinterpret_cast<const float4*>(src + p);
+        const float4 l = lap2d_x4(mu, p, WS, m.inv_h2);
+        val[0] = make_float4(ch_update(c.x, l.x, m), ch_update(c.y, l.y, m),
+                             ch_update(c.z, l.z, m), ch_update(c.w, l.w, m));
       } else {
-        const float* su = src;
-        const float* sv = src + PL;
-        const float u = su[p], v = sv[p];
-        const float lu = lap2d(u, su[p - 1], su[p + 1], su[p - W], su[p + W], m.inv_h2);
-        const float lv = lap2d(v, sv[p - 1], sv[p + 1], sv[p - W], sv[p + W], m.inv_h2);
-        gs_update(u, v, lu, lv, m, val[0], val[1]);
+        const float4 u = *reinterpret_cast<const float4*>(src + p);
+        const float4 v = *reinterpret_cast<const float4*>(src + PL + p);
+        const float4 lu = lap2d_x4(src, p, WS, m.inv_h2);
+        const float4 lv = lap2d_x4(src + PL, p, WS, m.inv_h2);
+        gs_update(u.x, v.x, lu.x, lv.x, m, val[0].x, val[1].x);
+        gs_update(u.y, v.y, lu.y, lv.y, m, val[0].y, val[1].y);
+        gs_update(u.z, v.z, lu.z, lv.z, m, val[0].z, val[1].z);
+        gs_update(u.w, v.w, lu.w, lv.w, m, val[0].w, val[1].w);
       }
       if (last) {
-        const int gx = x0 + c - C::H;
+        const int gx = x0 + 4 * j - C::HP;
         const int gy = y0 + r - C::H;
-        if (gx < nx && gy < ny) {
+        if (gy < ny) {
           const int64_t off = (int64_t)gy * pitch + gx;
+          if (gx + 3 < nx) {
 #pragma unroll
-          for (int f = 0; f < C::NF; ++f) out.f[f][off] = val[f];
+            for (int f = 0; f < C::NF; ++f) *reinterpret_cast<float4*>(out.f[f] + off) = val[f];
+          } else {
+#pragma unroll
+            for (int f = 0; f < C::NF; ++f) {
+              if (gx < nx) out.f[f][off] = val[f].x;
+              if (gx + 1 < nx) out.f[f][off + 1] = val[f].y;
+              if (gx + 2 < nx) out.f[f][off + 2] = val[f].z;
+            }
+          }
         }
       } else {
 #pragma unroll
-        for (int f = 0; f < C::NF; ++f) dst[f * PL + p] = val[f];
+        for (int f = 0; f < C::NF; ++f) *reinterpret_cast<float4*>(dst + f * PL + p) = val[f];
       }
     }
     if (!last) __syncthreads();
