@@ -34,6 +34,9 @@ UNIT = "GLUPS"
 WORKLOAD = "gs3d_256"
 BYTES_PER_LUP = {"gs": 16.0, "ac": 8.0, "ch": 8.0}  # k = 1: read + write every field once
 TMA_TILES = {(64, 16), (128, 8), (128, 16)}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now
+# (profiles/fe3d_tma_gs3d_256.md); reported only for that kernel and tile.
+PROFILED_TRAFFIC = {("fe3d_tma_kernel", 128, 16): 218.37e6}
 
 
 def _peaks():
@@ -268,7 +271,10 @@ def run_gpu(args, rank, world, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback",
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": PROFILED_TRAFFIC.get(("fe3d_tma_kernel",) + tuple(tuning[:2])),
+                     "traffic_note": "ncu dram__bytes_read+write per launch, 1 capture; writes "
+                                     "still dirty in L2 at kernel end are not counted",
                      "kernel": ("fe3d_tma_kernel (TMA-staged z-streaming, 7-point GS)"
                                 if tuple(tuning[:2]) in TMA_TILES else
                                 "fe3d_r1_kernel (general z-streaming, 7-point GS)"),
