@@ -160,6 +160,55 @@ void adjoint_release(pf_grid_s* g) {
   a = AdjointState();
 }
 
+// Enqueue the whole reverse pass on stream st (recorded into a graph by the caller):
+// zero the gradient slots, then per segment from last to first recompute its states and
+// run its reverse steps, then sum the slots. *lb_out receives the buffer holding lambda^0.
+static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStream_t st,
+                                   int* lb_out) {
+  AdjointState& a = g->adj;
+  const Geom q = grid_geom(g);
+  const dim3 grid = adj_grid(q);
+  const int64_t nctas = (int64_t)grid.x * grid.y;
+  cudaError_t e = cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, st);
+  int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
+  const int64_t C = a.interval;
+  for (int64_t s = a.n_ckpt - 1; s >= 0 && e == cudaSuccess; --s) {
+    const int64_t s0 = s * C;
+    const int64_t len = std::min(C, a.n_steps - s0);
+    // states x^{s0} .. x^{s0+len-1}: slot 0 is the checkpoint, slots 1.. are recomputed
+    auto state = [&](int64_t j, int f) -> float* {
+      return j == 0 ? ckpt_field(g, s, f) : seg_field(g, j - 1, f);
+    };
+    for (int64_t j = 1; j < len && e == cudaSuccess; ++j) {
+      FieldPtrs in{};
+      FieldOut out{};
+      for (int f = 0; f < 2; ++f) {
+        in.f[f] = state(j - 1, f);
+        out.f[f] = state(j, f);
+      }
+      e = launch_fe2d(PF_MODEL_GS, 0, 1, q, in, out, m, st);
+    }
+    for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j) {
+      FieldPtrs xs{}, li{};
+      FieldOut lo{};
+      for (int f = 0; f < 2; ++f) {
+        xs.f[f] = state(j, f);
+        li.f[f] = lam_field(g, lb, f);
+        lo.f[f] = lam_field(g, 1 - lb, f);
+      }
+      adj_gs2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+      e = cudaGetLastError();
+      lb = 1 - lb;
+    }
+  }
+  if (e == cudaSuccess) {
+    adj_final_kernel<<<1, 256, 0, st>>>(a.gpart, nctas, a.gout);
+    e = cudaGetLastError();
+  }
+  *lb_out = lb;
+  return e;
+}
+
 }  // namespace pf
 
 using namespace pf;
@@ -226,7 +275,6 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
     return PF_ERR_STATE;
   }
   if (dLdu_N == nullptr || dLdv_N == nullptr) return invalid("dL/dx_N must not be NULL");
-  const Geom q = grid_geom(g);
   const ModelParams m = make_params(PF_MODEL_GS, a.coeffs, a.dt, g->h);
   const size_t w = sizeof(float) * g->nx;
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -235,42 +283,33 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
   for (int f = 0; f < 2; ++f)
     PF_CUDA_TRY(cudaMemcpy2DAsync(lam_field(g, 0, f), sizeof(float) * g->pitch, src[f], w, w,
                                   (size_t)g->ny, kin, g->stream));
-  const dim3 grid = adj_grid(q);
-  const int64_t nctas = (int64_t)grid.x * grid.y;
-  PF_CUDA_TRY(cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, g->stream));
-  int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
-  const int64_t C = a.interval;
-  for (int64_t s = a.n_ckpt - 1; s >= 0; --s) {
-    const int64_t s0 = s * C;
-    const int64_t len = std::min(C, a.n_steps - s0);
-    // states x^{s0} .. x^{s0+len-1}: slot 0 is the checkpoint, slots 1.. are recomputed
-    auto state = [&](int64_t j, int f) -> float* {
-      return j == 0 ? ckpt_field(g, s, f) : seg_field(g, j - 1, f);
-    };
-    for (int64_t j = 1; j < len; ++j) {
-      FieldPtrs in{};
-      FieldOut out{};
-      for (int f = 0; f < 2; ++f) {
-        in.f[f] = state(j - 1, f);
-        out.f[f] = state(j, f);
-      }
-      PF_CUDA_TRY(launch_fe2d(PF_MODEL_GS, 0, 1, q, in, out, m, g->stream));
+  if (g->adj_exec == nullptr || g->adj_exec_steps != a.n_steps ||
+      g->adj_exec_interval != a.interval) {
+    if (g->adj_exec) cudaGraphExecDestroy(g->adj_exec);
+    g->adj_exec = nullptr;
+    if (g->capture == nullptr)
+      PF_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
+    PF_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeRelaxed));
+    int lb = 0;
+    cudaError_t e = enqueue_reverse(g, m, g->capture, &lb);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(e != cudaSuccess ? e : e2, "pf_adj_backward graph capture");
     }
-    for (int64_t j = len - 1; j >= 0; --j) {
-      FieldPtrs xs{}, li{};
-      FieldOut lo{};
-      for (int f = 0; f < 2; ++f) {
-        xs.f[f] = state(j, f);
-        li.f[f] = lam_field(g, lb, f);
-        lo.f[f] = lam_field(g, 1 - lb, f);
-      }
-      adj_gs2d_kernel<<<grid, kNT2, 0, g->stream>>>(xs, li, lo, q, m, a.gpart);
-      PF_CUDA_TRY(cudaGetLastError());
-      lb = 1 - lb;
+    e = cudaGraphInstantiate(&g->adj_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g->adj_exec = nullptr;
+      return cuda_fail(e, "pf_adj_backward cudaGraphInstantiate");
     }
+    g->adj_exec_steps = a.n_steps;
+    g->adj_exec_interval = a.interval;
+    g->adj_exec_lb = lb;
   }
-  adj_final_kernel<<<1, 256, 0, g->stream>>>(a.gpart, nctas, a.gout);
-  PF_CUDA_TRY(cudaGetLastError());
+  PF_CUDA_TRY(cudaGraphLaunch(g->adj_exec, g->stream));
+  const int lb = g->adj_exec_lb;
   PF_CUDA_TRY(cudaMemcpyAsync(a.ghost, a.gout, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                               g->stream));
   float* dst[2] = {dLdu0, dLdv0};

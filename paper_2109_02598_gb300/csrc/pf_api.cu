@@ -154,7 +154,7 @@ int check_device_error(pf_grid_s* g) {
 }
 
 // One launch advancing `k` steps from buffer `src` into buffer `dst`.
-cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst) {
+cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStream_t st) {
   FieldPtrs in{};
   FieldOut out{};
   for (int f = 0; f < g->nf; ++f) {
@@ -162,10 +162,67 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst) {
     out.f[f] = g->buf[dst][f];
   }
   const Geom q = grid_geom(g);
-  if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, g->stream);
-  if (tile >= kFirstTmaTile3D) return launch_fe3d_tma(g, tile - kFirstTmaTile3D, src, dst);
-  return launch_fe3d(g->model, tile, q, in, out, g->params, g->stream);
+  if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, st);
+  if (tile >= kFirstTmaTile3D) return launch_fe3d_tma(g, tile - kFirstTmaTile3D, src, dst, st);
+  return launch_fe3d(g->model, tile, q, in, out, g->params, st);
 }
+
+// Forget every recorded graph (their kernel parameters carry coefficients and tuning).
+void drop_graphs(pf_grid_s* g) {
+  for (auto& sg : g->step_graphs) {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    sg = pf_grid_s::StepGraph();
+  }
+  if (g->adj_exec) cudaGraphExecDestroy(g->adj_exec);
+  g->adj_exec = nullptr;
+  g->adj_exec_steps = -1;
+}
+
+// Launch plan of pf_step: depths k, k, ..., then smaller ones for the remainder.
+static int count_launches(int64_t n, int kmax) {
+  int c = 0;
+  while (n > 0) {
+    int k = kmax;
+    while (k > n) k >>= 1;
+    n -= k;
+    ++c;
+  }
+  return c;
+}
+
+// Record the launches of pf_step(n) from buffer g->cur into a graph on the private stream.
+static int record_step_graph(pf_grid_s* g, int64_t n, cudaGraphExec_t* exec, int* flip) {
+  if (g->capture == nullptr)
+    PF_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
+  PF_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = cudaSuccess;
+  int src = g->cur, launches = 0;
+  int64_t left = n;
+  while (left > 0 && e == cudaSuccess) {
+    int k = g->k;
+    while (k > left) k >>= 1;
+    e = launch_step(g, g->tile, k, src, 1 - src, g->capture);
+    src = 1 - src;
+    left -= k;
+    ++launches;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e != cudaSuccess ? e : e2, "pf_step graph capture");
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return cuda_fail(e, "pf_step cudaGraphInstantiate");
+  }
+  *flip = launches & 1;
+  return PF_OK;
+}
+
+constexpr int kGraphMinLaunches = 8;
 
 int check_grid(pf_grid_s* g) {
   if (g == nullptr || g->magic != kGridMagic) return invalid("invalid grid handle");
@@ -240,6 +297,8 @@ void pf_destroy(pf_grid_t g) {
   if (g == nullptr || g->magic != kGridMagic) return;
   cudaStreamSynchronize(g->stream);
   pf::adjoint_release(g);
+  drop_graphs(g);
+  if (g->capture) cudaStreamDestroy(g->capture);
   if (g->base) cudaFree(g->base);
   if (g->red_partials) cudaFree(g->red_partials);
   if (g->red_host) cudaFreeHost(g->red_host);
@@ -271,6 +330,7 @@ int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, dou
   g->dt = dt;
   g->params = make_params(model, coeffs, dt, g->h);
   g->model_set = 1;
+  drop_graphs(g);  // recorded graphs carry the old coefficients
   resolve_tuning(g);
   return PF_OK;
 }
@@ -308,11 +368,37 @@ int pf_step(pf_grid_t g, int64_t n_steps) {
     return PF_ERR_STATE;
   }
   if (n_steps < 0) return invalid("n_steps must be >= 0");
+  if (n_steps == 0) return PF_OK;
+  if (count_launches(n_steps, g->k) >= kGraphMinLaunches) {
+    // replay a recorded graph of the whole launch sequence (one host call)
+    pf_grid_s::StepGraph* hit = nullptr;
+    pf_grid_s::StepGraph* victim = &g->step_graphs[0];
+    for (auto& sg : g->step_graphs) {
+      if (sg.exec && sg.steps == n_steps && sg.tile == g->tile && sg.k == g->k &&
+          sg.start == g->cur)
+        hit = &sg;
+      if (sg.used < victim->used) victim = &sg;
+    }
+    if (hit == nullptr) {
+      if (victim->exec) cudaGraphExecDestroy(victim->exec);
+      *victim = pf_grid_s::StepGraph();
+      if (int rc = record_step_graph(g, n_steps, &victim->exec, &victim->flip)) return rc;
+      victim->steps = n_steps;
+      victim->tile = g->tile;
+      victim->k = g->k;
+      victim->start = g->cur;
+      hit = victim;
+    }
+    hit->used = ++g->graph_clock;
+    PF_CUDA_TRY(cudaGraphLaunch(hit->exec, g->stream));
+    if (hit->flip) g->cur = 1 - g->cur;
+    return PF_OK;
+  }
   int64_t left = n_steps;
   while (left > 0) {
     int k = g->k;
     while (k > left) k >>= 1;  // k in {4, 2, 1}
-    PF_CUDA_TRY(launch_step(g, g->tile, k, g->cur, 1 - g->cur));
+    PF_CUDA_TRY(launch_step(g, g->tile, k, g->cur, 1 - g->cur, g->stream));
     g->cur = 1 - g->cur;
     left -= k;
   }
@@ -371,6 +457,7 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
                    tile_x, tile_y, tile_x, tile_y);
   g->req_tile = tile;
   g->req_k = k_steps;
+  drop_graphs(g);
   return resolve_tuning(g);
 }
 
@@ -406,10 +493,10 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
     for (int ki = 0; ki < 3 && rc == PF_OK; ++ki) {
       const int k = ks[ki];
       if (!tile_supported(g, t, k)) continue;
-      cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur);  // warm-up
+      cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur, g->stream);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
       for (int i = 0; i < probe_launches && e == cudaSuccess; ++i)
-        e = launch_step(g, t, k, g->cur, 1 - g->cur);
+        e = launch_step(g, t, k, g->cur, 1 - g->cur, g->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0;
@@ -431,6 +518,7 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   if (rc != PF_OK) return rc;
   g->req_tile = best_tile;
   g->req_k = best_k;
+  drop_graphs(g);
   resolve_tuning(g);
   return pf_get_tuning(g, tile_x, tile_y, k_steps);
 }

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
 }
 
 template <int MODEL, int TX, int TY, int NS>
-cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out) {
+cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out, cudaStream_t st) {
   using C = CfgT<MODEL, TX, TY, NS>;
   auto kern = fe3d_tma_kernel<MODEL, TX, TY, NS>;
   static int occ = 0;  // resident CTAs per SM (same on every GB300)
@@ -230,7 +230,7 @@ cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out) {
   nchunks = (g.nz + chunk_len - 1) / chunk_len;
   const long long items = ncols * nchunks;
   const long long grid = items < slots ? items : slots;
-  kern<<<(unsigned)grid, C::NT, C::SMEM, gr->stream>>>(maps, out, g, gr->params, tiles_x,
+  kern<<<(unsigned)grid, C::NT, C::SMEM, st>>>(maps, out, g, gr->params, tiles_x,
                                                        (int)nchunks, chunk_len, gr->d_err);
   return cudaGetLastError();
 }
@@ -250,7 +250,7 @@ void tma3d_tile_shape(int tma_tile, int* tx, int* ty) {
   *ty = s[tma_tile][1];
 }
 
-cudaError_t launch_fe3d_tma(pf_grid_s* gr, int tma_tile, int src, int dst) {
+cudaError_t launch_fe3d_tma(pf_grid_s* gr, int tma_tile, int src, int dst, cudaStream_t st) {
   cudaError_t e = tma3d_maps(gr, tma_tile, src);
   if (e != cudaSuccess) return e;
   FieldOut out{};
@@ -258,15 +258,15 @@ cudaError_t launch_fe3d_tma(pf_grid_s* gr, int tma_tile, int src, int dst) {
   const Tma3dMaps& maps = gr->tma.maps[src];
   if (gr->model == PF_MODEL_GS) {
     switch (tma_tile) {
-      case 0: return launch_tma<PF_MODEL_GS, 64, 16, 5>(gr, maps, out);
-      case 1: return launch_tma<PF_MODEL_GS, 128, 8, 5>(gr, maps, out);
-      case 2: return launch_tma<PF_MODEL_GS, 128, 16, 5>(gr, maps, out);
+      case 0: return launch_tma<PF_MODEL_GS, 64, 16, 5>(gr, maps, out, st);
+      case 1: return launch_tma<PF_MODEL_GS, 128, 8, 5>(gr, maps, out, st);
+      case 2: return launch_tma<PF_MODEL_GS, 128, 16, 5>(gr, maps, out, st);
     }
   } else if (gr->model == PF_MODEL_AC) {
     switch (tma_tile) {
-      case 0: return launch_tma<PF_MODEL_AC, 64, 16, 6>(gr, maps, out);
-      case 1: return launch_tma<PF_MODEL_AC, 128, 8, 6>(gr, maps, out);
-      case 2: return launch_tma<PF_MODEL_AC, 128, 16, 5>(gr, maps, out);
+      case 0: return launch_tma<PF_MODEL_AC, 64, 16, 6>(gr, maps, out, st);
+      case 1: return launch_tma<PF_MODEL_AC, 128, 8, 6>(gr, maps, out, st);
+      case 2: return launch_tma<PF_MODEL_AC, 128, 16, 5>(gr, maps, out, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -69,20 +69,35 @@ struct pf_grid_s {
   pf::AdjointState adj;
   pf::TmaCache tma;
   int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
+  // CUDA-graph cache of pf_step: a few recorded launch sequences, keyed by
+  // (steps, tile, k, starting buffer), least recently used replaced first
+  cudaStream_t capture = nullptr;  // private stream used only to record graphs
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t steps = -1;
+    int tile = -1, k = -1, start = -1, flip = 0;
+    uint64_t used = 0;
+  } step_graphs[4];
+  uint64_t graph_clock = 0;
+  // CUDA-graph cache of the adjoint's reverse pass
+  cudaGraphExec_t adj_exec = nullptr;
+  int64_t adj_exec_steps = -1, adj_exec_interval = -1;
+  int adj_exec_lb = 0;  // lambda buffer holding lambda^0 after the graph
 };
 
 namespace pf {
 void adjoint_release(pf_grid_s* g);
+void drop_graphs(pf_grid_s* g);
 int invalid(const char* fmt, ...);
 int check_grid(pf_grid_s* g);
 Geom grid_geom(const pf_grid_s* g);
 ModelParams make_params(int model, const double* c, double dt, double h);
-cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst);
+cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStream_t st);
 
 // ---- 3D TMA kernel (AC, GS): TMA tile ids 0 = 64x16, 1 = 128x8, 2 = 128x16
 constexpr int kNumTmaTiles3D = 3;
 void tma3d_tile_shape(int tma_tile, int* tx, int* ty);
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g);
 cudaError_t tma3d_maps(pf_grid_s* g, int tma_tile, int buf);
-cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst);
+cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst, cudaStream_t st);
 }  // namespace pf

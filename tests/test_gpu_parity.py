@@ -120,6 +120,26 @@ def test_tiles_and_temporal_blocking_are_bitwise_identical(pf, model):
             assert np.array_equal(a, b), t
 
 
+@pytest.mark.parametrize("shape", [(40, 72), (6, 32, 64)])
+def test_recorded_step_graphs_follow_model_and_tuning_changes(pf, shape):
+    # pf_step replays recorded CUDA graphs for long launch sequences; changing the
+    # coefficients or the tuning must not replay a stale graph
+    (x0,) = init_fields("ac", shape, seed=9)
+    g = pf.Grid(shape, 1).set_model("ac", (1.0, 1.0), 0.05)
+    g.write_field(0, x0)
+    g.step(30)
+    g.step(30)  # replay from the other buffer
+    g.set_model("ac", (0.5, 2.0), 0.02)
+    g.step(30)
+    g.set_tuning(32, 16, 1) if len(shape) == 3 else g.set_tuning(32, 32, 2)
+    g.step(30)
+    got = g.read_field(0)
+    g.close()
+    ref = oracle.run("ac", (x0,), (1.0, 1.0), 0.05, 60)
+    ref = oracle.run("ac", ref, (0.5, 2.0), 0.02, 60)
+    assert rel_linf((got,), ref) <= 5e-5
+
+
 def test_tma_tile_rejected_when_grid_does_not_divide(pf):
     from paper_2109_02598_gb300 import PfError
     g = pf.Grid((8, 20, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
