@@ -105,3 +105,23 @@ class Batch:
         check(self._lib.pf_batch_autotune(self._h, probe_launches, ctypes.byref(a),
                                           ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+
+def shard_instances(sizes, rank: int, world: int):
+    """Indices of the batch instances rank ``rank`` of ``world`` runs.
+
+    The instances are independent, so ranks share no data: a deterministic greedy split
+    (largest grid first, to the rank with the fewest sites so far; ties to the lowest rank)
+    balances lattice sites across ranks.  ``sizes`` are sites per instance.
+    """
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]), i))
+    load = [0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += int(sizes[i])
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
