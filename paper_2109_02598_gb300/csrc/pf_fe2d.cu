@@ -50,13 +50,9 @@ cudaError_t launch_batch_one(const BatchInst* d_insts, const BatchTile* d_tiles,
                              const float* in_base, float* out_base, cudaStream_t s) {
   using C = Cfg2<PF_MODEL_GS, K, TX, TY>;
   const size_t smem = sizeof(float) * C::SMEM_FLOATS;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(batch_gs2d_kernel<K, TX, TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static unsigned long long attr_mask = 0;
+  cudaError_t e = ensure_smem_attr(batch_gs2d_kernel<K, TX, TY>, smem, &attr_mask);
+  if (e != cudaSuccess) return e;
   batch_gs2d_kernel<K, TX, TY><<<ntiles, kNT2, smem, s>>>(d_insts, d_tiles, in_base, out_base);
   return cudaGetLastError();
 }
@@ -78,14 +74,9 @@ cudaError_t launch_one(const Geom& g, FieldPtrs in, FieldOut out, const ModelPar
                        cudaStream_t s) {
   using C = Cfg2<MODEL, K, TX, TY>;
   const size_t smem = sizeof(float) * C::SMEM_FLOATS;
-  static bool attr_done = false;  // per instantiation; idempotent if raced
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fe2d_kernel<MODEL, K, TX, TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static unsigned long long attr_mask = 0;  // per instantiation and device
+  cudaError_t e = ensure_smem_attr(fe2d_kernel<MODEL, K, TX, TY>, smem, &attr_mask);
+  if (e != cudaSuccess) return e;
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
   fe2d_kernel<MODEL, K, TX, TY><<<grid, kNT2, smem, s>>>(in, out, g, m);
   return cudaGetLastError();

@@ -173,14 +173,6 @@ __global__ void __launch_bounds__(kNT3) fe3d_ch_kernel(FieldPtrs in, FieldOut ou
   }
 }
 
-template <class KernelT>
-cudaError_t set_smem(KernelT k, size_t bytes, bool* done) {
-  if (*done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) *done = true;
-  return e;
-}
-
 int choose_tz(const Geom& g, int tiles_xy) {
   // enough CTAs for several waves on 152 SMs, but chunks long enough that the two
   // extra prologue planes stay a small fraction
@@ -194,16 +186,16 @@ cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams
                     cudaStream_t s) {
   using C = Cfg3<MODEL, TX, TY>;
   const size_t smem = sizeof(float) * C::SMEM_FLOATS;
-  static bool done = false;
+  static unsigned long long attr_mask = 0;  // per instantiation and device
   const int bx = (g.nx + TX - 1) / TX, by = (g.ny + TY - 1) / TY;
   const int tz = choose_tz(g, bx * by);
   dim3 grid(bx, by, (g.nz + tz - 1) / tz);
   if constexpr (MODEL == PF_MODEL_CH) {
-    cudaError_t e = set_smem(fe3d_ch_kernel<TX, TY>, smem, &done);
+    cudaError_t e = ensure_smem_attr(fe3d_ch_kernel<TX, TY>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
     fe3d_ch_kernel<TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   } else {
-    cudaError_t e = set_smem(fe3d_r1_kernel<MODEL, TX, TY>, smem, &done);
+    cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
     fe3d_r1_kernel<MODEL, TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   }

@@ -204,15 +204,16 @@ template <int MODEL, int TX, int TY, int NS>
 cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out, cudaStream_t st) {
   using C = CfgT<MODEL, TX, TY, NS>;
   auto kern = fe3d_tma_kernel<MODEL, TX, TY, NS>;
-  static int occ = 0;  // resident CTAs per SM (same on every GB300)
+  static unsigned long long attr_mask = 0;  // per instantiation and device
+  cudaError_t e0 = ensure_smem_attr(kern, C::SMEM, &attr_mask);
+  if (e0 != cudaSuccess) return e0;
+  static int occ_by_dev[64] = {};  // resident CTAs per SM, per device
+  int occ = gr->device < 64 ? occ_by_dev[gr->device] : 0;
   if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    int o = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::NT, C::SMEM);
-    if (e != cudaSuccess) return e;
-    occ = o > 0 ? o : 1;
+    e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::NT, C::SMEM);
+    if (e0 != cudaSuccess) return e0;
+    if (occ < 1) occ = 1;
+    if (gr->device < 64) occ_by_dev[gr->device] = occ;
   }
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gr->device);

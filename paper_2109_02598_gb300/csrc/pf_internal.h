@@ -29,6 +29,20 @@ struct FieldOut {
   float* f[PF_MAX_FIELDS];
 };
 
+// Set a kernel's dynamic shared-memory limit once per device (the attribute is per device;
+// `mask` has one bit per device ordinal below 64, set after success).
+template <class KernelT>
+cudaError_t ensure_smem_attr(KernelT kernel, size_t bytes, unsigned long long* mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit != 0 && (*mask & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *mask |= bit;
+  return e;
+}
+
 // Thread-local error reporting (pf_last_error).
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
