@@ -16,6 +16,10 @@ Every function is plain numpy in float64 and follows the paper's definitions dir
   the first two numbered equations), with the coefficient names of the model
   definitions figure (Fig. "models_abc_definitions"): A uses c1 (linear) and c2 (cubic);
   B uses c1, c2 and a mobility M multiplying the whole right-hand side;
+* Model C (eutectic; Sec. 3, third numbered equation and its model definition): a
+  non-conserved psi and a conserved m coupled through c5,
+  dpsi/dt = lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
+  dm/dt = lap(c4 m^3 - c3 m - c5 psi^2 - lap m);
 * Gray-Scott, which the paper names as a reaction-diffusion example (Sec. 1) but does not
   write out, in its standard two-species form
   du/dt = Du lap u - u v^2 + F (1 - u),  dv/dt = Dv lap v + u v^2 - (F + k) v;
@@ -31,7 +35,7 @@ from __future__ import annotations
 
 import numpy as np
 
-MODELS = ("ac", "ch", "gs")
+MODELS = ("ac", "ch", "gs", "c")
 
 
 def _f64(x):
@@ -84,6 +88,16 @@ def rhs_gray_scott(u, v, Du: float, Dv: float, F: float, k: float, h: float = 1.
     return fu, fv
 
 
+def rhs_model_c(psi, m, c1=1.0, c2=1.0, c3=1.0, c4=1.0, c5=1.0, h: float = 1.0):
+    """Model C: (lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
+                 lap(c4 m^3 - c3 m - c5 psi^2 - lap m))."""
+    psi = _f64(psi)
+    m = _f64(m)
+    f_psi = laplacian(psi, h) + c1 * psi - c2 * psi ** 3 + 2.0 * c5 * psi * m
+    mu_m = c4 * m ** 3 - c3 * m - c5 * psi ** 2 - laplacian(m, h)
+    return f_psi, laplacian(mu_m, h)
+
+
 def rhs(model: str, fields, coeffs, h: float = 1.0):
     """Right-hand side f(x) of ``model`` for the tuple of fields ``x``."""
     if model == "ac":
@@ -92,6 +106,8 @@ def rhs(model: str, fields, coeffs, h: float = 1.0):
         return (rhs_cahn_hilliard(fields[0], *coeffs, h=h),)
     if model == "gs":
         return rhs_gray_scott(fields[0], fields[1], *coeffs, h=h)
+    if model == "c":
+        return rhs_model_c(fields[0], fields[1], *coeffs, h=h)
     raise ValueError(f"unknown model {model!r}")
 
 
@@ -134,6 +150,24 @@ def energy(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
         grad2 += d * d
     dens = 0.5 * grad2 - 0.5 * c1 * phi ** 2 + 0.25 * c2 * phi ** 4
     return h ** phi.ndim * dens.sum()
+
+
+def energy_model_c(psi, m, c1=1.0, c2=1.0, c3=1.0, c4=1.0, c5=1.0, h: float = 1.0):
+    """Model C free energy h^d sum_x [ 1/2 |grad psi|^2 - c1/2 psi^2 + c2/4 psi^4
+    + 1/2 |grad m|^2 - c3/2 m^2 + c4/4 m^4 - c5 psi^2 m ] (forward differences).
+
+    -dE/dpsi / h^d is the psi right-hand side and dE/dm / h^d the m chemical potential.
+    """
+    psi = _f64(psi)
+    m = _f64(m)
+    g = np.zeros(psi.shape, dtype=np.result_type(psi, m))
+    for ax in range(psi.ndim):
+        dp = (np.roll(psi, -1, axis=ax) - psi) / h
+        dm = (np.roll(m, -1, axis=ax) - m) / h
+        g += dp * dp + dm * dm
+    dens = (0.5 * g - 0.5 * c1 * psi ** 2 + 0.25 * c2 * psi ** 4 - 0.5 * c3 * m ** 2
+            + 0.25 * c4 * m ** 4 - c5 * psi ** 2 * m)
+    return h ** psi.ndim * dens.sum()
 
 
 # --------------------------------------------------------- Gray-Scott discrete adjoint

@@ -119,6 +119,15 @@ def _brute_force_step(model, fields, coeffs, dt, h):
             mu[s] = c2 * p[s] ** 3 - c1 * p[s] - lap(p, s)
         for s in sites:
             out[0][s] = p[s] + dt * M * lap(mu, s)
+    elif model == "c":
+        c1, c2, c3, c4, c5 = coeffs
+        p, q = fields
+        mu = np.zeros(shape)
+        for s in sites:
+            mu[s] = c4 * q[s] ** 3 - c3 * q[s] - c5 * p[s] ** 2 - lap(q, s)
+        for s in sites:
+            out[0][s] = p[s] + dt * (lap(p, s) + c1 * p[s] - c2 * p[s] ** 3 + 2 * c5 * p[s] * q[s])
+            out[1][s] = q[s] + dt * lap(mu, s)
     else:
         Du, Dv, F, k = coeffs
         u, v = fields
@@ -130,11 +139,12 @@ def _brute_force_step(model, fields, coeffs, dt, h):
 
 
 @pytest.mark.parametrize("model,coeffs", [("ac", (1.0, 1.0)), ("ch", (0.8, 1.2, 0.9)),
-                                          ("gs", (0.2, 0.1, 0.04, 0.06))])
+                                          ("gs", (0.2, 0.1, 0.04, 0.06)),
+                                          ("c", (0.9, 1.1, 0.8, 1.2, 0.7))])
 @pytest.mark.parametrize("shape", [(3, 4), (5, 5), (2, 3, 4)])
 def test_step_matches_per_site_brute_force(model, coeffs, shape):
     rng = np.random.default_rng(17)
-    nf = 2 if model == "gs" else 1
+    nf = 2 if model in ("gs", "c") else 1
     fields = tuple(rng.uniform(-0.5, 1.0, shape) for _ in range(nf))
     h, dt = 0.9, 0.01
     ref = _brute_force_step(model, fields, coeffs, dt, h)
@@ -144,12 +154,13 @@ def test_step_matches_per_site_brute_force(model, coeffs, shape):
 
 
 @pytest.mark.parametrize("model,coeffs", [("ac", (1.0, 1.0)), ("ch", (1.0, 1.0, 1.0)),
-                                          ("gs", (0.2, 0.1, 0.04, 0.06))])
+                                          ("gs", (0.2, 0.1, 0.04, 0.06)),
+                                          ("c", (1.0, 1.0, 1.0, 1.0, 1.0))])
 def test_step_commutes_with_grid_symmetries(model, coeffs):
     # Periodic translations, axis reflections and the transpose of a square grid commute
     # with the step: catches a wrong axis, sign or transposed operand.
     rng = np.random.default_rng(23)
-    nf = 2 if model == "gs" else 1
+    nf = 2 if model in ("gs", "c") else 1
     fields = tuple(rng.uniform(0.0, 1.0, (12, 12)) for _ in range(nf))
     base = oracle.euler_step(model, fields, coeffs, 0.01)
     for op in (lambda a: np.roll(a, 3, axis=0), lambda a: np.roll(a, -5, axis=1),
@@ -157,3 +168,59 @@ def test_step_commutes_with_grid_symmetries(model, coeffs):
         moved = oracle.euler_step(model, tuple(op(f) for f in fields), coeffs, 0.01)
         for b, m in zip(base, moved):
             np.testing.assert_allclose(m, op(b), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------------ Model C
+
+@pytest.mark.parametrize("shape,m_", [((16, 12), (2, 3)), ((8, 6, 10), (1, 1, 2))])
+def test_model_c_uncoupled_linear_closed_forms(shape, m_):
+    # c2 = c4 = c5 = 0: psi modes grow by 1 + dt (lam + c1), m modes by 1 + dt (-lam^2 - c3 lam)
+    mode, lam = _mode(shape, m_, 1.0, amp=0.1)
+    c1, c3, dt, n = 0.7, 0.9, 0.004, 40
+    psi, m = oracle.run("c", (mode, 0.5 * mode), (c1, 0.0, c3, 0.0, 0.0), dt, n)
+    np.testing.assert_allclose(psi, (1 + dt * (lam + c1)) ** n * mode, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(m, (1 + dt * (-lam * lam - c3 * lam)) ** n * 0.5 * mode, rtol=0,
+                               atol=1e-12)
+
+
+def test_model_c_reduces_to_models_a_and_b_without_coupling():
+    rng = np.random.default_rng(31)
+    psi, m = rng.uniform(-0.5, 0.5, (12, 10)), rng.uniform(-0.5, 0.5, (12, 10))
+    fp, fm = oracle.rhs_model_c(psi, m, 0.8, 1.3, 0.6, 1.1, 0.0)
+    np.testing.assert_allclose(fp, oracle.rhs_allen_cahn(psi, 0.8, 1.3), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(fm, oracle.rhs_cahn_hilliard(m, 0.6, 1.1, 1.0), rtol=0, atol=1e-13)
+
+
+def test_model_c_conserves_m_and_its_energy_decreases():
+    rng = np.random.default_rng(37)
+    psi, m = rng.uniform(-0.3, 0.3, (32, 32)), rng.uniform(-0.3, 0.3, (32, 32)) + 0.1
+    coeffs = (1.0, 1.0, 1.0, 1.0, 1.0)
+    m0 = oracle.mass(m)
+    e_prev = oracle.energy_model_c(psi, m, *coeffs)
+    x = (psi, m)
+    for _ in range(300):
+        x = oracle.euler_step("c", x, coeffs, 0.005)
+        e = oracle.energy_model_c(*x, *coeffs)
+        assert e <= e_prev + 1e-12 * abs(e_prev)
+        e_prev = e
+    assert abs(oracle.mass(x[1]) - m0) <= 1e-12 * np.abs(m).sum()
+
+
+@pytest.mark.parametrize("shape", [(5, 6), (3, 4, 5)])
+def test_model_c_energy_gradients_by_complex_step(shape):
+    # -dE/dpsi = f_psi and dE/dm = mu_m (whose Laplacian is f_m)
+    rng = np.random.default_rng(41)
+    psi, m = rng.uniform(-0.8, 0.8, shape), rng.uniform(-0.8, 0.8, shape)
+    c = (0.9, 1.2, 0.7, 1.3, 0.6)
+    fp, _ = oracle.rhs_model_c(psi, m, *c)
+    mu = c[3] * m ** 3 - c[2] * m - c[4] * psi ** 2 - oracle.laplacian(m)
+    eps = 1e-30
+    for site in itertools.islice(itertools.product(*[range(n) for n in shape]), 0, None, 4):
+        zp = psi.astype(np.complex128)
+        zp[site] += 1j * eps
+        dpsi = np.imag(oracle.energy_model_c(zp, m, *c)) / eps
+        zm = m.astype(np.complex128)
+        zm[site] += 1j * eps
+        dm = np.imag(oracle.energy_model_c(psi, zm, *c)) / eps
+        assert abs(-dpsi - fp[site]) <= 1e-12 * max(1.0, abs(fp[site]))
+        assert abs(dm - mu[site]) <= 1e-12 * max(1.0, abs(mu[site]))
