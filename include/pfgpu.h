@@ -57,12 +57,16 @@ extern "C" {
 #define PF_MODEL_AC 1 /* Allen-Cahn, 1 field, coeffs {c1, c2}          (Sec. 3, Model A) */
 #define PF_MODEL_CH 2 /* Cahn-Hilliard, 1 field, coeffs {c1, c2, M}    (Sec. 3, Model B) */
 #define PF_MODEL_GS 3 /* Gray-Scott, 2 fields (u, v), coeffs {Du, Dv, F, k}   (Sec. 1) */
+#define PF_MODEL_C 4  /* Model C (eutectic), 2 fields (psi, m), coeffs {c1, c2, c3, c4, c5}:
+                         dpsi/dt = lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
+                         dm/dt = -lap^2 m - lap(c3 m - c4 m^3 + c5 psi^2)   (Sec. 3) */
 
 /* ---------------------------------------------------------------- reductions */
 #define PF_REDUCE_MASS 1   /* h^d * sum_x phi_x of one field                         */
-#define PF_REDUCE_ENERGY 2 /* discrete free energy of field 0 (AC and CH only):
+#define PF_REDUCE_ENERGY 2 /* discrete free energy (AC, CH: of field 0; Model C: of both):
                               h^d sum_x [1/2 sum_i ((phi_{x+e_i}-phi_x)/h)^2
-                                         - c1/2 phi^2 + c2/4 phi^4]                  */
+                                         - c1/2 phi^2 + c2/4 phi^4]; Model C adds
+                              1/2 |grad m|^2 - c3/2 m^2 + c4/4 m^4 - c5 psi^2 m     */
 
 typedef struct pf_grid_s* pf_grid_t;
 typedef struct pf_batch_s* pf_batch_t;
@@ -91,7 +95,8 @@ int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stre
 void pf_destroy(pf_grid_t g);
 
 /* Choose the equation of motion and its coefficients (Sec. 3; see PF_MODEL_*).
- *   coeffs/n_coeffs  AC {c1, c2}, CH {c1, c2, M}, GS {Du, Dv, F, k} (exact count);
+ *   coeffs/n_coeffs  AC {c1, c2}, CH {c1, c2, M}, GS {Du, Dv, F, k},
+ *                    C {c1, c2, c3, c4, c5} (exact count);
  *   dt               time step, > 0;
  *   force            0: reject dt beyond the linear stability bound of forward Euler
  *                    (PF_ERR_UNSTABLE_DT, nothing changed); 1: accept it.
@@ -127,7 +132,7 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out);
 /* Kernel tuning: tile_x, tile_y (2D tile, or xy tile of the 3D z-streaming kernel) and
  * k_steps (temporal-blocking depth, 2D only). 0 for any value = library default.
  * Unsupported combinations are rejected with PF_ERR_INVALID_ARG.
- * Supported: 2D tiles 64x16, 128x16, 32x32, 128x32; k in {1, 2, 4} (CH: {1, 2});
+ * Supported: 2D tiles 64x16, 128x16, 32x32, 128x32; k in {1, 2, 4} (CH, C: {1, 2});
  * 3D tiles 32x16, 64x8 (general kernel, every model and size) and 64x16, 128x8, 128x16
  * (TMA-staged kernel: AC and GS with nx % tile_x == 0 and ny % tile_y == 0); k = 1. */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);

@@ -25,8 +25,9 @@ PF_ERR_TIMEOUT = -7
 PF_MODEL_AC = 1
 PF_MODEL_CH = 2
 PF_MODEL_GS = 3
-MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS}
-MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2}
+PF_MODEL_C = 4
+MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS, "c": PF_MODEL_C}
+MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2, "c": 2}
 
 PF_REDUCE_MASS = 1
 PF_REDUCE_ENERGY = 2

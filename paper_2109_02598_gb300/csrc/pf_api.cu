@@ -38,6 +38,7 @@ int model_fields(int model) {
     case PF_MODEL_AC: return 1;
     case PF_MODEL_CH: return 1;
     case PF_MODEL_GS: return 2;
+    case PF_MODEL_C: return 2;
   }
   return 0;
 }
@@ -47,6 +48,7 @@ int model_ncoeffs(int model) {
     case PF_MODEL_AC: return 2;
     case PF_MODEL_CH: return 3;
     case PF_MODEL_GS: return 4;
+    case PF_MODEL_C: return 5;
   }
   return 0;
 }
@@ -67,6 +69,12 @@ double stable_dt_limit(int model, int dim, double h, const double* c) {
     }
     case PF_MODEL_GS: {
       const double s = std::fmax(c[0], c[1]) * lmax + c[2] + c[3];
+      return s > 0 ? 2.0 / s : INFINITY;
+    }
+    case PF_MODEL_C: {  // the stiffer of the psi (Model A-like) and m (Model B-like) parts
+      const double sa = lmax + std::fmax(0.0, 3.0 * c[1] - c[0]) + 2.0 * std::fabs(c[4]);
+      const double sb = lmax * (lmax + std::fmax(0.0, 3.0 * c[3] - c[2]));
+      const double s = std::fmax(sa, sb);
       return s > 0 ? 2.0 / s : INFINITY;
     }
   }
@@ -92,6 +100,14 @@ ModelParams make_params(int model, const double* c, double dt, double h) {
       m.a1 = (float)c[1];
       m.a2 = (float)c[2];
       m.a3 = (float)(c[2] + c[3]);
+      break;
+    case PF_MODEL_C:
+      m.a0 = (float)c[0];
+      m.a1 = (float)c[1];
+      m.a2 = (float)c[2];
+      m.a3 = (float)c[3];
+      m.a4 = (float)c[4];
+      m.a5 = (float)(2.0 * c[4]);
       break;
   }
   return m;
@@ -412,15 +428,22 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out) {
   if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
   double c1 = 0, c2 = 0;
   if (what == PF_REDUCE_ENERGY) {
-    if (!g->model_set || (g->model != PF_MODEL_AC && g->model != PF_MODEL_CH)) {
-      set_error("energy needs an Allen-Cahn or Cahn-Hilliard model");
+    if (!g->model_set ||
+        (g->model != PF_MODEL_AC && g->model != PF_MODEL_CH && g->model != PF_MODEL_C)) {
+      set_error("energy needs an Allen-Cahn, Cahn-Hilliard or Model C model");
       return PF_ERR_STATE;
     }
     c1 = g->coeffs[0];
     c2 = g->coeffs[1];
   }
-  PF_CUDA_TRY(launch_reduce(what, grid_geom(g), g->buf[g->cur][field], c1, c2, g->h,
-                            g->red_partials, g->red_partials + kReduceBlocks, g->stream));
+  if (what == PF_REDUCE_ENERGY && g->model == PF_MODEL_C) {
+    PF_CUDA_TRY(launch_reduce_energy_c(grid_geom(g), g->buf[g->cur][0], g->buf[g->cur][1],
+                                       g->coeffs, g->h, g->red_partials,
+                                       g->red_partials + kReduceBlocks, g->stream));
+  } else {
+    PF_CUDA_TRY(launch_reduce(what, grid_geom(g), g->buf[g->cur][field], c1, c2, g->h,
+                              g->red_partials, g->red_partials + kReduceBlocks, g->stream));
+  }
   PF_CUDA_TRY(cudaMemcpyAsync(g->red_host, g->red_partials + kReduceBlocks, sizeof(double),
                               cudaMemcpyDeviceToHost, g->stream));
   if (int rc = check_device_error(g)) return rc;

@@ -146,7 +146,7 @@ int tile2d_id(int tx, int ty) {
 }
 
 bool fe2d_supported(int model, int k) {
-  if (model == PF_MODEL_CH) return k == 1 || k == 2;
+  if (model == PF_MODEL_CH || model == PF_MODEL_C) return k == 1 || k == 2;
   return k == 1 || k == 2 || k == 4;
 }
 
@@ -166,6 +166,9 @@ cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs 
     case PF_MODEL_CH:
       if (k == 1) return launch_tile<PF_MODEL_CH, 1>(tile_id, g, in, out, m, s);
       return launch_tile<PF_MODEL_CH, 2>(tile_id, g, in, out, m, s);
+    case PF_MODEL_C:
+      if (k == 1) return launch_tile<PF_MODEL_C, 1>(tile_id, g, in, out, m, s);
+      return launch_tile<PF_MODEL_C, 2>(tile_id, g, in, out, m, s);
   }
   return cudaErrorInvalidValue;
 }

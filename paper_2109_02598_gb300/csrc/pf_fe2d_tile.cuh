@@ -27,7 +27,7 @@ struct Cfg2 {
   static constexpr int HT = TY + 2 * H;        // staged rows
   static constexpr int PL = WS * HT;           // floats per staged field
   static constexpr int NBUF = (K > 1) ? 2 : 1;
-  static constexpr int MU = (MODEL == PF_MODEL_CH) ? PL : 0;
+  static constexpr int MU = (MODEL == PF_MODEL_CH || MODEL == PF_MODEL_C) ? PL : 0;
   static constexpr int SMEM_FLOATS = NF * NBUF * PL + MU;
   static_assert(TX % 4 == 0, "tile width must be a multiple of 4");
 };
@@ -92,8 +92,8 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
     const float* src = sm + (s & 1) * C::NF * PL;
     float* dst = sm + ((s + 1) & 1) * C::NF * PL;
     float* mu = sm + C::NF * C::NBUF * PL;
-    if constexpr (MODEL == PF_MODEL_CH) {
-      // mu on the region one ring wider than this sub-step's phi update
+    if constexpr (MODEL == PF_MODEL_CH || MODEL == PF_MODEL_C) {
+      // mu on the region one ring wider than this sub-step's update
       const int rlo = C::R * s + 1, rhi = C::HT - rlo;
       const int clo = (C::HP - C::H + C::R * s + 1) / 4, chi = (WS - (C::HP - C::H + C::R * s + 1) + 3) / 4;
       const int nch = chi - clo;
@@ -101,11 +101,20 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
         const int rr = i / nch;
         const int r = rlo + rr;
         const int p = r * WS + 4 * (clo + i - rr * nch);
-        const float4 c = *reinterpret_cast<const float4*>(src + p);
-        const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
-        *reinterpret_cast<float4*>(mu + p) =
-            make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
-                        ch_mu(c.w, l.w, m));
+        if constexpr (MODEL == PF_MODEL_CH) {
+          const float4 c = *reinterpret_cast<const float4*>(src + p);
+          const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
+          *reinterpret_cast<float4*>(mu + p) =
+              make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
+                          ch_mu(c.w, l.w, m));
+        } else {  // Model C: chemical potential of m (field 1), coupled to psi (field 0)
+          const float4 ps = *reinterpret_cast<const float4*>(src + p);
+          const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
+          const float4 l = lap2d_x4(src + PL, p, WS, m.inv_h2);
+          *reinterpret_cast<float4*>(mu + p) =
+              make_float4(mc_mu(ps.x, c.x, l.x, m), mc_mu(ps.y, c.y, l.y, m),
+                          mc_mu(ps.z, c.z, l.z, m), mc_mu(ps.w, c.w, l.w, m));
+        }
       }
       __syncthreads();
     }
@@ -130,6 +139,15 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
         const float4 l = lap2d_x4(mu, p, WS, m.inv_h2);
         val[0] = make_float4(ch_update(c.x, l.x, m), ch_update(c.y, l.y, m),
                              ch_update(c.z, l.z, m), ch_update(c.w, l.w, m));
+      } else if constexpr (MODEL == PF_MODEL_C) {
+        const float4 ps = *reinterpret_cast<const float4*>(src + p);
+        const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
+        const float4 lp = lap2d_x4(src, p, WS, m.inv_h2);
+        const float4 lm = lap2d_x4(mu, p, WS, m.inv_h2);
+        mc_update(ps.x, c.x, lp.x, lm.x, m, val[0].x, val[1].x);
+        mc_update(ps.y, c.y, lp.y, lm.y, m, val[0].y, val[1].y);
+        mc_update(ps.z, c.z, lp.z, lm.z, m, val[0].z, val[1].z);
+        mc_update(ps.w, c.w, lp.w, lm.w, m, val[0].w, val[1].w);
       } else {
         const float4 u = *reinterpret_cast<const float4*>(src + p);
         const float4 v = *reinterpret_cast<const float4*>(src + PL + p);

@@ -3,7 +3,8 @@
 // xy plane and a chunk of tz planes; it streams through z keeping a ring of three
 // planes (z-1, z, z+1) with a periodic xy halo in shared memory, so every input value is
 // fetched from HBM once per CTA plus the halo.  Model B keeps three phi planes (halo 2)
-// and three mu planes (halo 1); mu is computed on chip and never stored.
+// and three mu planes (halo 1); mu is computed on chip and never stored.  Model C keeps
+// both of its fields in the phi planes and the chemical potential of m in the mu planes.
 #include "pf_internal.h"
 
 namespace pf {
@@ -24,7 +25,10 @@ struct Cfg3 {
   static constexpr int W1 = TX + 2;
   static constexpr int HT1 = TY + 2;
   static constexpr int PL1 = W1 * HT1;
-  static constexpr int SMEM_FLOATS = 3 * NF * PL + (MODEL == PF_MODEL_CH ? 3 * PL1 : 0);
+  // ring of phi planes: three (z-1, z, z+1), four for Model C, whose psi needs plane z-1
+  // while plane z+2 is already staged for the chemical potential of m
+  static constexpr int NPH = (MODEL == PF_MODEL_C) ? 4 : 3;
+  static constexpr int SMEM_FLOATS = NPH * NF * PL + (R == 2 ? 3 * PL1 : 0);
 };
 
 // Stage plane z (periodic) of every field into ring slot `slot`.
@@ -100,74 +104,96 @@ __global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut ou
   }
 }
 
-// Model B: mu planes computed on chip from phi planes.
-template <int TX, int TY>
-__device__ __forceinline__ void ch_mu_plane(const float* phb, const float* phc,
-                                            const float* pha, float* mu,
-                                            const ModelParams& m) {
-  using C = Cfg3<PF_MODEL_CH, TX, TY>;
+// Model B and Model C: mu planes computed on chip from the staged phi planes (halo 2).
+// Model B: mu = c2 phi^3 - c1 phi - lap phi of its one field.  Model C: the chemical
+// potential of m (field 1), coupled to psi (field 0).
+template <int MODEL, int TX, int TY>
+__device__ __forceinline__ void r2_mu_plane(const float* pb, const float* pc, const float* pa,
+                                            float* mu, const ModelParams& m) {
+  using C = Cfg3<MODEL, TX, TY>;
   constexpr int W = C::W;
+  constexpr int PL = C::PL;
+  constexpr int F = C::NF - 1;  // the field whose chemical potential is needed
   for (int i = threadIdx.x; i < C::PL1; i += kNT3) {
     const int r1 = i / C::W1;
     const int c1 = i - r1 * C::W1;
     const int p = (r1 + 1) * W + (c1 + 1);  // position in the phi plane (halo 2)
-    const float pc = phc[p];
-    const float l = lap3d(pc, phc[p - 1], phc[p + 1], phc[p - W], phc[p + W], phb[p], pha[p],
-                          m.inv_h2);
-    mu[i] = ch_mu(pc, l, m);
+    const float* q = pc + F * PL;
+    const float v = q[p];
+    const float l = lap3d(v, q[p - 1], q[p + 1], q[p - W], q[p + W], pb[F * PL + p],
+                          pa[F * PL + p], m.inv_h2);
+    if constexpr (MODEL == PF_MODEL_CH)
+      mu[i] = ch_mu(v, l, m);
+    else
+      mu[i] = mc_mu(pc[p], v, l, m);
   }
 }
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(kNT3) fe3d_ch_kernel(FieldPtrs in, FieldOut out, Geom g,
+template <int MODEL, int TX, int TY>
+__global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut out, Geom g,
                                                        ModelParams m, int tz) {
-  using C = Cfg3<PF_MODEL_CH, TX, TY>;
+  using C = Cfg3<MODEL, TX, TY>;
+  constexpr int NF = C::NF;
   constexpr int W = C::W;
   constexpr int PL = C::PL;
   constexpr int W1 = C::W1;
   constexpr int PL1 = C::PL1;
   extern __shared__ __align__(16) float sm[];
-  float* ph = sm;           // 3 phi slots, slot(p) = (p - z0 + 6) % 3
-  float* mu = sm + 3 * PL;  // 3 mu slots, same slot rule
+  constexpr int NPH = C::NPH;
+  float* ph = sm;                  // NPH slots of NF phi planes, pslot(p) = (p - z0 + 8) % NPH
+  float* mu = sm + NPH * NF * PL;  // 3 mu slots, slot(p) = (p - z0 + 6) % 3
   const int x0 = blockIdx.x * TX;
   const int y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * tz;
   const int z1 = min(z0 + tz, g.nz);
   auto slot = [&](int p) { return (p - z0 + 6) % 3; };
+  auto pslot = [&](int p) { return (p - z0 + 8) % NPH; };
+  auto plane = [&](int p) { return ph + pslot(p) * NF * PL; };
   // prologue: mu(z0-1) from phi(z0-2..z0), then mu(z0) from phi(z0-1..z0+1)
-  load_plane3d<C>(in, g, x0, y0, z0 - 2, slot(z0 - 2), ph);
-  load_plane3d<C>(in, g, x0, y0, z0 - 1, slot(z0 - 1), ph);
-  load_plane3d<C>(in, g, x0, y0, z0, slot(z0), ph);
+  load_plane3d<C>(in, g, x0, y0, z0 - 2, pslot(z0 - 2), ph);
+  load_plane3d<C>(in, g, x0, y0, z0 - 1, pslot(z0 - 1), ph);
+  load_plane3d<C>(in, g, x0, y0, z0, pslot(z0), ph);
   __syncthreads();
-  ch_mu_plane<TX, TY>(ph + slot(z0 - 2) * PL, ph + slot(z0 - 1) * PL, ph + slot(z0) * PL,
-                      mu + slot(z0 - 1) * PL1, m);
+  r2_mu_plane<MODEL, TX, TY>(plane(z0 - 2), plane(z0 - 1), plane(z0), mu + slot(z0 - 1) * PL1, m);
   __syncthreads();
-  load_plane3d<C>(in, g, x0, y0, z0 + 1, slot(z0 + 1), ph);
+  load_plane3d<C>(in, g, x0, y0, z0 + 1, pslot(z0 + 1), ph);
   __syncthreads();
-  ch_mu_plane<TX, TY>(ph + slot(z0 - 1) * PL, ph + slot(z0) * PL, ph + slot(z0 + 1) * PL,
-                      mu + slot(z0) * PL1, m);
+  r2_mu_plane<MODEL, TX, TY>(plane(z0 - 1), plane(z0), plane(z0 + 1), mu + slot(z0) * PL1, m);
   __syncthreads();
   for (int z = z0; z < z1; ++z) {
-    load_plane3d<C>(in, g, x0, y0, z + 2, slot(z + 2), ph);
+    load_plane3d<C>(in, g, x0, y0, z + 2, pslot(z + 2), ph);
     __syncthreads();
-    ch_mu_plane<TX, TY>(ph + slot(z) * PL, ph + slot(z + 1) * PL, ph + slot(z + 2) * PL,
-                        mu + slot(z + 1) * PL1, m);
+    r2_mu_plane<MODEL, TX, TY>(plane(z), plane(z + 1), plane(z + 2), mu + slot(z + 1) * PL1, m);
     __syncthreads();
     const float* mb = mu + slot(z - 1) * PL1;
     const float* mc = mu + slot(z) * PL1;
     const float* ma = mu + slot(z + 1) * PL1;
-    const float* pc = ph + slot(z) * PL;
+    const float* pb = plane(z - 1);
+    const float* pc = plane(z);
+    const float* pa = plane(z + 1);
     const int64_t zoff = (int64_t)z * g.plane;
     for (int i = threadIdx.x; i < TX * TY; i += kNT3) {
       const int rr = i / TX;
       const int cc = i - rr * TX;
       const int q = (rr + 1) * W1 + (cc + 1);  // mu plane position
+      const int p = (rr + 2) * W + (cc + 2);   // phi plane position
       const float l = lap3d(mc[q], mc[q - 1], mc[q + 1], mc[q - W1], mc[q + W1], mb[q], ma[q],
                             m.inv_h2);
-      const float v = ch_update(pc[(rr + 2) * W + (cc + 2)], l, m);
       const int gx = x0 + cc;
       const int gy = y0 + rr;
-      if (gx < g.nx && gy < g.ny) out.f[0][zoff + (int64_t)gy * g.pitch + gx] = v;
+      if (gx >= g.nx || gy >= g.ny) continue;
+      const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
+      if constexpr (MODEL == PF_MODEL_CH) {
+        out.f[0][off] = ch_update(pc[p], l, m);
+      } else {
+        const float ps = pc[p];
+        const float lp = lap3d(ps, pc[p - 1], pc[p + 1], pc[p - W], pc[p + W], pb[p], pa[p],
+                               m.inv_h2);
+        float psn, mn;
+        mc_update(ps, pc[PL + p], lp, l, m, psn, mn);
+        out.f[0][off] = psn;
+        out.f[1][off] = mn;
+      }
     }
     __syncthreads();
   }
@@ -190,10 +216,10 @@ cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams
   const int bx = (g.nx + TX - 1) / TX, by = (g.ny + TY - 1) / TY;
   const int tz = choose_tz(g, bx * by);
   dim3 grid(bx, by, (g.nz + tz - 1) / tz);
-  if constexpr (MODEL == PF_MODEL_CH) {
-    cudaError_t e = ensure_smem_attr(fe3d_ch_kernel<TX, TY>, smem, &attr_mask);
+  if constexpr (ModelTraits<MODEL>::R == 2) {
+    cudaError_t e = ensure_smem_attr(fe3d_r2_kernel<MODEL, TX, TY>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
-    fe3d_ch_kernel<TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+    fe3d_r2_kernel<MODEL, TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   } else {
     cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
@@ -233,6 +259,7 @@ cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, Fie
     case PF_MODEL_AC: return launch3_tile<PF_MODEL_AC>(tile_id, g, in, out, m, s);
     case PF_MODEL_CH: return launch3_tile<PF_MODEL_CH>(tile_id, g, in, out, m, s);
     case PF_MODEL_GS: return launch3_tile<PF_MODEL_GS>(tile_id, g, in, out, m, s);
+    case PF_MODEL_C: return launch3_tile<PF_MODEL_C>(tile_id, g, in, out, m, s);
   }
   return cudaErrorInvalidValue;
 }

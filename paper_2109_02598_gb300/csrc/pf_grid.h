@@ -56,7 +56,7 @@ struct pf_grid_s {
   float* buf[2][PF_MAX_FIELDS] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int cur = 0;
   int model = 0;
-  double coeffs[4] = {0, 0, 0, 0};
+  double coeffs[5] = {0, 0, 0, 0, 0};
   double dt = 0;
   int model_set = 0;
   pf::ModelParams params{};

@@ -93,5 +93,9 @@ cudaError_t launch_batch_gs2d(int tile_id, int k, const BatchInst* d_insts,
 constexpr int kReduceBlocks = 512;
 cudaError_t launch_reduce(int what, const Geom& g, const float* field, double c1, double c2,
                           double h, double* d_partials, double* d_out, cudaStream_t s);
+// Model C free energy of (psi, m) with coefficients c[0..4] = c1..c5.
+cudaError_t launch_reduce_energy_c(const Geom& g, const float* psi, const float* m,
+                                   const double* c, double h, double* d_partials,
+                                   double* d_out, cudaStream_t s);
 
 }  // namespace pf

@@ -7,6 +7,8 @@
 //   Model A (AC):  f = lap phi + c1 phi - c2 phi^3
 //   Model B (CH):  mu = c2 phi^3 - c1 phi - lap phi,   f = M lap mu
 //   Gray-Scott:    f_u = Du lap u - u v^2 + F (1 - u),  f_v = Dv lap v + u v^2 - (F + k) v
+//   Model C:       f_psi = lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
+//                  mu_m = c4 m^3 - c3 m - c5 psi^2 - lap m,  f_m = lap mu_m
 // Forward Euler (Sec. 2.4.1): x_new = x + dt f(x).
 // Laplacian (Sec. 2.2.2): second-order central, 5 points in 2D and 7 in 3D, evaluated as
 // ((x- - c) + (x+ - c)) + ((y- - c) + (y+ - c)) [+ ((z- - c) + (z+ - c))], times 1/h^2.
@@ -22,8 +24,9 @@ namespace pf {
 //   AC: a0 = c1, a1 = c2
 //   CH: a0 = c1, a1 = c2, a2 = dt * M
 //   GS: a0 = Du, a1 = Dv, a2 = F, a3 = F + k
+//   C:  a0 = c1, a1 = c2, a2 = c3, a3 = c4, a4 = c5, a5 = 2 c5
 struct ModelParams {
-  float a0, a1, a2, a3;
+  float a0, a1, a2, a3, a4, a5;
   float dt;
   float inv_h2;
 };
@@ -44,6 +47,11 @@ template <>
 struct ModelTraits<PF_MODEL_GS> {
   static constexpr int NF = 2;
   static constexpr int R = 1;
+};
+template <>
+struct ModelTraits<PF_MODEL_C> {
+  static constexpr int NF = 2;
+  static constexpr int R = 2;  // m needs the Laplacian of its chemical potential
 };
 
 __device__ __forceinline__ float lap2d(float c, float xm, float xp, float ym, float yp,
@@ -91,6 +99,25 @@ __device__ __forceinline__ void gs_update(float u, float v, float lu, float lv,
   fv = __fmaf_rn(-m.a3, v, fv);
   un = __fmaf_rn(m.dt, fu, u);
   vn = __fmaf_rn(m.dt, fv, v);
+}
+
+// Model C chemical potential of m: c4 m^3 - c3 m - c5 psi^2 - lap m
+__device__ __forceinline__ float mc_mu(float psi, float m, float lap_m, const ModelParams& p) {
+  const float m3 = __fmul_rn(__fmul_rn(m, m), m);
+  float mu = __fmaf_rn(p.a3, m3, -lap_m);
+  mu = __fmaf_rn(-p.a2, m, mu);
+  return __fmaf_rn(-p.a4, __fmul_rn(psi, psi), mu);
+}
+
+// Model C update: psi + dt (lap psi + c1 psi - c2 psi^3 + 2 c5 psi m),  m + dt lap mu_m
+__device__ __forceinline__ void mc_update(float psi, float m, float lap_psi, float lap_mu,
+                                          const ModelParams& p, float& psi_n, float& m_n) {
+  const float p3 = __fmul_rn(__fmul_rn(psi, psi), psi);
+  float f = __fmaf_rn(p.a0, psi, lap_psi);
+  f = __fmaf_rn(-p.a1, p3, f);
+  f = __fmaf_rn(p.a5, __fmul_rn(psi, m), f);
+  psi_n = __fmaf_rn(p.dt, f, psi);
+  m_n = __fmaf_rn(p.dt, lap_mu, m);
 }
 
 // Periodic index: i in [-n, 2n) maps into [0, n); anything else takes the slow modulo

@@ -82,7 +82,8 @@ class Grid:
 
     # ---------------------------------------------------------------- model
     def set_model(self, model: str, coeffs, dt: float, force: bool = False):
-        """model in {"ac", "ch", "gs"}; coeffs AC (c1, c2), CH (c1, c2, M), GS (Du, Dv, F, k)."""
+        """model in {"ac", "ch", "gs", "c"}; coeffs AC (c1, c2), CH (c1, c2, M),
+        GS (Du, Dv, F, k), Model C (c1, c2, c3, c4, c5)."""
         c = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         check(self._lib.pf_set_model(self._h, MODEL_IDS[model], c, len(coeffs), float(dt),
                                      1 if force else 0))

@@ -14,8 +14,10 @@ import synthetic
 
 pytestmark = pytest.mark.gpu
 
-COEFFS = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06)}
-DT = {"ac": 0.05, "ch": 0.01, "gs": 0.5}
+COEFFS = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06),
+          "c": (1.0, 1.0, 1.0, 1.0, 1.0)}
+DT = {"ac": 0.05, "ch": 0.01, "gs": 0.5, "c": 0.005}
+MODELS = ["ac", "ch", "gs", "c"]
 
 
 @pytest.fixture(scope="module")
@@ -34,6 +36,9 @@ def init_fields(model, shape, seed=0):
         return (synthetic.allen_cahn_init(shape, seed=100 + seed, lo=-0.5, hi=0.5),)
     if model == "ch":
         return (synthetic.cahn_hilliard_init(shape, seed=200 + seed, amp=0.3),)
+    if model == "c":
+        return (synthetic.allen_cahn_init(shape, seed=400 + seed, lo=-0.5, hi=0.5),
+                synthetic.cahn_hilliard_init(shape, seed=450 + seed, amp=0.4))
     n_seeds = max(2, int(np.prod(shape)) // 2000)
     return synthetic.gray_scott_init(shape, seed=300 + seed, n_seeds=n_seeds, side=4,
                                      noise=0.05)
@@ -71,7 +76,7 @@ SHAPES_3D = [(9, 20, 70), (4, 4, 4), (3, 17, 33), (17, 5, 130), (5, 48, 192), (1
              (2, 32, 128)]
 
 
-@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+@pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D)
 def test_single_step_parity(pf, model, shape):
     x0 = init_fields(model, shape)
@@ -81,7 +86,7 @@ def test_single_step_parity(pf, model, shape):
     assert rel_linf(got, ref) <= 1e-6
 
 
-@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+@pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("shape", [(37, 150), (6, 11, 40)])
 def test_twenty_steps_parity(pf, model, shape):
     x0 = init_fields(model, shape, seed=1)
@@ -90,18 +95,18 @@ def test_twenty_steps_parity(pf, model, shape):
     assert rel_linf(got, ref) <= 2e-5
 
 
-@pytest.mark.parametrize("model", ["ac", "ch", "gs"])
+@pytest.mark.parametrize("model", MODELS)
 def test_tiles_and_temporal_blocking_are_bitwise_identical(pf, model):
     x0 = init_fields(model, (70, 200), seed=2)
     base = gpu_run(pf, model, x0, 12, tuning=(64, 16, 1))
-    ks = (1, 2) if model == "ch" else (1, 2, 4)
+    ks = (1, 2) if model in ("ch", "c") else (1, 2, 4)
     for tile in [(64, 16), (128, 16), (32, 32), (128, 32)]:
         for k in ks:
             got = gpu_run(pf, model, x0, 12, tuning=(tile[0], tile[1], k))
             for a, b in zip(base, got):
                 assert np.array_equal(a, b), (tile, k)
     # n not a multiple of k: remainder launches with smaller k
-    got = gpu_run(pf, model, x0, 12, tuning=(128, 16, 2 if model == "ch" else 4))
+    got = gpu_run(pf, model, x0, 12, tuning=(128, 16, 2 if model in ("ch", "c") else 4))
     for a, b in zip(base, got):
         assert np.array_equal(a, b)
     # 3D tiles: general kernel on a ragged grid
@@ -113,7 +118,7 @@ def test_tiles_and_temporal_blocking_are_bitwise_identical(pf, model):
     # 3D tiles on a grid the TMA kernel accepts: general and TMA kernels agree bitwise
     y1 = init_fields(model, (12, 32, 128), seed=4)
     b3 = gpu_run(pf, model, y1, 7, tuning=(32, 16, 1))
-    tiles = [(64, 8)] + ([] if model == "ch" else [(64, 16), (128, 8), (128, 16)])
+    tiles = [(64, 8)] + ([] if model in ("ch", "c") else [(64, 16), (128, 8), (128, 16)])
     for t in tiles:
         got = gpu_run(pf, model, y1, 7, tuning=(t[0], t[1], 1))
         for a, b in zip(b3, got):
@@ -293,3 +298,26 @@ def test_errors_are_reported(pf):
     with pytest.raises(PfError, match="not finite"):
         g.mass()
     g.close()
+
+
+# ---------------------------------------------------------------- Model C (eutectic)
+
+@pytest.mark.parametrize("shape", [(96, 80), (16, 24, 20)])
+def test_model_c_invariants_and_energy(pf, shape):
+    x0 = init_fields("c", shape, seed=11)
+    g = pf.Grid(shape, 2).set_model("c", COEFFS["c"], DT["c"])
+    g.write_fields(x0)
+    m0 = g.mass(1)
+    e0 = g.energy()
+    assert abs(e0 - oracle.energy_model_c(*x0, *COEFFS["c"])) <= 1e-10 * abs(e0)
+    e_prev = e0
+    for _ in range(20):
+        g.step(10)
+        e = g.energy()
+        assert e <= e_prev + 1e-6 * abs(e_prev)
+        e_prev = e
+    assert abs(g.mass(1) - m0) / np.prod(shape) <= 1e-6
+    got = g.read_fields()
+    g.close()
+    ref = oracle.run("c", x0, COEFFS["c"], DT["c"], 200)
+    assert rel_l2(got, ref) <= 1e-4
