@@ -371,6 +371,34 @@ def companions(stream, hbm):
             out[name] = {"steps": steps, "glups": sites * steps / (ms * 1e-3) / 1e9,
                          "tuning": list(t)}
             g.close()
+        # ---- the paper's performance table (Sec. 3.1) with the forward-Euler solver:
+        # 10^4 steps of Models A and C; device time and end to end (host in/out)
+        rows = []
+        for case in synthetic.PAPER_TABLE:
+            nsteps = synthetic.PAPER_TABLE_STEPS
+            x0 = synthetic.paper_timing_init(case["model"], case["shape"])
+            g = pf.Grid(case["shape"], len(x0), stream=stream).set_model(
+                case["model"], case["coeffs"], case["dt"])
+            g.write_fields(x0)
+            t = g.autotune(3)
+            g.step(nsteps)  # records the graph
+            dev_ms = _time(stream, lambda: g.step(nsteps))
+            t0 = time.perf_counter()
+            g.write_fields(x0)
+            g.step(nsteps)
+            g.read_fields()
+            e2e_s = time.perf_counter() - t0
+            sites = int(np.prod(case["shape"]))
+            rows.append({"model": "A" if case["model"] == "ac" else "C",
+                         "shape": "x".join(str(v) for v in case["shape"][::-1]),
+                         "steps": nsteps, "device_s": dev_ms / 1e3, "e2e_s": e2e_s,
+                         "glups": sites * nsteps / (dev_ms * 1e-3) / 1e9, "tuning": list(t),
+                         "paper_best_cpu_s": case["paper_best_s"]})
+            g.close()
+        out["paper_table_forward_euler"] = {
+            "rows": rows,
+            "note": "paper times are whole-program runs of its semi-implicit spectral solver "
+                    "on 2016-2017 desktop CPUs (context only)"}
     return out
 
 

@@ -200,10 +200,10 @@ __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut ou
 }
 
 int choose_tz(const Geom& g, int tiles_xy) {
-  // enough CTAs for several waves on 152 SMs, but chunks long enough that the two
-  // extra prologue planes stay a small fraction
+  // enough CTAs for several waves on 152 SMs; small grids take short chunks (down to 4
+  // planes) and accept the prologue planes they re-read, large grids keep long chunks
   int tz = g.nz;
-  while (tz > 16 && (int64_t)tiles_xy * ((g.nz + tz - 1) / tz) < 4 * 152) tz = (tz + 1) / 2;
+  while (tz > 4 && (int64_t)tiles_xy * ((g.nz + tz - 1) / tz) < 4 * 152) tz = (tz + 1) / 2;
   return tz;
 }
 

@@ -223,9 +223,9 @@ cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out, cudaS
   const int tiles_y = g.ny / TY;
   const long long ncols = (long long)tiles_x * tiles_y;
   const long long slots = (long long)sms * occ;
-  // as many z-chunks as keep every column of a chunk resident at once, chunks >= 4 planes
+  // as many z-chunks as keep every column of a chunk resident at once, chunks >= 2 planes
   long long nchunks = slots / ncols;
-  if (nchunks > g.nz / 4) nchunks = g.nz / 4;
+  if (nchunks > g.nz / 2) nchunks = g.nz / 2;
   if (nchunks < 1) nchunks = 1;
   const int chunk_len = (int)((g.nz + nchunks - 1) / nchunks);
   nchunks = (g.nz + chunk_len - 1) / chunk_len;

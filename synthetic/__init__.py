@@ -130,6 +130,31 @@ def batch_instance_init(side: int, index: int, seed: int = 4):
     return gray_scott_init((side, side), seed=seed * 1_000_003 + index + 1, n_seeds=n_seeds)
 
 
+def paper_timing_init(model: str, shape, seed: int = 6):
+    """Fields seeded uniformly in [-1, 1] (the paper's initial conditions for Models A-C,
+    Sec. 3): one field for Model A, (psi, m) for Model C."""
+    n = int(np.prod(shape))
+    f0 = uniform(seed, 30, n, -1.0, 1.0).reshape(shape).astype(np.float32)
+    if model == "ac":
+        return (f0,)
+    return (f0, uniform(seed, 31, n, -1.0, 1.0).reshape(shape).astype(np.float32))
+
+
+# The paper's performance workloads (Sec. 3.1 table), run here with the forward-Euler
+# solver: Models A and C on 128^2, 512^2 and 64^3 for 10^4 iterations.  `paper_best_s` is
+# the fastest whole-program time the paper reports for that case (min over its three CPUs,
+# semi-implicit spectral solver) -- context, not a like-for-like target.
+PAPER_TABLE = [
+    dict(model="ac", shape=(128, 128), coeffs=(1.0, 1.0), dt=0.05, paper_best_s=1.7),
+    dict(model="ac", shape=(512, 512), coeffs=(1.0, 1.0), dt=0.05, paper_best_s=32.6),
+    dict(model="ac", shape=(64, 64, 64), coeffs=(1.0, 1.0), dt=0.05, paper_best_s=31.1),
+    dict(model="c", shape=(128, 128), coeffs=(1.0,) * 5, dt=0.005, paper_best_s=4.1),
+    dict(model="c", shape=(512, 512), coeffs=(1.0,) * 5, dt=0.005, paper_best_s=102.8),
+    dict(model="c", shape=(64, 64, 64), coeffs=(1.0,) * 5, dt=0.005, paper_best_s=96.7),
+]
+PAPER_TABLE_STEPS = 10000
+
+
 # Concrete workloads: the five configurations the measurements use.
 WORKLOADS = {
     "ac2d_128": dict(model="ac", shape=(128, 128), h=1.0, dt=0.05, coeffs=(1.0, 1.0), steps=1000),
