@@ -124,6 +124,8 @@ Geom grid_geom(const pf_grid_s* g) {
   return q;
 }
 
+bool tile_supported(pf_grid_s* g, int tile, int k);
+
 // Turn the requested tuning (or the defaults) into the tuning in effect for the current
 // model and grid.
 int resolve_tuning(pf_grid_s* g) {
@@ -141,19 +143,34 @@ int resolve_tuning(pf_grid_s* g) {
         if (fe3d_tma_supported(g->model, pref[i], grid_geom(g))) def = kFirstTmaTile3D + pref[i];
     }
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
-    if (g->tile >= kFirstTmaTile3D &&
-        !(g->model_set && fe3d_tma_supported(g->model, g->tile - kFirstTmaTile3D, grid_geom(g))))
+    g->k = g->req_k > 0 ? g->req_k : 1;
+    if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
       g->tile = def;
-    g->k = 1;
+      g->k = 1;
+    }
   }
   return PF_OK;
 }
 
 bool tile_supported(pf_grid_s* g, int tile, int k) {
   if (g->dim == 2) return fe2d_supported(g->model, k);
+  int tx, ty;
+  tile3d_shape(tile, &tx, &ty);
+  if (k == 2) return fe3d_tb2_supported(g->model, tx, ty, grid_geom(g));
   if (k != 1) return false;
   if (tile < kFirstTmaTile3D) return true;
   return fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g));
+}
+
+// The depth-1 kernel used for the remainder of a depth-2 launch plan: the tile itself if it
+// has a depth-1 form, else the fastest depth-1 TMA tile that divides the grid, else the
+// general kernel (every path gives the same result bit for bit).
+int k1_tile(pf_grid_s* g, int tile) {
+  if (tile_supported(g, tile, 1)) return tile;
+  static const int pref[3] = {2, 0, 1};
+  for (int i = 0; i < 3; ++i)
+    if (fe3d_tma_supported(g->model, pref[i], grid_geom(g))) return kFirstTmaTile3D + pref[i];
+  return 0;
 }
 
 // A kernel that gave up on a bounded wait leaves a flag; report it (and clear it).
@@ -169,6 +186,8 @@ int check_device_error(pf_grid_s* g) {
   return PF_OK;
 }
 
+int k1_tile(pf_grid_s* g, int tile);
+
 // One launch advancing `k` steps from buffer `src` into buffer `dst`.
 cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStream_t st) {
   FieldPtrs in{};
@@ -179,6 +198,12 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
   }
   const Geom q = grid_geom(g);
   if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, st);
+  if (k == 2) {
+    int tx, ty;
+    tile3d_shape(tile, &tx, &ty);
+    return launch_fe3d_tb2(g, tx, src, dst, st);
+  }
+  tile = k1_tile(g, tile);
   if (tile >= kFirstTmaTile3D) return launch_fe3d_tma(g, tile - kFirstTmaTile3D, src, dst, st);
   return launch_fe3d(g->model, tile, q, in, out, g->params, st);
 }
@@ -468,13 +493,19 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (tile < 0) return invalid("unsupported 3D tile %dx%d", tile_x, tile_y);
   }
   if (k_steps < 0) return invalid("k_steps must be >= 0");
-  if (g->dim == 3 && k_steps > 1) return invalid("3D grids support k = 1 only");
+  if (g->dim == 3 && k_steps > 2) return invalid("3D grids support k = 1 and 2");
+  if (g->dim == 3 && k_steps == 2) {
+    int tx = tile_x, ty = tile_y;
+    if (tile < 0) return invalid("k = 2 in 3D needs an explicit tile (nx x 8, nx = 128 or 256)");
+    if (!(g->model_set && fe3d_tb2_supported(g->model, tx, ty, grid_geom(g))))
+      return invalid("3D k = 2 needs an AC/GS model, tile nx x 8 with nx = 128 or 256, ny %% 8 == 0");
+  }
   if (k_steps > 0 && g->dim == 2) {
     const int model = g->model_set ? g->model : PF_MODEL_AC;
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
   }
-  if (g->dim == 3 && tile >= kFirstTmaTile3D &&
+  if (g->dim == 3 && k_steps != 2 && tile >= kFirstTmaTile3D &&
       !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g))))
     return invalid("3D tile %dx%d needs an AC/GS model and nx %% %d == 0, ny %% %d == 0",
                    tile_x, tile_y, tile_x, tile_y);

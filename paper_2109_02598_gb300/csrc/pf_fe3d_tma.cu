@@ -240,6 +240,7 @@ cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out, cudaS
 
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g) {
   if (model != PF_MODEL_AC && model != PF_MODEL_GS) return false;
+  if (tma_tile < 0 || tma_tile >= kNumTmaTiles3D) return false;
   int tx, ty;
   tma3d_tile_shape(tma_tile, &tx, &ty);
   return g.nx % tx == 0 && g.ny % ty == 0;

@@ -23,6 +23,19 @@ struct TmaCache {
   Tma3dMaps maps[2];
 };
 
+// TMA descriptors of the depth-2 3D kernel: a two-row halo box and the 8-row interior box,
+// both spanning the whole x-row, per field.
+struct Tb2Maps {
+  CUtensorMap row2[PF_MAX_FIELDS];
+  CUtensorMap inner[PF_MAX_FIELDS];
+};
+
+struct Tb2Cache {
+  int width = -1;
+  bool valid[2] = {false, false};
+  Tb2Maps maps[2];
+};
+
 constexpr uint32_t kGridMagic = 0x50464744u;  // "PFGD"
 
 struct AdjointState {
@@ -68,6 +81,7 @@ struct pf_grid_s {
   double* red_host = nullptr;      // pinned
   pf::AdjointState adj;
   pf::TmaCache tma;
+  pf::Tb2Cache tb2;
   int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
   // CUDA-graph cache of pf_step: a few recorded launch sequences, keyed by
   // (steps, tile, k, starting buffer), least recently used replaced first
@@ -100,4 +114,8 @@ void tma3d_tile_shape(int tma_tile, int* tx, int* ty);
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g);
 cudaError_t tma3d_maps(pf_grid_s* g, int tma_tile, int buf);
 cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst, cudaStream_t st);
+
+// ---- 3D depth-2 kernel (AC, GS; full x-rows of 128 or 256, 8-row tiles)
+bool fe3d_tb2_supported(int model, int tx, int ty, const Geom& g);
+cudaError_t launch_fe3d_tb2(pf_grid_s* g, int tx, int src, int dst, cudaStream_t st);
 }  // namespace pf

@@ -64,8 +64,9 @@ cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs 
 
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
-//           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0).
-constexpr int kNumTiles3D = 5;
+//           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);
+//           with k = 2: 3 = 128x8 and 5 = 256x8 (depth-2 TMA kernel, AC/GS, nx == TX).
+constexpr int kNumTiles3D = 6;
 constexpr int kFirstTmaTile3D = 2;
 void tile3d_shape(int tile_id, int* tx, int* ty);
 int tile3d_id(int tx, int ty);

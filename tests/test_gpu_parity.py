@@ -145,6 +145,35 @@ def test_recorded_step_graphs_follow_model_and_tuning_changes(pf, shape):
     assert rel_linf((got,), ref) <= 5e-5
 
 
+@pytest.mark.parametrize("model", ["ac", "gs"])
+@pytest.mark.parametrize("shape,tile", [((12, 32, 128), (128, 8)), ((6, 16, 256), (256, 8)),
+                                        ((9, 40, 128), (128, 8))])
+def test_depth2_3d_kernel_is_bitwise_depth1(pf, model, shape, tile):
+    # two time steps per pass (temporal blocking in 3D); odd step counts end with a
+    # depth-1 launch; every result equals the depth-1 kernels' bit for bit
+    x0 = init_fields(model, shape, seed=12)
+    for n in (8, 7, 1):
+        base = gpu_run(pf, model, x0, n, tuning=(32, 16, 1))
+        got = gpu_run(pf, model, x0, n, tuning=(tile[0], tile[1], 2))
+        for a, b in zip(base, got):
+            assert np.array_equal(a, b), (n, tile)
+    ref = oracle.run(model, x0, COEFFS[model], DT[model], 8)
+    got = gpu_run(pf, model, x0, 8, tuning=(tile[0], tile[1], 2))
+    assert rel_linf(got, ref) <= 1e-5
+
+
+def test_depth2_3d_rejected_where_unsupported(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((8, 16, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
+    with pytest.raises(PfError):
+        g.set_tuning(128, 8, 2)  # nx != 128
+    g.close()
+    h = pf.Grid((8, 16, 128), 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    with pytest.raises(PfError):
+        h.set_tuning(128, 8, 2)  # no depth-2 kernel for Model B
+    h.close()
+
+
 def test_tma_tile_rejected_when_grid_does_not_divide(pf):
     from paper_2109_02598_gb300 import PfError
     g = pf.Grid((8, 20, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
