@@ -36,7 +36,9 @@ BYTES_PER_LUP = {"gs": 16.0, "ac": 8.0, "ch": 8.0}  # k = 1: read + write every 
 TMA_TILES = {(64, 16), (128, 8), (128, 16)}
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now
 # (profiles/fe3d_tma_gs3d_256.md); reported only for that kernel and tile.
-PROFILED_TRAFFIC = {("fe3d_tma_kernel", 128, 16): 218.37e6, ("fe3d_tma_kernel", 64, 16): 218.73e6}
+PROFILED_TRAFFIC = {("fe3d_tma_kernel", 128, 16, 1): 218.37e6,
+                    ("fe3d_tma_kernel", 64, 16, 1): 218.73e6,
+                    ("fe3d_tb2_kernel", 256, 8, 2): 220.53e6}
 
 
 def _peaks():
@@ -251,12 +253,20 @@ def run_gpu(args, rank, world, local):
     if rank != 0:
         return
     hbm, peak_kind = _peaks()
+    if tuning[2] == 2:
+        kernel_name = "fe3d_tb2_kernel (TMA-staged z-streaming, 2 time steps per pass, 7-point GS)"
+    elif tuple(tuning[:2]) in TMA_TILES:
+        kernel_name = "fe3d_tma_kernel (TMA-staged z-streaming, 7-point GS)"
+    else:
+        kernel_name = "fe3d_r1_kernel (general z-streaming, 7-point GS)"
     n_launch = args.steps * launches_per_step
     lups = sites * S * args.steps * world
     value = lups / (ms * 1e-3) / 1e9
-    launch_ms = ms / n_launch
+    launch_ms = ms / n_launch  # every launch of the plan does k steps (S is a multiple of k)
     k = tuning[2]
-    alg_bytes = BYTES_PER_LUP[w["model"]] * sites  # per launch: every field read and written once
+    # per launch: k steps of every site at the k = 1 algorithmic 16 B/LUP (the figure can
+    # exceed the HBM peak when k > 1, since a depth-k launch moves each field once for k steps)
+    alg_bytes = BYTES_PER_LUP[w["model"]] * sites * k
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -272,12 +282,12 @@ def run_gpu(args, rank, world, local):
                      "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback",
                      "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": PROFILED_TRAFFIC.get(("fe3d_tma_kernel",) + tuple(tuning[:2])),
+                     "traffic": PROFILED_TRAFFIC.get((kernel_name.split()[0],) + tuple(tuning)),
                      "traffic_note": "ncu dram__bytes_read+write per launch, 1 capture; writes "
                                      "still dirty in L2 at kernel end are not counted",
-                     "kernel": ("fe3d_tma_kernel (TMA-staged z-streaming, 7-point GS)"
-                                if tuple(tuning[:2]) in TMA_TILES else
-                                "fe3d_r1_kernel (general z-streaming, 7-point GS)"),
+                     "kernel": kernel_name,
+                     "bytes_convention": "k=1 algorithmic 16 B per lattice-site update x sites "
+                                         "x k steps per launch",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms},
         "e2e": {"value": sites * S * args.steps * world / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(a.nbytes for a in x0)),
