@@ -218,6 +218,45 @@ def gray_scott_adjoint(u0, v0, coeffs, dt, n_steps, dLdu_N, dLdv_N, h=1.0):
     return a, b, g
 
 
+def allen_cahn_adjoint_step(phi, lam, c1, c2, dt, h=1.0):
+    """Reverse step of x' = x + dt (lap x + c1 x - c2 x^3) at x = phi^n, lam = lambda^{n+1}:
+    lambda^n = lam + dt (lap lam + (c1 - 3 c2 phi^2) lam); gradient terms for (c1, c2)."""
+    phi, lam = _f64(phi), _f64(lam)
+    lam_new = lam + dt * (laplacian(lam, h) + (c1 - 3.0 * c2 * phi * phi) * lam)
+    g = np.array([dt * float((lam * phi).sum()), -dt * float((lam * phi ** 3).sum())])
+    return lam_new, g
+
+
+def cahn_hilliard_adjoint_step(phi, lam, c1, c2, M, dt, h=1.0):
+    """Reverse step of x' = x + dt M lap mu(x), mu = c2 x^3 - c1 x - lap x, at x = phi^n:
+    with w = lap lam, lambda^n = lam + dt M [(3 c2 phi^2 - c1) w - lap w] (lap symmetric);
+    gradient terms for (c1, c2, M)."""
+    phi, lam = _f64(phi), _f64(lam)
+    w = laplacian(lam, h)
+    lam_new = lam + dt * M * ((3.0 * c2 * phi * phi - c1) * w - laplacian(w, h))
+    mu = chemical_potential(phi, c1, c2, h)
+    g = np.array([-dt * M * float((w * phi).sum()), dt * M * float((w * phi ** 3).sum()),
+                  dt * float((w * mu).sum())])
+    return lam_new, g
+
+
+def phase_field_adjoint(model, phi0, coeffs, dt, n_steps, dLdphi_N, h=1.0):
+    """dL/dphi0 and dL/dcoeffs of a final-state loss through n forward-Euler steps of Model A
+    ("ac", coeffs (c1, c2)) or Model B ("ch", coeffs (c1, c2, M)); stores the trajectory."""
+    traj = [_f64(phi0)]
+    for _ in range(int(n_steps)):
+        traj.append(euler_step(model, (traj[-1],), coeffs, dt, h)[0])
+    lam = _f64(dLdphi_N)
+    g = np.zeros(len(coeffs))
+    for n in range(int(n_steps) - 1, -1, -1):
+        if model == "ac":
+            lam, gn = allen_cahn_adjoint_step(traj[n], lam, *coeffs, dt, h)
+        else:
+            lam, gn = cahn_hilliard_adjoint_step(traj[n], lam, *coeffs, dt, h)
+        g += gn
+    return lam, g
+
+
 def gray_scott_final_and_loss(u0, v0, coeffs, dt, n_steps, u_target, v_target, h=1.0):
     """Forward run then loss; returns (u_N, v_N, L)."""
     uN, vN = run("gs", (u0, v0), coeffs, dt, n_steps, h)

@@ -124,3 +124,72 @@ def test_adjoint_vs_central_differences(adjoint_32):
         fd = (fp - fm) / (2 * eps)
         ad = (d["gu0"] * du).sum() + (d["gv0"] * dv).sum()
         assert abs(ad - fd) <= 1e-6 * max(1e-3, abs(fd)), (ad, fd)
+
+
+# ------------------------------------------------------------ Models A and B (c1, c2, M)
+
+PF_CASES = [("ac", (0.9, 1.2), 0.02), ("ch", (0.8, 1.1, 0.7), 0.004)]
+
+
+@pytest.mark.parametrize("model,coeffs,dt", PF_CASES)
+def test_phase_field_adjoint_step_is_jacobian_transpose(model, coeffs, dt):
+    rng = np.random.default_rng(5)
+    shape = (5, 6)
+    phi = rng.uniform(-0.9, 0.9, shape)
+    lam = rng.standard_normal(shape)
+    n = phi.size
+    J = np.zeros((n, n))
+    eps = 1e-30
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        out, = oracle.euler_step(model, (phi + 1j * eps * e.reshape(shape),), coeffs, dt)
+        J[:, j] = (np.imag(out) / eps).ravel()
+    if model == "ac":
+        got, _ = oracle.allen_cahn_adjoint_step(phi, lam, *coeffs, dt)
+    else:
+        got, _ = oracle.cahn_hilliard_adjoint_step(phi, lam, *coeffs, dt)
+    np.testing.assert_allclose(got.ravel(), J.T @ lam.ravel(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("model,coeffs,dt", PF_CASES)
+def test_phase_field_adjoint_step_parameter_gradient(model, coeffs, dt):
+    rng = np.random.default_rng(6)
+    shape = (7, 6)
+    phi = rng.uniform(-0.9, 0.9, shape)
+    lam = rng.standard_normal(shape)
+    if model == "ac":
+        _, g = oracle.allen_cahn_adjoint_step(phi, lam, *coeffs, dt)
+    else:
+        _, g = oracle.cahn_hilliard_adjoint_step(phi, lam, *coeffs, dt)
+    eps = 1e-30
+    for i in range(len(coeffs)):
+        th = np.array(coeffs, dtype=np.complex128)
+        th[i] += 1j * eps
+        out, = oracle.euler_step(model, (phi,), tuple(th), dt)
+        d = np.imag((lam * out).sum()) / eps
+        assert abs(g[i] - d) <= 1e-12 * max(1.0, abs(d))
+
+
+@pytest.mark.parametrize("model,coeffs,dt", PF_CASES)
+def test_phase_field_adjoint_vs_complex_step_of_the_loop(model, coeffs, dt):
+    # the whole time loop: dL/dtheta and a direction of dL/dphi0 by complex step
+    phi0 = synthetic.allen_cahn_init((24, 20), seed=3, lo=-0.6, hi=0.6).astype(np.float64)
+    target = oracle.run(model, (phi0 * 0.9,), coeffs, dt, 150)[0]
+    n = 150
+    phiN = oracle.run(model, (phi0,), coeffs, dt, n)[0]
+    g0, gth = oracle.phase_field_adjoint(model, phi0, coeffs, dt, n, phiN - target)
+    eps = 1e-30
+
+    def loss(p0, th):
+        p = oracle.run(model, (p0,), th, dt, n)[0]
+        return 0.5 * ((p - target) ** 2).sum()
+
+    for i in range(len(coeffs)):
+        th = np.array(coeffs, dtype=np.complex128)
+        th[i] += 1j * eps
+        d = np.imag(loss(phi0.astype(np.complex128), tuple(th))) / eps
+        assert abs(gth[i] - d) <= 1e-9 * max(1e-6, abs(d)), (i, gth[i], d)
+    dirn = np.random.default_rng(7).standard_normal(phi0.shape)
+    d = np.imag(loss(phi0 + 1j * eps * dirn, coeffs)) / eps
+    assert abs((g0 * dirn).sum() - d) <= 1e-9 * max(1.0, abs(d))
