@@ -200,10 +200,11 @@ int pf_batch_synchronize(pf_batch_t b);
 /* Total lattice sites of all instances, and bytes of one state copy (with padding). */
 int pf_batch_info(pf_batch_t b, int64_t* sites, int64_t* bytes_per_copy);
 
-/* ------------------------------------------------------- adjoint (2D Gray-Scott) */
+/* -------------------------------------- adjoint (2D Gray-Scott, Model A, Model B) */
 
 /* Forward pass that records checkpoints for pf_adj_backward: advances the grid's current
- * state (Gray-Scott model set, 2D grid) by n_steps forward-Euler steps exactly like
+ * state (2D grid; Gray-Scott, Allen-Cahn or Cahn-Hilliard model) by n_steps forward-Euler
+ * steps exactly like
  * pf_step, storing the state every ckpt_interval steps (0 = ceil(sqrt(n_steps))), i.e.
  * sqrt(N) checkpointing of the time loop of Sec. 2.4.1. Allocates the checkpoints
  * (ceil(N/C) states), one segment of C-1 states and the adjoint buffers on first use.
@@ -212,9 +213,11 @@ int pf_batch_info(pf_batch_t b, int64_t* sites, int64_t* bytes_per_copy);
 int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval);
 
 /* Reverse pass of the recorded forward pass (discrete adjoint of the forward-Euler map):
- * given dL/du_N, dL/dv_N (dense float32 [ny][nx]) of any loss of the final state, writes
- * dL/du_0, dL/dv_0 (same layout; either may be NULL) and dtheta[4] = dL/d(Du, Dv, F, k)
- * (host doubles; may be NULL). Arrays are device memory if on_device, else host memory.
+ * given dL/dx_N (dense float32 [ny][nx]: dLdu_N for field 0, dLdv_N for field 1 of
+ * Gray-Scott, NULL for one-field models) of any loss of the final state, writes dL/dx_0
+ * (dLdu0, dLdv0; either may be NULL) and dtheta = dL/dcoeffs in pf_set_model order
+ * (host doubles, may be NULL): Gray-Scott 4 values (Du, Dv, F, k), Model A 2 (c1, c2),
+ * Model B 3 (c1, c2, M). Arrays are device memory if on_device, else host memory.
  * Recomputes each segment from its checkpoint with the forward kernel (bitwise the same
  * states), then applies lambda^n = lambda^{n+1} + dt J(x^n)^T lambda^{n+1} per step;
  * parameter terms are summed in FP64 in a fixed order. The grid's state is not changed.

@@ -6,8 +6,10 @@ The compute path is libpfgpu.so (hand-written CUDA for sm_103a behind the C ABI 
 """
 from ._lib import PfError, load  # noqa: F401
 from .grid import Grid  # noqa: F401
-from .adjoint import GrayScottAdjoint, adjoint_backward, adjoint_forward  # noqa: F401
+from .adjoint import (GrayScottAdjoint, PhaseFieldAdjoint, adjoint_backward,  # noqa: F401
+                      adjoint_forward)
 from .batch import Batch, shard_instances  # noqa: F401
 
-__all__ = ["Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PfError", "adjoint_backward",
+__all__ = ["Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PhaseFieldAdjoint", "PfError",
+           "adjoint_backward",
            "adjoint_forward", "load"]

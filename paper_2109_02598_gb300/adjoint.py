@@ -1,10 +1,12 @@
-"""Gradients of a final-state loss through the forward-Euler Gray-Scott time loop.
+"""Gradients of a final-state loss through the forward-Euler time loop (2D grids).
 
-``GrayScottAdjoint`` is a ``torch.autograd.Function`` over the library's adjoint entry points
-(``pf_adj_forward`` / ``pf_adj_backward`` in include/pfgpu.h): the forward pass advances
-(u0, v0) by n steps with sqrt(N) checkpointing, the backward pass runs the hand-written
-adjoint kernel and returns dL/du0, dL/dv0 and dL/d(Du, Dv, F, k).  Argument marshalling
-only; all arithmetic runs in libpfgpu's kernels.
+``GrayScottAdjoint`` and ``PhaseFieldAdjoint`` are ``torch.autograd.Function`` wrappers over
+the library's adjoint entry points (``pf_adj_forward`` / ``pf_adj_backward`` in
+include/pfgpu.h): the forward pass advances the initial fields by n steps with sqrt(N)
+checkpointing, the backward pass runs the hand-written adjoint kernels and returns the
+gradient with respect to the initial fields and the model coefficients -- Gray-Scott
+(Du, Dv, F, k), Model A (c1, c2), Model B (c1, c2, mobility M).  Argument marshalling only;
+all arithmetic runs in libpfgpu's kernels.
 """
 from __future__ import annotations
 
@@ -20,19 +22,26 @@ def adjoint_forward(grid: Grid, n_steps: int, ckpt_interval: int = 0):
     check(grid._lib.pf_adj_forward(grid.handle, int(n_steps), int(ckpt_interval)))
 
 
-def adjoint_backward(grid: Grid, dLdu_N, dLdv_N):
-    """pf_adj_backward with CUDA tensors; returns (dL/du0, dL/dv0, [dL/dDu, dDv, dF, dk])."""
+def adjoint_backward(grid: Grid, dLdu_N, dLdv_N=None):
+    """pf_adj_backward with CUDA tensors.
+
+    Returns (dL/dx0 of field 0, of field 1 or None, [dL/dcoeff, ...]) with the coefficients
+    in ``set_model`` order.
+    """
     torch = _torch()
     gu = dLdu_N.detach().to(torch.float32).contiguous()
-    gv = dLdv_N.detach().to(torch.float32).contiguous()
     du0 = torch.empty_like(gu)
-    dv0 = torch.empty_like(gv)
+    gv = dv0 = None
+    if grid.n_fields == 2:
+        gv = dLdv_N.detach().to(torch.float32).contiguous()
+        dv0 = torch.empty_like(gv)
     dth = (ctypes.c_double * 4)()
     check(grid._lib.pf_adj_backward(grid.handle, ctypes.c_void_p(gu.data_ptr()),
-                                    ctypes.c_void_p(gv.data_ptr()), 1,
+                                    ctypes.c_void_p(gv.data_ptr() if gv is not None else None), 1,
                                     ctypes.c_void_p(du0.data_ptr()),
-                                    ctypes.c_void_p(dv0.data_ptr()), dth))
-    return du0, dv0, list(dth)
+                                    ctypes.c_void_p(dv0.data_ptr() if dv0 is not None else None),
+                                    dth))
+    return du0, dv0, list(dth)[:len(grid.coeffs)]
 
 
 class GrayScottAdjoint:
@@ -86,4 +95,54 @@ class GrayScottAdjoint:
     def apply(cls, u0, v0, theta, n_steps: int, dt: float, h: float = 1.0,
               ckpt_interval: int = 0):
         return cls._function().apply(u0, v0, theta, int(n_steps), float(dt), float(h),
+                                     int(ckpt_interval))
+
+
+class PhaseFieldAdjoint:
+    """``apply(phi0, theta, model, n_steps, dt, h=1.0, ckpt_interval=0) -> phi_N`` for
+    Model A (``"ac"``, theta = (c1, c2)) or Model B (``"ch"``, theta = (c1, c2, M)).
+
+    Gradients flow to phi0 and theta (including the mobility M of Model B).
+    """
+
+    _fn = None
+
+    @classmethod
+    def _function(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, phi0, theta, model, n_steps, dt, h, ckpt_interval):
+                    grid = Grid(tuple(phi0.shape), 1, h)
+                    grid.set_model(model, [float(t) for t in theta.detach().cpu().tolist()], dt)
+                    grid.write_field(0, phi0)
+                    adjoint_forward(grid, n_steps, ckpt_interval)
+                    out = grid.read_field(0, device=True)
+                    grid.synchronize()
+                    ctx.grid = grid
+                    ctx.theta_meta = (theta.dtype, theta.device)
+                    return out
+
+                @staticmethod
+                def backward(ctx, g):
+                    torch = _torch()
+                    grid = ctx.grid
+                    d0, _, dth = adjoint_backward(grid, g)
+                    dtype, device = ctx.theta_meta
+                    grid.close()
+                    ctx.grid = None
+                    return (d0, torch.tensor(dth, dtype=dtype, device=device),
+                            None, None, None, None, None)
+
+            cls._fn = _Fn
+        return cls._fn
+
+    @classmethod
+    def apply(cls, phi0, theta, model: str, n_steps: int, dt: float, h: float = 1.0,
+              ckpt_interval: int = 0):
+        if model not in ("ac", "ch"):
+            raise ValueError("PhaseFieldAdjoint takes model 'ac' or 'ch'")
+        return cls._function().apply(phi0, theta, model, int(n_steps), float(dt), float(h),
                                      int(ckpt_interval))

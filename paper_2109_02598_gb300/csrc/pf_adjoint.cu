@@ -11,6 +11,13 @@
 //   dL/dDu += dt sum a lap u,  dL/dDv += dt sum b lap v,
 //   dL/dF  += dt sum [(1 - u) a - v b],  dL/dk += -dt sum v b.
 //
+// Model A (x' = x + dt (lap x + c1 x - c2 x^3)) and Model B (x' = x + dt M lap mu(x),
+// mu = c2 x^3 - c1 x - lap x) take the same loop with their own reverse steps:
+//   A: lambda^n = lambda + dt [lap lambda + (c1 - 3 c2 x^2) lambda];
+//      sums S = (sum lambda x, sum lambda x^3), dL/d(c1, c2) = dt (S0, -S1).
+//   B: w = lap lambda, lambda^n = lambda + dt M [(3 c2 x^2 - c1) w - lap w];
+//      sums S = (sum w x, sum w x^3, sum w mu), dL/d(c1, c2, M) = dt (-M S0, M S1, S2).
+//
 // Memory/recompute: the forward pass stores x at every C-th step (C ~ sqrt(N)); the
 // backward pass walks the segments from last to first, recomputes the segment's states
 // from its checkpoint with the forward kernel, then runs the segment's adjoint steps.
@@ -101,6 +108,114 @@ __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs l
   }
 }
 
+// Add this CTA's per-thread sums t[0..NG) into its FP64 slot (fixed order).
+template <int NG>
+__device__ __forceinline__ void add_to_slot(double (&t)[4], double (&red)[4][kNT2 / 32],
+                                            double* gpart) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    t[q] = warp_sum_d(t[q]);
+    if (lane == 0) red[q][wid] = t[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NG) {
+    double s = 0.0;
+    for (int w = 0; w < kNT2 / 32; ++w) s += red[threadIdx.x][w];
+    gpart[4 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] += s;
+  }
+}
+
+// Model A reverse step on a tile (halo 1 of x = phi^n and lambda^{n+1}).
+__global__ void __launch_bounds__(kNT2) adj_ac2d_kernel(FieldPtrs x, FieldPtrs lam,
+                                                        FieldOut lam_out, Geom g,
+                                                        ModelParams m, double* gpart) {
+  __shared__ float sp[kAPL], sl[kAPL];
+  __shared__ double red[4][kNT2 / 32];
+  const int x0 = blockIdx.x * kATX;
+  const int y0 = blockIdx.y * kATY;
+  for (int i = threadIdx.x; i < kAPL; i += kNT2) {
+    const int r = i / kAW;
+    const int c = i - r * kAW;
+    const int64_t off =
+        (int64_t)wrap_index(y0 - 1 + r, g.ny) * g.pitch + wrap_index(x0 - 1 + c, g.nx);
+    sp[i] = __ldg(x.f[0] + off);
+    sl[i] = __ldg(lam.f[0] + off);
+  }
+  __syncthreads();
+  const float c2x3 = __fmul_rn(3.0f, m.a1);
+  float s0 = 0.f, s1 = 0.f;
+  for (int i = threadIdx.x; i < kATX * kATY; i += kNT2) {
+    const int rr = i / kATX;
+    const int cc = i - rr * kATX;
+    const int gx = x0 + cc, gy = y0 + rr;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    const int p = (rr + 1) * kAW + (cc + 1);
+    const float ph = sp[p], l = sl[p];
+    const float ll = lap2d(l, sl[p - 1], sl[p + 1], sl[p - kAW], sl[p + kAW], m.inv_h2);
+    const float sfac = __fmaf_rn(-c2x3, __fmul_rn(ph, ph), m.a0);  // c1 - 3 c2 phi^2
+    const float f = __fmaf_rn(sfac, l, ll);
+    lam_out.f[0][(int64_t)gy * g.pitch + gx] = __fmaf_rn(m.dt, f, l);
+    const float lp = __fmul_rn(l, ph);
+    s0 = __fadd_rn(s0, lp);
+    s1 = __fmaf_rn(lp, __fmul_rn(ph, ph), s1);
+  }
+  double t[4] = {s0, s1, 0.0, 0.0};
+  add_to_slot<2>(t, red, gpart);
+}
+
+// Model B reverse step on a tile: stage phi^n and lambda^{n+1} with a halo of 2, form
+// w = lap lambda on the tile plus one ring, then lambda^n on the tile.
+constexpr int kBW = kATX + 4, kBH = kATY + 4, kBPL = kBW * kBH;
+__global__ void __launch_bounds__(kNT2) adj_ch2d_kernel(FieldPtrs x, FieldPtrs lam,
+                                                        FieldOut lam_out, Geom g,
+                                                        ModelParams m, double* gpart) {
+  __shared__ float sp[kBPL], sl[kBPL], sw[kBPL];
+  __shared__ double red[4][kNT2 / 32];
+  const int x0 = blockIdx.x * kATX;
+  const int y0 = blockIdx.y * kATY;
+  for (int i = threadIdx.x; i < kBPL; i += kNT2) {
+    const int r = i / kBW;
+    const int c = i - r * kBW;
+    const int64_t off =
+        (int64_t)wrap_index(y0 - 2 + r, g.ny) * g.pitch + wrap_index(x0 - 2 + c, g.nx);
+    sp[i] = __ldg(x.f[0] + off);
+    sl[i] = __ldg(lam.f[0] + off);
+  }
+  __syncthreads();
+  // w on rows/cols 1 .. kBH-2 / kBW-2 (the tile and one ring)
+  for (int i = threadIdx.x; i < (kATX + 2) * (kATY + 2); i += kNT2) {
+    const int r = 1 + i / (kATX + 2);
+    const int c = 1 + i % (kATX + 2);
+    const int p = r * kBW + c;
+    sw[p] = lap2d(sl[p], sl[p - 1], sl[p + 1], sl[p - kBW], sl[p + kBW], m.inv_h2);
+  }
+  __syncthreads();
+  const float c2x3 = __fmul_rn(3.0f, m.a1);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int i = threadIdx.x; i < kATX * kATY; i += kNT2) {
+    const int rr = i / kATX;
+    const int cc = i - rr * kATX;
+    const int gx = x0 + cc, gy = y0 + rr;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    const int p = (rr + 2) * kBW + (cc + 2);
+    const float ph = sp[p], l = sl[p], w = sw[p];
+    const float lw = lap2d(w, sw[p - 1], sw[p + 1], sw[p - kBW], sw[p + kBW], m.inv_h2);
+    const float ph2 = __fmul_rn(ph, ph);
+    const float sfac = __fmaf_rn(c2x3, ph2, -m.a0);  // 3 c2 phi^2 - c1
+    const float f = __fmaf_rn(sfac, w, -lw);
+    lam_out.f[0][(int64_t)gy * g.pitch + gx] = __fmaf_rn(m.a2, f, l);  // a2 = dt M
+    const float lph = lap2d(ph, sp[p - 1], sp[p + 1], sp[p - kBW], sp[p + kBW], m.inv_h2);
+    const float mu = ch_mu(ph, lph, m);
+    const float wp = __fmul_rn(w, ph);
+    s0 = __fadd_rn(s0, wp);
+    s1 = __fmaf_rn(wp, ph2, s1);
+    s2 = __fmaf_rn(w, mu, s2);
+  }
+  double t[4] = {s0, s1, s2, 0.0};
+  add_to_slot<3>(t, red, gpart);
+}
+
 // out[q] = sum over CTAs of gpart[4 * cta + q], in CTA order split over 256 threads.
 __global__ void __launch_bounds__(256) adj_final_kernel(const double* gpart, int64_t nctas,
                                                         double* out) {
@@ -139,8 +254,9 @@ float* lam_field(pf_grid_s* g, int b, int f) {
 }
 
 int check_gs2d(pf_grid_s* g) {
-  if (!g->model_set || g->model != PF_MODEL_GS) {
-    set_error("the adjoint needs a Gray-Scott model");
+  if (!g->model_set ||
+      (g->model != PF_MODEL_GS && g->model != PF_MODEL_AC && g->model != PF_MODEL_CH)) {
+    set_error("the adjoint needs a Gray-Scott, Allen-Cahn or Cahn-Hilliard model");
     return PF_ERR_STATE;
   }
   if (g->dim != 2) return invalid("the adjoint is implemented for 2D grids");
@@ -182,21 +298,26 @@ static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStrea
     for (int64_t j = 1; j < len && e == cudaSuccess; ++j) {
       FieldPtrs in{};
       FieldOut out{};
-      for (int f = 0; f < 2; ++f) {
+      for (int f = 0; f < g->nf; ++f) {
         in.f[f] = state(j - 1, f);
         out.f[f] = state(j, f);
       }
-      e = launch_fe2d(PF_MODEL_GS, 0, 1, q, in, out, m, st);
+      e = launch_fe2d(g->model, 0, 1, q, in, out, m, st);
     }
     for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j) {
       FieldPtrs xs{}, li{};
       FieldOut lo{};
-      for (int f = 0; f < 2; ++f) {
+      for (int f = 0; f < g->nf; ++f) {
         xs.f[f] = state(j, f);
         li.f[f] = lam_field(g, lb, f);
         lo.f[f] = lam_field(g, 1 - lb, f);
       }
-      adj_gs2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+      if (g->model == PF_MODEL_GS)
+        adj_gs2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+      else if (g->model == PF_MODEL_AC)
+        adj_ac2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+      else
+        adj_ch2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
       e = cudaGetLastError();
       lb = 1 - lb;
     }
@@ -274,13 +395,14 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
     set_error("pf_adj_backward: no recorded forward pass (call pf_adj_forward first)");
     return PF_ERR_STATE;
   }
-  if (dLdu_N == nullptr || dLdv_N == nullptr) return invalid("dL/dx_N must not be NULL");
-  const ModelParams m = make_params(PF_MODEL_GS, a.coeffs, a.dt, g->h);
+  if (dLdu_N == nullptr || (g->nf == 2 && dLdv_N == nullptr))
+    return invalid("dL/dx_N must not be NULL");
+  const ModelParams m = make_params(g->model, a.coeffs, a.dt, g->h);
   const size_t w = sizeof(float) * g->nx;
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const float* src[2] = {dLdu_N, dLdv_N};
-  for (int f = 0; f < 2; ++f)
+  for (int f = 0; f < g->nf; ++f)
     PF_CUDA_TRY(cudaMemcpy2DAsync(lam_field(g, 0, f), sizeof(float) * g->pitch, src[f], w, w,
                                   (size_t)g->ny, kin, g->stream));
   if (g->adj_exec == nullptr || g->adj_exec_steps != a.n_steps ||
@@ -313,13 +435,25 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
   PF_CUDA_TRY(cudaMemcpyAsync(a.ghost, a.gout, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                               g->stream));
   float* dst[2] = {dLdu0, dLdv0};
-  for (int f = 0; f < 2; ++f)
+  for (int f = 0; f < g->nf; ++f)
     if (dst[f] != nullptr)
       PF_CUDA_TRY(cudaMemcpy2DAsync(dst[f], w, lam_field(g, lb, f), sizeof(float) * g->pitch, w,
                                     (size_t)g->ny, kout, g->stream));
   PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-  if (dtheta != nullptr)
-    for (int i = 0; i < 4; ++i) dtheta[i] = a.dt * a.ghost[i];
+  if (dtheta != nullptr) {
+    const double* S = a.ghost;
+    if (g->model == PF_MODEL_GS) {
+      for (int i = 0; i < 4; ++i) dtheta[i] = a.dt * S[i];
+    } else if (g->model == PF_MODEL_AC) {
+      dtheta[0] = a.dt * S[0];
+      dtheta[1] = -a.dt * S[1];
+    } else {
+      const double M = a.coeffs[2];
+      dtheta[0] = -a.dt * M * S[0];
+      dtheta[1] = a.dt * M * S[1];
+      dtheta[2] = a.dt * S[2];
+    }
+  }
   return PF_OK;
 }
 

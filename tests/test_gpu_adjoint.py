@@ -145,3 +145,74 @@ def test_full_size_theta_gradient_vs_central_differences(pf):
         lm = oracle.gray_scott_final_and_loss(u0, v0, tuple(cm), DT, n, ut, vt)[2]
         fd = (lp - lm) / (2 * eps)
         assert abs(gth[i] - fd) <= 1e-3 * abs(fd), (i, gth[i], fd)
+
+
+# --------------------------------------------- Models A and B: dL/d(c1, c2) and mobility M
+
+PF = {"ac": ((0.9, 1.1), 0.02), "ch": ((0.8, 1.1, 0.7), 0.004)}
+
+
+def pf_gpu_adjoint(pf, model, phi0, n, ckpt, target):
+    import ctypes
+    from paper_2109_02598_gb300 import _lib
+    coeffs, dt = PF[model]
+    g = pf.Grid(phi0.shape, 1).set_model(model, coeffs, dt)
+    g.write_field(0, phi0)
+    _lib.check(g._lib.pf_adj_forward(g.handle, n, ckpt))
+    phiN = g.read_field(0)
+    d = (phiN.astype(np.float64) - target).astype(np.float32)
+    g0 = np.empty_like(d)
+    dth = (ctypes.c_double * 4)()
+    _lib.check(g._lib.pf_adj_backward(g.handle, d.ctypes.data_as(ctypes.c_void_p), None, 0,
+                                      g0.ctypes.data_as(ctypes.c_void_p), None, dth))
+    g.close()
+    return g0, np.array(list(dth)[:len(coeffs)])
+
+
+@pytest.mark.parametrize("model", ["ac", "ch"])
+@pytest.mark.parametrize("shape,n,ckpt", [((40, 48), 60, 7), ((33, 70), 25, 0)])
+def test_phase_field_adjoint_matches_oracle(pf, model, shape, n, ckpt):
+    coeffs, dt = PF[model]
+    phi0 = synthetic.allen_cahn_init(shape, seed=91, lo=-0.6, hi=0.6)
+    target = oracle.run(model, (phi0.astype(np.float64) * 0.9,), coeffs, dt, n)[0]
+    g0, gth = pf_gpu_adjoint(pf, model, phi0, n, ckpt, target)
+    phiN = oracle.run(model, (phi0,), coeffs, dt, n)[0]
+    r0, rth = oracle.phase_field_adjoint(model, phi0, coeffs, dt, n, phiN - target)
+    assert rel_l2((g0,), (r0,)) <= 1e-3
+    assert np.all(np.abs(gth - rth) <= 1e-3 * np.abs(rth)), (gth, rth)
+
+
+def test_mobility_gradient_autograd_vs_central_differences(pf):
+    # Model B 128^2, 400 steps: torch loss through PhaseFieldAdjoint; dL/dM and dL/dc1
+    # against FP64 central differences of the oracle's loss
+    import torch
+    coeffs, dt = PF["ch"]
+    n = 400
+    phi0 = synthetic.cahn_hilliard_init((128, 128), seed=93, amp=0.3)
+    target = oracle.run("ch", (phi0.astype(np.float64) * 0.8,), coeffs, dt, n)[0]
+    P0 = torch.tensor(phi0, device="cuda", requires_grad=True)
+    th = torch.tensor(coeffs, dtype=torch.float64, device="cuda", requires_grad=True)
+    out = pf.PhaseFieldAdjoint.apply(P0, th, "ch", n, dt)
+    T = torch.tensor(target, device="cuda", dtype=torch.float32)
+    loss = 0.5 * ((out - T) ** 2).sum()
+    loss.backward()
+    gth = th.grad.cpu().numpy()
+
+    def L(c):
+        p = oracle.run("ch", (phi0,), c, dt, n)[0]
+        return 0.5 * ((p - target) ** 2).sum()
+
+    for i in (0, 2):
+        eps = 1e-6
+        cp = list(coeffs); cp[i] += eps
+        cm = list(coeffs); cm[i] -= eps
+        fd = (L(tuple(cp)) - L(tuple(cm))) / (2 * eps)
+        assert abs(gth[i] - fd) <= 1e-3 * abs(fd), (i, gth[i], fd)
+    # and the initial-field gradient in one direction
+    d = np.random.default_rng(3).standard_normal(phi0.shape)
+    eps = 1e-6
+    p_plus = oracle.run("ch", (phi0 + eps * d,), coeffs, dt, n)[0]
+    p_minus = oracle.run("ch", (phi0 - eps * d,), coeffs, dt, n)[0]
+    fd = (0.5 * ((p_plus - target) ** 2).sum() - 0.5 * ((p_minus - target) ** 2).sum()) / (2 * eps)
+    ad = float((P0.grad.cpu().numpy().astype(np.float64) * d).sum())
+    assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
