@@ -11,7 +11,11 @@
 //                  mu_m = c4 m^3 - c3 m - c5 psi^2 - lap m,  f_m = lap mu_m
 // Forward Euler (Sec. 2.4.1): x_new = x + dt f(x).
 // Laplacian (Sec. 2.2.2): second-order central, 5 points in 2D and 7 in 3D, evaluated as
-// ((x- - c) + (x+ - c)) + ((y- - c) + (y+ - c)) [+ ((z- - c) + (z+ - c))], times 1/h^2.
+// fma(-2d, c, ((x- + x+) + (y- + y+)) [+ (z- + z+)]) times 1/h^2: six operations in 3D
+// instead of the twelve of the paired-difference form, which matters because the 3D
+// kernels are bound by instruction issue.  Each neighbour pair is one commutative
+// addition, so the streaming direction does not change the result, and a constant field
+// gives exactly zero.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,17 +60,14 @@ struct ModelTraits<PF_MODEL_C> {
 
 __device__ __forceinline__ float lap2d(float c, float xm, float xp, float ym, float yp,
                                        float inv_h2) {
-  const float sx = __fadd_rn(__fsub_rn(xm, c), __fsub_rn(xp, c));
-  const float sy = __fadd_rn(__fsub_rn(ym, c), __fsub_rn(yp, c));
-  return __fmul_rn(__fadd_rn(sx, sy), inv_h2);
+  const float s = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp));
+  return __fmul_rn(__fmaf_rn(-4.0f, c, s), inv_h2);
 }
 
 __device__ __forceinline__ float lap3d(float c, float xm, float xp, float ym, float yp,
                                        float zm, float zp, float inv_h2) {
-  const float sx = __fadd_rn(__fsub_rn(xm, c), __fsub_rn(xp, c));
-  const float sy = __fadd_rn(__fsub_rn(ym, c), __fsub_rn(yp, c));
-  const float sz = __fadd_rn(__fsub_rn(zm, c), __fsub_rn(zp, c));
-  return __fmul_rn(__fadd_rn(__fadd_rn(sx, sy), sz), inv_h2);
+  const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+  return __fmul_rn(__fmaf_rn(-6.0f, c, s), inv_h2);
 }
 
 // Model A: phi + dt (lap + c1 phi - c2 phi^3)
