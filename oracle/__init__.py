@@ -59,72 +59,119 @@ def laplacian(phi, h: float = 1.0):
     return out / (h * h)
 
 
+# Further Laplacian stencils of Sec. 2.2.2 (second-order isotropic 9-point in 2D and
+# 19-point in 3D; fourth-order 9-point in 2D), written from their weights:
+#   "9iso":  (1/6h^2) [4 (axial neighbours) + (diagonal neighbours) - 20 phi]
+#   "9o4":   (1/12h^2) sum over axes [16 (phi[+1] + phi[-1]) - (phi[+2] + phi[-2]) - 30 phi]
+#   "19iso": (1/6h^2) [2 (face neighbours) + (edge neighbours) - 24 phi]
+# "std" is the 5-point (2D) / 7-point (3D) stencil above.
+STENCILS_2D = ("std", "9iso", "9o4")
+STENCILS_3D = ("std", "19iso")
+
+
+def laplacian_stencil(phi, h: float = 1.0, stencil: str = "std"):
+    """Periodic Laplacian with the named stencil."""
+    phi = _f64(phi)
+    if stencil == "std":
+        return laplacian(phi, h)
+    d = phi.ndim
+    sh = lambda a, *o: np.roll(a, tuple(-x for x in o), axis=tuple(range(len(o))))  # a[x + o]
+    if stencil == "9iso" and d == 2:
+        axial = sh(phi, 1, 0) + sh(phi, -1, 0) + sh(phi, 0, 1) + sh(phi, 0, -1)
+        diag = sh(phi, 1, 1) + sh(phi, 1, -1) + sh(phi, -1, 1) + sh(phi, -1, -1)
+        return (4.0 * axial + diag - 20.0 * phi) / (6.0 * h * h)
+    if stencil == "9o4" and d == 2:
+        out = np.zeros_like(phi)
+        for ax in range(2):
+            p1 = np.roll(phi, 1, axis=ax) + np.roll(phi, -1, axis=ax)
+            p2 = np.roll(phi, 2, axis=ax) + np.roll(phi, -2, axis=ax)
+            out += 16.0 * p1 - p2 - 30.0 * phi
+        return out / (12.0 * h * h)
+    if stencil == "19iso" and d == 3:
+        faces = np.zeros_like(phi)
+        edges = np.zeros_like(phi)
+        for ax in range(3):
+            faces += np.roll(phi, 1, axis=ax) + np.roll(phi, -1, axis=ax)
+        for a in range(3):
+            for b in range(a + 1, 3):
+                for sa in (1, -1):
+                    for sb in (1, -1):
+                        edges += np.roll(np.roll(phi, sa, axis=a), sb, axis=b)
+        return (2.0 * faces + edges - 24.0 * phi) / (6.0 * h * h)
+    raise ValueError(f"stencil {stencil!r} is not defined for {d}D")
+
+
 # ------------------------------------------------------------ right-hand sides (Sec. 3)
 
-def rhs_allen_cahn(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
+def rhs_allen_cahn(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0, stencil="std"):
     """Model A: dphi/dt = lap phi + c1 phi - c2 phi^3."""
     phi = _f64(phi)
-    return laplacian(phi, h) + c1 * phi - c2 * phi ** 3
+    return laplacian_stencil(phi, h, stencil) + c1 * phi - c2 * phi ** 3
 
 
-def chemical_potential(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0):
+def chemical_potential(phi, c1: float = 1.0, c2: float = 1.0, h: float = 1.0, stencil="std"):
     """Model B chemical potential mu = c2 phi^3 - c1 phi - lap phi."""
     phi = _f64(phi)
-    return c2 * phi ** 3 - c1 * phi - laplacian(phi, h)
+    return c2 * phi ** 3 - c1 * phi - laplacian_stencil(phi, h, stencil)
 
 
-def rhs_cahn_hilliard(phi, c1: float = 1.0, c2: float = 1.0, M: float = 1.0, h: float = 1.0):
+def rhs_cahn_hilliard(phi, c1: float = 1.0, c2: float = 1.0, M: float = 1.0, h: float = 1.0,
+                      stencil="std"):
     """Model B: dphi/dt = M lap mu = -M lap^2 phi - M lap (c1 phi - c2 phi^3)."""
-    return M * laplacian(chemical_potential(phi, c1, c2, h), h)
+    return M * laplacian_stencil(chemical_potential(phi, c1, c2, h, stencil), h, stencil)
 
 
-def rhs_gray_scott(u, v, Du: float, Dv: float, F: float, k: float, h: float = 1.0):
+def rhs_gray_scott(u, v, Du: float, Dv: float, F: float, k: float, h: float = 1.0,
+                   stencil="std"):
     """Gray-Scott: (Du lap u - u v^2 + F (1-u),  Dv lap v + u v^2 - (F+k) v)."""
     u = _f64(u)
     v = _f64(v)
     uvv = u * v * v
-    fu = Du * laplacian(u, h) - uvv + F * (1.0 - u)
-    fv = Dv * laplacian(v, h) + uvv - (F + k) * v
+    fu = Du * laplacian_stencil(u, h, stencil) - uvv + F * (1.0 - u)
+    fv = Dv * laplacian_stencil(v, h, stencil) + uvv - (F + k) * v
     return fu, fv
 
 
-def rhs_model_c(psi, m, c1=1.0, c2=1.0, c3=1.0, c4=1.0, c5=1.0, h: float = 1.0):
+def rhs_model_c(psi, m, c1=1.0, c2=1.0, c3=1.0, c4=1.0, c5=1.0, h: float = 1.0,
+                stencil="std"):
     """Model C: (lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
                  lap(c4 m^3 - c3 m - c5 psi^2 - lap m))."""
     psi = _f64(psi)
     m = _f64(m)
-    f_psi = laplacian(psi, h) + c1 * psi - c2 * psi ** 3 + 2.0 * c5 * psi * m
-    mu_m = c4 * m ** 3 - c3 * m - c5 * psi ** 2 - laplacian(m, h)
-    return f_psi, laplacian(mu_m, h)
+    lap = lambda a: laplacian_stencil(a, h, stencil)
+    f_psi = lap(psi) + c1 * psi - c2 * psi ** 3 + 2.0 * c5 * psi * m
+    mu_m = c4 * m ** 3 - c3 * m - c5 * psi ** 2 - lap(m)
+    return f_psi, lap(mu_m)
 
 
-def rhs(model: str, fields, coeffs, h: float = 1.0):
+def rhs(model: str, fields, coeffs, h: float = 1.0, stencil: str = "std"):
     """Right-hand side f(x) of ``model`` for the tuple of fields ``x``."""
     if model == "ac":
-        return (rhs_allen_cahn(fields[0], *coeffs, h=h),)
+        return (rhs_allen_cahn(fields[0], *coeffs, h=h, stencil=stencil),)
     if model == "ch":
-        return (rhs_cahn_hilliard(fields[0], *coeffs, h=h),)
+        return (rhs_cahn_hilliard(fields[0], *coeffs, h=h, stencil=stencil),)
     if model == "gs":
-        return rhs_gray_scott(fields[0], fields[1], *coeffs, h=h)
+        return rhs_gray_scott(fields[0], fields[1], *coeffs, h=h, stencil=stencil)
     if model == "c":
-        return rhs_model_c(fields[0], fields[1], *coeffs, h=h)
+        return rhs_model_c(fields[0], fields[1], *coeffs, h=h, stencil=stencil)
     raise ValueError(f"unknown model {model!r}")
 
 
 # ----------------------------------------------------------- forward Euler (Sec. 2.4.1)
 
-def euler_step(model: str, fields, coeffs, dt: float, h: float = 1.0):
+def euler_step(model: str, fields, coeffs, dt: float, h: float = 1.0, stencil: str = "std"):
     """One explicit step x^{n+1} = x^n + dt f(x^n); all fields read x^n."""
     fields = tuple(_f64(f) for f in fields)
-    f = rhs(model, fields, coeffs, h)
+    f = rhs(model, fields, coeffs, h, stencil)
     return tuple(x + dt * fx for x, fx in zip(fields, f))
 
 
-def run(model: str, fields, coeffs, dt: float, n_steps: int, h: float = 1.0):
+def run(model: str, fields, coeffs, dt: float, n_steps: int, h: float = 1.0,
+        stencil: str = "std"):
     """``n_steps`` forward-Euler steps from ``fields``."""
     x = tuple(_f64(f) for f in fields)
     for _ in range(int(n_steps)):
-        x = euler_step(model, x, coeffs, dt, h)
+        x = euler_step(model, x, coeffs, dt, h, stencil)
     return x
 
 
