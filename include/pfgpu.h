@@ -61,6 +61,14 @@ extern "C" {
                          dpsi/dt = lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
                          dm/dt = -lap^2 m - lap(c3 m - c4 m^3 + c5 psi^2)   (Sec. 3) */
 
+/* ---------------------------------------------------------------- Laplacian stencils */
+#define PF_STENCIL_STD 0 /* second order: 5-point (2D), 7-point (3D); the default      */
+#define PF_STENCIL_ISO 1 /* second order, isotropic leading error: 9-point (2D) with
+                            weights (4 axial, 1 diagonal, -20)/6h^2; 19-point (3D) with
+                            (2 faces, 1 edges, -24)/6h^2                     (Sec. 2.2.2) */
+#define PF_STENCIL_4TH 2 /* fourth order, 9-point (2D only): per axis
+                            (-1, 16, -30, 16, -1)/12h^2                     (Sec. 2.2.2) */
+
 /* ---------------------------------------------------------------- reductions */
 #define PF_REDUCE_MASS 1   /* h^d * sum_x phi_x of one field                         */
 #define PF_REDUCE_ENERGY 2 /* discrete free energy (AC, CH: of field 0; Model C: of both):
@@ -128,6 +136,14 @@ int pf_step(pf_grid_t g, int64_t n_steps);
  * Synchronizes the stream. Errors: PF_ERR_INVALID_ARG, PF_ERR_STATE (energy without an
  * AC/CH model), PF_ERR_CUDA, PF_ERR_NONFINITE (*out is still written). */
 int pf_reduce(pf_grid_t g, int what, int field, double* out);
+
+/* Choose the Laplacian stencil of the step (PF_STENCIL_*; Sec. 2.2.2 lists these among the
+ * stencil families). Model B and Model C apply it twice. The tuning returns to the default
+ * for the stencil. The isotropic and fourth-order stencils run with 2D tiles 64x16 or
+ * 128x32 (k <= 2) and with the general 3D kernel (k = 1); the batch and the adjoint use the
+ * standard stencil. Errors: PF_ERR_INVALID_ARG (unknown stencil; fourth order in 3D),
+ * PF_ERR_UNSTABLE_DT (the current dt exceeds the bound for the new stencil; nothing changed). */
+int pf_set_stencil(pf_grid_t g, int stencil);
 
 /* Kernel tuning: tile_x, tile_y (2D tile, or xy tile of the 3D z-streaming kernel) and
  * k_steps (temporal-blocking depth, 2D only). 0 for any value = library default.

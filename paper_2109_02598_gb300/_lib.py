@@ -29,6 +29,8 @@ PF_MODEL_C = 4
 MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS, "c": PF_MODEL_C}
 MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2, "c": 2}
 
+STENCIL_IDS = {"std": 0, "iso": 1, "4th": 2}
+
 PF_REDUCE_MASS = 1
 PF_REDUCE_ENERGY = 2
 
@@ -56,6 +58,7 @@ SIGNATURES = {
     "pf_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pf_reduce": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _c_double_p]),
+    "pf_set_stencil": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pf_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pf_get_tuning": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
     "pf_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p]),

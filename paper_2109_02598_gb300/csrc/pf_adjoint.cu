@@ -72,10 +72,10 @@ __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs l
     if (gx >= g.nx || gy >= g.ny) continue;
     const int p = (rr + 1) * kAW + (cc + 1);
     const float u = su[p], v = sv[p], a = sa[p], b = sb[p];
-    const float la = lap2d(a, sa[p - 1], sa[p + 1], sa[p - kAW], sa[p + kAW], m.inv_h2);
-    const float lb = lap2d(b, sb[p - 1], sb[p + 1], sb[p - kAW], sb[p + kAW], m.inv_h2);
-    const float lu = lap2d(u, su[p - 1], su[p + 1], su[p - kAW], su[p + kAW], m.inv_h2);
-    const float lv = lap2d(v, sv[p - 1], sv[p + 1], sv[p - kAW], sv[p + kAW], m.inv_h2);
+    const float la = lap2d(a, sa[p - 1], sa[p + 1], sa[p - kAW], sa[p + kAW], m.lap_scale);
+    const float lb = lap2d(b, sb[p - 1], sb[p + 1], sb[p - kAW], sb[p + kAW], m.lap_scale);
+    const float lu = lap2d(u, su[p - 1], su[p + 1], su[p - kAW], su[p + kAW], m.lap_scale);
+    const float lv = lap2d(v, sv[p - 1], sv[p + 1], sv[p - kAW], sv[p + kAW], m.lap_scale);
     const float vv = __fmul_rn(v, v);
     const float uv2 = __fmul_rn(2.0f, __fmul_rn(u, v));
     // a' = a + dt [Du la - (v^2 + F) a + v^2 b]
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kNT2) adj_ac2d_kernel(FieldPtrs x, FieldPtrs l
     if (gx >= g.nx || gy >= g.ny) continue;
     const int p = (rr + 1) * kAW + (cc + 1);
     const float ph = sp[p], l = sl[p];
-    const float ll = lap2d(l, sl[p - 1], sl[p + 1], sl[p - kAW], sl[p + kAW], m.inv_h2);
+    const float ll = lap2d(l, sl[p - 1], sl[p + 1], sl[p - kAW], sl[p + kAW], m.lap_scale);
     const float sfac = __fmaf_rn(-c2x3, __fmul_rn(ph, ph), m.a0);  // c1 - 3 c2 phi^2
     const float f = __fmaf_rn(sfac, l, ll);
     lam_out.f[0][(int64_t)gy * g.pitch + gx] = __fmaf_rn(m.dt, f, l);
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kNT2) adj_ch2d_kernel(FieldPtrs x, FieldPtrs l
     const int r = 1 + i / (kATX + 2);
     const int c = 1 + i % (kATX + 2);
     const int p = r * kBW + c;
-    sw[p] = lap2d(sl[p], sl[p - 1], sl[p + 1], sl[p - kBW], sl[p + kBW], m.inv_h2);
+    sw[p] = lap2d(sl[p], sl[p - 1], sl[p + 1], sl[p - kBW], sl[p + kBW], m.lap_scale);
   }
   __syncthreads();
   const float c2x3 = __fmul_rn(3.0f, m.a1);
@@ -200,12 +200,12 @@ __global__ void __launch_bounds__(kNT2) adj_ch2d_kernel(FieldPtrs x, FieldPtrs l
     if (gx >= g.nx || gy >= g.ny) continue;
     const int p = (rr + 2) * kBW + (cc + 2);
     const float ph = sp[p], l = sl[p], w = sw[p];
-    const float lw = lap2d(w, sw[p - 1], sw[p + 1], sw[p - kBW], sw[p + kBW], m.inv_h2);
+    const float lw = lap2d(w, sw[p - 1], sw[p + 1], sw[p - kBW], sw[p + kBW], m.lap_scale);
     const float ph2 = __fmul_rn(ph, ph);
     const float sfac = __fmaf_rn(c2x3, ph2, -m.a0);  // 3 c2 phi^2 - c1
     const float f = __fmaf_rn(sfac, w, -lw);
     lam_out.f[0][(int64_t)gy * g.pitch + gx] = __fmaf_rn(m.a2, f, l);  // a2 = dt M
-    const float lph = lap2d(ph, sp[p - 1], sp[p + 1], sp[p - kBW], sp[p + kBW], m.inv_h2);
+    const float lph = lap2d(ph, sp[p - 1], sp[p + 1], sp[p - kBW], sp[p + kBW], m.lap_scale);
     const float mu = ch_mu(ph, lph, m);
     const float wp = __fmul_rn(w, ph);
     s0 = __fadd_rn(s0, wp);
@@ -260,6 +260,7 @@ int check_gs2d(pf_grid_s* g) {
     return PF_ERR_STATE;
   }
   if (g->dim != 2) return invalid("the adjoint is implemented for 2D grids");
+  if (g->stencil != PF_ST_STD) return invalid("the adjoint uses the standard 5-point stencil");
   return PF_OK;
 }
 

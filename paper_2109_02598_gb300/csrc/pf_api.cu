@@ -56,8 +56,15 @@ int model_ncoeffs(int model) {
 // Linear forward-Euler stability: dt * |largest eigenvalue of the linearised right-hand
 // side| <= 2, with the periodic Laplacian's spectrum in [-4d/h^2, 0] and, for AC/CH, the
 // cubic term linearised about |phi| <= 1 (slope between -c1 and 3 c2 - c1).
-double stable_dt_limit(int model, int dim, double h, const double* c) {
-  const double lmax = 4.0 * dim / (h * h);
+// Largest magnitude of the Laplacian stencil's Fourier symbol, times h^2.
+double stencil_lmax(int dim, int stencil) {
+  if (stencil == PF_ST_ISO) return 16.0 / 3.0;               // 9-point (pi,pi); 19-point (pi,pi,0)
+  if (stencil == PF_ST_O4) return 32.0 / 3.0;                // fourth order, both axes at pi
+  return 4.0 * dim;                                          // 5- / 7-point
+}
+
+double stable_dt_limit(int model, int dim, double h, const double* c, int stencil = PF_ST_STD) {
+  const double lmax = stencil_lmax(dim, stencil) / (h * h);
   switch (model) {
     case PF_MODEL_AC: {
       const double s = lmax + std::fmax(0.0, 3.0 * c[1] - c[0]);
@@ -81,10 +88,11 @@ double stable_dt_limit(int model, int dim, double h, const double* c) {
   return 0.0;
 }
 
-ModelParams make_params(int model, const double* c, double dt, double h) {
+ModelParams make_params(int model, const double* c, double dt, double h, int stencil) {
   ModelParams m{};
   m.dt = (float)dt;
-  m.inv_h2 = (float)(1.0 / (h * h));
+  const double denom = stencil == PF_ST_ISO ? 6.0 : (stencil == PF_ST_O4 ? 12.0 : 1.0);
+  m.lap_scale = (float)(1.0 / (denom * h * h));
   switch (model) {
     case PF_MODEL_AC:
       m.a0 = (float)c[0];
@@ -130,9 +138,17 @@ bool tile_supported(pf_grid_s* g, int tile, int k);
 // model and grid.
 int resolve_tuning(pf_grid_s* g) {
   if (g->dim == 2) {
-    g->tile = g->req_tile >= 0 ? g->req_tile : 1;  // 128 x 16
+    const int def = g->stencil == PF_ST_STD ? 1 : 0;  // 128 x 16; other stencils 64 x 16
+    g->tile = g->req_tile >= 0 ? g->req_tile : def;
     g->k = g->req_k > 0 ? g->req_k : 1;
     if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
+    if (!fe2d_stencil_supported(g->stencil, g->tile, g->k)) {
+      g->tile = def;
+      g->k = 1;
+    }
+  } else if (g->stencil != PF_ST_STD) {
+    g->tile = (g->req_tile == 0 || g->req_tile == 1) ? g->req_tile : 0;  // general kernel
+    g->k = 1;
   } else {
     // default: the fastest TMA tile that divides the grid (measured on GS 256^3:
     // 128x16 > 64x16 = 128x8), else the general kernel
@@ -153,7 +169,8 @@ int resolve_tuning(pf_grid_s* g) {
 }
 
 bool tile_supported(pf_grid_s* g, int tile, int k) {
-  if (g->dim == 2) return fe2d_supported(g->model, k);
+  if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
+  if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
   int tx, ty;
   tile3d_shape(tile, &tx, &ty);
   if (k == 2) return fe3d_tb2_supported(g->model, tx, ty, grid_geom(g));
@@ -197,7 +214,8 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
     out.f[f] = g->buf[dst][f];
   }
   const Geom q = grid_geom(g);
-  if (g->dim == 2) return launch_fe2d(g->model, tile, k, q, in, out, g->params, st);
+  if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
+  if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
   if (k == 2) {
     int tx, ty;
     tile3d_shape(tile, &tx, &ty);
@@ -360,7 +378,7 @@ int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, dou
   for (int i = 0; i < n_coeffs; ++i)
     if (!std::isfinite(coeffs[i])) return invalid("coefficient %d is not finite", i);
   if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("dt must be finite and > 0");
-  const double lim = stable_dt_limit(model, g->dim, g->h, coeffs);
+  const double lim = stable_dt_limit(model, g->dim, g->h, coeffs, g->stencil);
   if (dt > lim && !force) {
     set_error("dt = %g exceeds the forward-Euler stability limit %g for this model and grid "
               "(pass force=1 to accept)", dt, lim);
@@ -369,7 +387,7 @@ int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, dou
   g->model = model;
   for (int i = 0; i < n_coeffs; ++i) g->coeffs[i] = coeffs[i];
   g->dt = dt;
-  g->params = make_params(model, coeffs, dt, g->h);
+  g->params = make_params(model, coeffs, dt, g->h, g->stencil);
   g->model_set = 1;
   drop_graphs(g);  // recorded graphs carry the old coefficients
   resolve_tuning(g);
@@ -480,6 +498,28 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out) {
   return PF_OK;
 }
 
+int pf_set_stencil(pf_grid_t g, int stencil) {
+  if (int rc = check_grid(g)) return rc;
+  if (stencil != PF_STENCIL_STD && stencil != PF_STENCIL_ISO && stencil != PF_STENCIL_4TH)
+    return invalid("unknown stencil %d", stencil);
+  if (stencil == PF_STENCIL_4TH && g->dim != 2)
+    return invalid("the fourth-order stencil is defined for 2D grids only");
+  if (g->model_set && stencil != g->stencil) {
+    const double lim = stable_dt_limit(g->model, g->dim, g->h, g->coeffs, stencil);
+    if (g->dt > lim) {
+      set_error("dt = %g exceeds the forward-Euler stability limit %g with this stencil "
+                "(set a smaller dt first)", g->dt, lim);
+      return PF_ERR_UNSTABLE_DT;
+    }
+  }
+  g->stencil = stencil;
+  if (g->model_set) g->params = make_params(g->model, g->coeffs, g->dt, g->h, stencil);
+  g->req_tile = -1;
+  g->req_k = 0;
+  drop_graphs(g);
+  return resolve_tuning(g);
+}
+
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
   if (int rc = check_grid(g)) return rc;
   int tile = -1;
@@ -504,6 +544,15 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     const int model = g->model_set ? g->model : PF_MODEL_AC;
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
+  }
+  if (g->stencil != PF_ST_STD) {
+    const int t = tile >= 0 ? tile : 0;
+    const int kk = k_steps > 0 ? k_steps : 1;
+    const bool ok = g->dim == 2 ? fe2d_stencil_supported(g->stencil, t, kk)
+                                : ((t == 0 || t == 1) && kk == 1);
+    if (!ok)
+      return invalid("this stencil runs with 2D tiles 64x16 or 128x32 and k <= 2, or 3D tiles "
+                     "32x16 or 64x8 and k = 1");
   }
   if (g->dim == 3 && k_steps != 2 && tile >= kFirstTmaTile3D &&
       !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g))))

@@ -15,7 +15,7 @@
 #include "pf_internal.h"
 
 namespace pf {
-double stable_dt_limit(int model, int dim, double h, const double* c);
+double stable_dt_limit(int model, int dim, double h, const double* c, int stencil);
 }
 
 struct pf_batch_s {
@@ -112,9 +112,9 @@ int pf_batch_create(int n, const pf_gs2d_spec* specs, double dt, double h, void*
     const double c[4] = {s.Du, s.Dv, s.F, s.k};
     for (double v : c)
       if (!std::isfinite(v)) return invalid("instance %d: non-finite coefficient", i);
-    if (dt > stable_dt_limit(PF_MODEL_GS, 2, h, c)) {
+    if (dt > stable_dt_limit(PF_MODEL_GS, 2, h, c, PF_ST_STD)) {
       set_error("instance %d: dt = %g exceeds the forward-Euler stability limit %g", i, dt,
-                stable_dt_limit(PF_MODEL_GS, 2, h, c));
+                stable_dt_limit(PF_MODEL_GS, 2, h, c, PF_ST_STD));
       return PF_ERR_UNSTABLE_DT;
     }
     const int64_t pitch = (s.nx + 3) / 4 * 4;

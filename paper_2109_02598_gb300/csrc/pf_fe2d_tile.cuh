@@ -17,10 +17,11 @@ namespace pf {
 
 constexpr int kNT2 = 256;  // threads per CTA of every 2D kernel
 
-template <int MODEL, int K, int TX, int TY>
+template <int MODEL, int K, int TX, int TY, int ST = PF_ST_STD>
 struct Cfg2 {
   static constexpr int NF = ModelTraits<MODEL>::NF;
-  static constexpr int R = ModelTraits<MODEL>::R;
+  static constexpr int RS = StencilTraits<ST>::R;       // one Laplacian's radius
+  static constexpr int R = ModelTraits<MODEL>::R * RS;  // one step's radius
   static constexpr int H = K * R;              // halo the k sub-steps consume (sites)
   static constexpr int HP = (H + 3) / 4 * 4;   // staged halo, 16-byte aligned
   static constexpr int WS = TX + 2 * HP;       // staged row width (floats)
@@ -62,27 +63,45 @@ __device__ __forceinline__ void load_region2d(const FieldPtrs& in, int nx, int n
   }
 }
 
-// 2D Laplacians of four consecutive sites from a float4 row and its neighbours.
-__device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float inv_h2) {
+// 2D Laplacians of four consecutive sites from a float4 row and its neighbours, with the
+// stencil ST (its neighbours beyond the float4 come from scalars of the same rows).
+template <int ST = PF_ST_STD>
+__device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float scale) {
   const float4 c = *reinterpret_cast<const float4*>(s + p);
   const float4 u = *reinterpret_cast<const float4*>(s + p - ws);
   const float4 d = *reinterpret_cast<const float4*>(s + p + ws);
   const float l = s[p - 1], r = s[p + 4];
   float4 o;
-  o.x = lap2d(c.x, l, c.y, u.x, d.x, inv_h2);
-  o.y = lap2d(c.y, c.x, c.z, u.y, d.y, inv_h2);
-  o.z = lap2d(c.z, c.y, c.w, u.z, d.z, inv_h2);
-  o.w = lap2d(c.w, c.z, r, u.w, d.w, inv_h2);
+  if constexpr (ST == PF_ST_STD) {
+    o.x = lap2d(c.x, l, c.y, u.x, d.x, scale);
+    o.y = lap2d(c.y, c.x, c.z, u.y, d.y, scale);
+    o.z = lap2d(c.z, c.y, c.w, u.z, d.z, scale);
+    o.w = lap2d(c.w, c.z, r, u.w, d.w, scale);
+  } else if constexpr (ST == PF_ST_ISO) {
+    const float ul = s[p - ws - 1], ur = s[p - ws + 4], dl = s[p + ws - 1], dr = s[p + ws + 4];
+    o.x = lap2d_iso(c.x, l, c.y, u.x, d.x, ul, u.y, dl, d.y, scale);
+    o.y = lap2d_iso(c.y, c.x, c.z, u.y, d.y, u.x, u.z, d.x, d.z, scale);
+    o.z = lap2d_iso(c.z, c.y, c.w, u.z, d.z, u.y, u.w, d.y, d.w, scale);
+    o.w = lap2d_iso(c.w, c.z, r, u.w, d.w, u.z, ur, d.z, dr, scale);
+  } else {
+    const float l2 = s[p - 2], r2 = s[p + 5];
+    const float4 u2 = *reinterpret_cast<const float4*>(s + p - 2 * ws);
+    const float4 d2 = *reinterpret_cast<const float4*>(s + p + 2 * ws);
+    o.x = lap2d_o4(c.x, l, c.y, l2, c.z, u.x, d.x, u2.x, d2.x, scale);
+    o.y = lap2d_o4(c.y, c.x, c.z, l, c.w, u.y, d.y, u2.y, d2.y, scale);
+    o.z = lap2d_o4(c.z, c.y, c.w, c.x, r, u.z, d.z, u2.z, d2.z, scale);
+    o.w = lap2d_o4(c.w, c.z, r, c.y, r2, u.w, d.w, u2.w, d2.w, scale);
+  }
   return o;
 }
 
 // k forward-Euler sub-steps of one tile; the last one is written to `out` (sites beyond
 // nx, ny are computed on periodic images and not stored).
-template <int MODEL, int K, int TX, int TY>
+template <int MODEL, int K, int TX, int TY, int ST = PF_ST_STD>
 __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& out, int nx,
                                           int ny, int64_t pitch, int x0, int y0,
                                           const ModelParams& m, float* sm) {
-  using C = Cfg2<MODEL, K, TX, TY>;
+  using C = Cfg2<MODEL, K, TX, TY, ST>;
   constexpr int WS = C::WS;
   constexpr int PL = C::PL;
   load_region2d<C>(in, nx, ny, pitch, x0, y0, sm);
@@ -93,9 +112,10 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
     float* dst = sm + ((s + 1) & 1) * C::NF * PL;
     float* mu = sm + C::NF * C::NBUF * PL;
     if constexpr (MODEL == PF_MODEL_CH || MODEL == PF_MODEL_C) {
-      // mu on the region one ring wider than this sub-step's update
-      const int rlo = C::R * s + 1, rhi = C::HT - rlo;
-      const int clo = (C::HP - C::H + C::R * s + 1) / 4, chi = (WS - (C::HP - C::H + C::R * s + 1) + 3) / 4;
+      // mu on the region one stencil radius wider than this sub-step's update
+      const int rlo = C::R * s + C::RS, rhi = C::HT - rlo;
+      const int clo = (C::HP - C::H + C::R * s + C::RS) / 4;
+      const int chi = (WS - (C::HP - C::H + C::R * s + C::RS) + 3) / 4;
       const int nch = chi - clo;
       for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
         const int rr = i / nch;
@@ -103,14 +123,14 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
         const int p = r * WS + 4 * (clo + i - rr * nch);
         if constexpr (MODEL == PF_MODEL_CH) {
           const float4 c = *reinterpret_cast<const float4*>(src + p);
-          const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
+          const float4 l = lap2d_x4<ST>(src, p, WS, m.lap_scale);
           *reinterpret_cast<float4*>(mu + p) =
               make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
                           ch_mu(c.w, l.w, m));
         } else {  // Model C: chemical potential of m (field 1), coupled to psi (field 0)
           const float4 ps = *reinterpret_cast<const float4*>(src + p);
           const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
-          const float4 l = lap2d_x4(src + PL, p, WS, m.inv_h2);
+          const float4 l = lap2d_x4<ST>(src + PL, p, WS, m.lap_scale);
           *reinterpret_cast<float4*>(mu + p) =
               make_float4(mc_mu(ps.x, c.x, l.x, m), mc_mu(ps.y, c.y, l.y, m),
                           mc_mu(ps.z, c.z, l.z, m), mc_mu(ps.w, c.w, l.w, m));
@@ -131,19 +151,19 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
       float4 val[C::NF];
       if constexpr (MODEL == PF_MODEL_AC) {
         const float4 c = *reinterpret_cast<const float4*>(src + p);
-        const float4 l = lap2d_x4(src, p, WS, m.inv_h2);
+        const float4 l = lap2d_x4<ST>(src, p, WS, m.lap_scale);
         val[0] = make_float4(ac_update(c.x, l.x, m), ac_update(c.y, l.y, m),
                              ac_update(c.z, l.z, m), ac_update(c.w, l.w, m));
       } else if constexpr (MODEL == PF_MODEL_CH) {
         const float4 c = *reinterpret_cast<const float4*>(src + p);
-        const float4 l = lap2d_x4(mu, p, WS, m.inv_h2);
+        const float4 l = lap2d_x4<ST>(mu, p, WS, m.lap_scale);
         val[0] = make_float4(ch_update(c.x, l.x, m), ch_update(c.y, l.y, m),
                              ch_update(c.z, l.z, m), ch_update(c.w, l.w, m));
       } else if constexpr (MODEL == PF_MODEL_C) {
         const float4 ps = *reinterpret_cast<const float4*>(src + p);
         const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
-        const float4 lp = lap2d_x4(src, p, WS, m.inv_h2);
-        const float4 lm = lap2d_x4(mu, p, WS, m.inv_h2);
+        const float4 lp = lap2d_x4<ST>(src, p, WS, m.lap_scale);
+        const float4 lm = lap2d_x4<ST>(mu, p, WS, m.lap_scale);
         mc_update(ps.x, c.x, lp.x, lm.x, m, val[0].x, val[1].x);
         mc_update(ps.y, c.y, lp.y, lm.y, m, val[0].y, val[1].y);
         mc_update(ps.z, c.z, lp.z, lm.z, m, val[0].z, val[1].z);
@@ -151,8 +171,8 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
       } else {
         const float4 u = *reinterpret_cast<const float4*>(src + p);
         const float4 v = *reinterpret_cast<const float4*>(src + PL + p);
-        const float4 lu = lap2d_x4(src, p, WS, m.inv_h2);
-        const float4 lv = lap2d_x4(src + PL, p, WS, m.inv_h2);
+        const float4 lu = lap2d_x4<ST>(src, p, WS, m.lap_scale);
+        const float4 lv = lap2d_x4<ST>(src + PL, p, WS, m.lap_scale);
         gs_update(u.x, v.x, lu.x, lv.x, m, val[0].x, val[1].x);
         gs_update(u.y, v.y, lu.y, lv.y, m, val[0].y, val[1].y);
         gs_update(u.z, v.z, lu.z, lv.z, m, val[0].z, val[1].z);

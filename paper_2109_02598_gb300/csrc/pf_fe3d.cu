@@ -47,8 +47,27 @@ __device__ __forceinline__ void load_plane3d(const FieldPtrs& in, const Geom& g,
   }
 }
 
+// 3D Laplacian at position p of a staged plane c (row width W) with the planes b below and
+// a above: 7-point (ST = PF_ST_STD) or isotropic 19-point (faces and edges, PF_ST_ISO).
+template <int ST>
+__device__ __forceinline__ float lap3d_planes(const float* b, const float* c, const float* a,
+                                              int p, int W, float scale) {
+  if constexpr (ST == PF_ST_STD) {
+    return lap3d(c[p], c[p - 1], c[p + 1], c[p - W], c[p + W], b[p], a[p], scale);
+  } else {
+    const float faces = __fadd_rn(__fadd_rn(__fadd_rn(c[p - 1], c[p + 1]),
+                                            __fadd_rn(c[p - W], c[p + W])),
+                                  __fadd_rn(b[p], a[p]));
+    const float exy = __fadd_rn(__fadd_rn(c[p - W - 1], c[p - W + 1]),
+                                __fadd_rn(c[p + W - 1], c[p + W + 1]));
+    const float eb = __fadd_rn(__fadd_rn(b[p - 1], b[p + 1]), __fadd_rn(b[p - W], b[p + W]));
+    const float ea = __fadd_rn(__fadd_rn(a[p - 1], a[p + 1]), __fadd_rn(a[p - W], a[p + W]));
+    return lap3d_iso(c[p], faces, __fadd_rn(exy, __fadd_rn(eb, ea)), scale);
+  }
+}
+
 // AC and Gray-Scott (stencil radius 1).
-template <int MODEL, int TX, int TY>
+template <int MODEL, int TX, int TY, int ST>
 __global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut out, Geom g,
                                                        ModelParams m, int tz) {
   using C = Cfg3<MODEL, TX, TY>;
@@ -76,19 +95,16 @@ __global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut ou
       float val[C::NF];
       if constexpr (MODEL == PF_MODEL_AC) {
         const float* cp = sm + sc * PL;
-        const float pc = cp[p];
-        const float l = lap3d(pc, cp[p - 1], cp[p + 1], cp[p - W], cp[p + W], sm[sb * PL + p],
-                              sm[sa * PL + p], m.inv_h2);
-        val[0] = ac_update(pc, l, m);
+        const float l = lap3d_planes<ST>(sm + sb * PL, cp, sm + sa * PL, p, W, m.lap_scale);
+        val[0] = ac_update(cp[p], l, m);
       } else {
         const float* cu = sm + (sc * 2) * PL;
         const float* cv = cu + PL;
-        const float u = cu[p], v = cv[p];
-        const float lu = lap3d(u, cu[p - 1], cu[p + 1], cu[p - W], cu[p + W],
-                               sm[(sb * 2) * PL + p], sm[(sa * 2) * PL + p], m.inv_h2);
-        const float lv = lap3d(v, cv[p - 1], cv[p + 1], cv[p - W], cv[p + W],
-                               sm[(sb * 2 + 1) * PL + p], sm[(sa * 2 + 1) * PL + p], m.inv_h2);
-        gs_update(u, v, lu, lv, m, val[0], val[1]);
+        const float lu = lap3d_planes<ST>(sm + (sb * 2) * PL, cu, sm + (sa * 2) * PL, p, W,
+                                          m.lap_scale);
+        const float lv = lap3d_planes<ST>(sm + (sb * 2 + 1) * PL, cv, sm + (sa * 2 + 1) * PL, p,
+                                          W, m.lap_scale);
+        gs_update(cu[p], cv[p], lu, lv, m, val[0], val[1]);
       }
       if (gx < g.nx && gy < g.ny) {
         const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
@@ -107,7 +123,7 @@ __global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut ou
 // Model B and Model C: mu planes computed on chip from the staged phi planes (halo 2).
 // Model B: mu = c2 phi^3 - c1 phi - lap phi of its one field.  Model C: the chemical
 // potential of m (field 1), coupled to psi (field 0).
-template <int MODEL, int TX, int TY>
+template <int MODEL, int TX, int TY, int ST>
 __device__ __forceinline__ void r2_mu_plane(const float* pb, const float* pc, const float* pa,
                                             float* mu, const ModelParams& m) {
   using C = Cfg3<MODEL, TX, TY>;
@@ -118,10 +134,8 @@ __device__ __forceinline__ void r2_mu_plane(const float* pb, const float* pc, co
     const int r1 = i / C::W1;
     const int c1 = i - r1 * C::W1;
     const int p = (r1 + 1) * W + (c1 + 1);  // position in the phi plane (halo 2)
-    const float* q = pc + F * PL;
-    const float v = q[p];
-    const float l = lap3d(v, q[p - 1], q[p + 1], q[p - W], q[p + W], pb[F * PL + p],
-                          pa[F * PL + p], m.inv_h2);
+    const float v = pc[F * PL + p];
+    const float l = lap3d_planes<ST>(pb + F * PL, pc + F * PL, pa + F * PL, p, W, m.lap_scale);
     if constexpr (MODEL == PF_MODEL_CH)
       mu[i] = ch_mu(v, l, m);
     else
@@ -129,7 +143,7 @@ __device__ __forceinline__ void r2_mu_plane(const float* pb, const float* pc, co
   }
 }
 
-template <int MODEL, int TX, int TY>
+template <int MODEL, int TX, int TY, int ST>
 __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut out, Geom g,
                                                        ModelParams m, int tz) {
   using C = Cfg3<MODEL, TX, TY>;
@@ -154,16 +168,16 @@ __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut ou
   load_plane3d<C>(in, g, x0, y0, z0 - 1, pslot(z0 - 1), ph);
   load_plane3d<C>(in, g, x0, y0, z0, pslot(z0), ph);
   __syncthreads();
-  r2_mu_plane<MODEL, TX, TY>(plane(z0 - 2), plane(z0 - 1), plane(z0), mu + slot(z0 - 1) * PL1, m);
+  r2_mu_plane<MODEL, TX, TY, ST>(plane(z0 - 2), plane(z0 - 1), plane(z0), mu + slot(z0 - 1) * PL1, m);
   __syncthreads();
   load_plane3d<C>(in, g, x0, y0, z0 + 1, pslot(z0 + 1), ph);
   __syncthreads();
-  r2_mu_plane<MODEL, TX, TY>(plane(z0 - 1), plane(z0), plane(z0 + 1), mu + slot(z0) * PL1, m);
+  r2_mu_plane<MODEL, TX, TY, ST>(plane(z0 - 1), plane(z0), plane(z0 + 1), mu + slot(z0) * PL1, m);
   __syncthreads();
   for (int z = z0; z < z1; ++z) {
     load_plane3d<C>(in, g, x0, y0, z + 2, pslot(z + 2), ph);
     __syncthreads();
-    r2_mu_plane<MODEL, TX, TY>(plane(z), plane(z + 1), plane(z + 2), mu + slot(z + 1) * PL1, m);
+    r2_mu_plane<MODEL, TX, TY, ST>(plane(z), plane(z + 1), plane(z + 2), mu + slot(z + 1) * PL1, m);
     __syncthreads();
     const float* mb = mu + slot(z - 1) * PL1;
     const float* mc = mu + slot(z) * PL1;
@@ -177,8 +191,7 @@ __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut ou
       const int cc = i - rr * TX;
       const int q = (rr + 1) * W1 + (cc + 1);  // mu plane position
       const int p = (rr + 2) * W + (cc + 2);   // phi plane position
-      const float l = lap3d(mc[q], mc[q - 1], mc[q + 1], mc[q - W1], mc[q + W1], mb[q], ma[q],
-                            m.inv_h2);
+      const float l = lap3d_planes<ST>(mb, mc, ma, q, W1, m.lap_scale);
       const int gx = x0 + cc;
       const int gy = y0 + rr;
       if (gx >= g.nx || gy >= g.ny) continue;
@@ -187,8 +200,7 @@ __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut ou
         out.f[0][off] = ch_update(pc[p], l, m);
       } else {
         const float ps = pc[p];
-        const float lp = lap3d(ps, pc[p - 1], pc[p + 1], pc[p - W], pc[p + W], pb[p], pa[p],
-                               m.inv_h2);
+        const float lp = lap3d_planes<ST>(pb, pc, pa, p, W, m.lap_scale);
         float psn, mn;
         mc_update(ps, pc[PL + p], lp, l, m, psn, mn);
         out.f[0][off] = psn;
@@ -207,7 +219,7 @@ int choose_tz(const Geom& g, int tiles_xy) {
   return tz;
 }
 
-template <int MODEL, int TX, int TY>
+template <int MODEL, int TX, int TY, int ST>
 cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
                     cudaStream_t s) {
   using C = Cfg3<MODEL, TX, TY>;
@@ -217,22 +229,27 @@ cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams
   const int tz = choose_tz(g, bx * by);
   dim3 grid(bx, by, (g.nz + tz - 1) / tz);
   if constexpr (ModelTraits<MODEL>::R == 2) {
-    cudaError_t e = ensure_smem_attr(fe3d_r2_kernel<MODEL, TX, TY>, smem, &attr_mask);
+    cudaError_t e = ensure_smem_attr(fe3d_r2_kernel<MODEL, TX, TY, ST>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
-    fe3d_r2_kernel<MODEL, TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+    fe3d_r2_kernel<MODEL, TX, TY, ST><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   } else {
-    cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY>, smem, &attr_mask);
+    cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY, ST>, smem, &attr_mask);
     if (e != cudaSuccess) return e;
-    fe3d_r1_kernel<MODEL, TX, TY><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+    fe3d_r1_kernel<MODEL, TX, TY, ST><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   }
   return cudaGetLastError();
 }
 
 template <int MODEL>
 cudaError_t launch3_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
-                         const ModelParams& m, cudaStream_t s) {
-  if (tile_id == 0) return launch3<MODEL, 32, 16>(g, in, out, m, s);
-  return launch3<MODEL, 64, 8>(g, in, out, m, s);
+                         const ModelParams& m, cudaStream_t s, int stencil) {
+  if (stencil == PF_ST_ISO) {
+    if (tile_id == 0) return launch3<MODEL, 32, 16, PF_ST_ISO>(g, in, out, m, s);
+    return launch3<MODEL, 64, 8, PF_ST_ISO>(g, in, out, m, s);
+  }
+  if (stencil != PF_ST_STD) return cudaErrorInvalidValue;
+  if (tile_id == 0) return launch3<MODEL, 32, 16, PF_ST_STD>(g, in, out, m, s);
+  return launch3<MODEL, 64, 8, PF_ST_STD>(g, in, out, m, s);
 }
 
 }  // namespace
@@ -254,13 +271,13 @@ int tile3d_id(int tx, int ty) {
 }
 
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
-                        const ModelParams& m, cudaStream_t s) {
+                        const ModelParams& m, cudaStream_t s, int stencil) {
   if (tile_id < 0 || tile_id >= kFirstTmaTile3D) return cudaErrorInvalidValue;
   switch (model) {
-    case PF_MODEL_AC: return launch3_tile<PF_MODEL_AC>(tile_id, g, in, out, m, s);
-    case PF_MODEL_CH: return launch3_tile<PF_MODEL_CH>(tile_id, g, in, out, m, s);
-    case PF_MODEL_GS: return launch3_tile<PF_MODEL_GS>(tile_id, g, in, out, m, s);
-    case PF_MODEL_C: return launch3_tile<PF_MODEL_C>(tile_id, g, in, out, m, s);
+    case PF_MODEL_AC: return launch3_tile<PF_MODEL_AC>(tile_id, g, in, out, m, s, stencil);
+    case PF_MODEL_CH: return launch3_tile<PF_MODEL_CH>(tile_id, g, in, out, m, s, stencil);
+    case PF_MODEL_GS: return launch3_tile<PF_MODEL_GS>(tile_id, g, in, out, m, s, stencil);
+    case PF_MODEL_C: return launch3_tile<PF_MODEL_C>(tile_id, g, in, out, m, s, stencil);
   }
   return cudaErrorInvalidValue;
 }

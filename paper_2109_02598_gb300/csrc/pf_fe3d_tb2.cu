@@ -68,12 +68,12 @@ __device__ __forceinline__ void update4(const float4* c, const float4* lap, floa
 // two x-edge scalars of the centre row.
 __device__ __forceinline__ float4 lap3d_x4(const float4& c, const float4& ym, const float4& yp,
                                            const float4& zm, const float4& zp, float xm,
-                                           float xp, float inv_h2) {
+                                           float xp, float lap_scale) {
   float4 l;
-  l.x = lap3d(c.x, xm, c.y, ym.x, yp.x, zm.x, zp.x, inv_h2);
-  l.y = lap3d(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, inv_h2);
-  l.z = lap3d(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, inv_h2);
-  l.w = lap3d(c.w, c.z, xp, ym.w, yp.w, zm.w, zp.w, inv_h2);
+  l.x = lap3d(c.x, xm, c.y, ym.x, yp.x, zm.x, zp.x, lap_scale);
+  l.y = lap3d(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, lap_scale);
+  l.z = lap3d(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, lap_scale);
+  l.w = lap3d(c.w, c.z, xp, ym.w, yp.w, zm.w, zp.w, lap_scale);
   return l;
 }
 
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         izp[f] = *reinterpret_cast<const float4*>(sp + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
         float xm, xp;
         x_edges<W>(F + (r + 1) * W, x4, xm, xp);
-        lap[f] = lap3d_x4(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.inv_h2);
+        lap[f] = lap3d_x4(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.lap_scale);
       }
       update4<MODEL>(ic, lap, l1v, m);
       float* l1p = l1 + (j % 3) * C::L1_PLANE;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
           const float4 yp = *reinterpret_cast<const float4*>(F + (r + 1) * W + 4 * x4);
           float xm, xp;
           x_edges<W>(F + r * W, x4, xm, xp);
-          lap2[f] = lap3d_x4(lc[f], ym, yp, lzm[f], l1v[f], xm, xp, m.inv_h2);
+          lap2[f] = lap3d_x4(lc[f], ym, yp, lzm[f], l1v[f], xm, xp, m.lap_scale);
         }
         update4<MODEL>(lc, lap2, res, m);
         const int z = zfirst + (j - 2) * dir;

@@ -72,6 +72,7 @@ struct pf_grid_s {
   double coeffs[5] = {0, 0, 0, 0, 0};
   double dt = 0;
   int model_set = 0;
+  int stencil = 0;  // PF_STENCIL_* (Laplacian stencil of the step)
   pf::ModelParams params{};
   int tile = -1;      // kernel tile id in effect (2D or 3D table)
   int k = 0;          // temporal-blocking depth in effect
@@ -105,7 +106,7 @@ void drop_graphs(pf_grid_s* g);
 int invalid(const char* fmt, ...);
 int check_grid(pf_grid_s* g);
 Geom grid_geom(const pf_grid_s* g);
-ModelParams make_params(int model, const double* c, double dt, double h);
+ModelParams make_params(int model, const double* c, double dt, double h, int stencil = 0);
 cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStream_t st);
 
 // ---- 3D TMA kernel (AC, GS): TMA tile ids 0 = 64x16, 1 = 128x8, 2 = 128x16

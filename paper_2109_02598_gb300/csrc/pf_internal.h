@@ -62,6 +62,13 @@ bool fe2d_supported(int model, int k);
 cudaError_t launch_fe2d(int model, int tile_id, int k, const Geom& g, FieldPtrs in,
                         FieldOut out, const ModelParams& m, cudaStream_t s);
 
+// Other Laplacian stencils in 2D (PF_ST_ISO, PF_ST_O4): tiles 0 (64x16) and 3 (128x32),
+// k in {1, 2}; PF_ST_STD forwards to launch_fe2d.
+bool fe2d_stencil_supported(int stencil, int tile_id, int k);
+cudaError_t launch_fe2d_stencil(int stencil, int model, int tile_id, int k, const Geom& g,
+                                FieldPtrs in, FieldOut out, const ModelParams& m,
+                                cudaStream_t s);
+
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
 //           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);
@@ -71,7 +78,7 @@ constexpr int kFirstTmaTile3D = 2;
 void tile3d_shape(int tile_id, int* tx, int* ty);
 int tile3d_id(int tx, int ty);
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
-                        const ModelParams& m, cudaStream_t s);
+                        const ModelParams& m, cudaStream_t s, int stencil = PF_ST_STD);
 
 // ---- batched 2D Gray-Scott (many independent grids, one launch per k steps) -------
 // Instance i: fields at buffer base + off (u) and base + off + pitch * ny (v).

@@ -29,10 +29,26 @@ namespace pf {
 //   CH: a0 = c1, a1 = c2, a2 = dt * M
 //   GS: a0 = Du, a1 = Dv, a2 = F, a3 = F + k
 //   C:  a0 = c1, a1 = c2, a2 = c3, a3 = c4, a4 = c5, a5 = 2 c5
+// lap_scale: the stencil's overall factor, 1/h^2 for the standard 5/7-point stencils,
+// 1/(6 h^2) for the isotropic 9/19-point ones, 1/(12 h^2) for the fourth-order 9-point one.
 struct ModelParams {
   float a0, a1, a2, a3, a4, a5;
   float dt;
-  float inv_h2;
+  float lap_scale;
+};
+
+// Laplacian stencils (Sec. 2.2.2).
+#define PF_ST_STD 0  // 5-point (2D) / 7-point (3D), second order
+#define PF_ST_ISO 1  // isotropic 9-point (2D) / 19-point (3D), second order
+#define PF_ST_O4 2   // fourth-order 9-point (2D): +-1 and +-2 along each axis
+
+static_assert(PF_ST_STD == PF_STENCIL_STD && PF_ST_ISO == PF_STENCIL_ISO &&
+                  PF_ST_O4 == PF_STENCIL_4TH,
+              "internal stencil ids follow the public ones");
+
+template <int ST>
+struct StencilTraits {
+  static constexpr int R = (ST == PF_ST_O4) ? 2 : 1;  // radius in sites
 };
 
 template <int MODEL>
@@ -59,15 +75,37 @@ struct ModelTraits<PF_MODEL_C> {
 };
 
 __device__ __forceinline__ float lap2d(float c, float xm, float xp, float ym, float yp,
-                                       float inv_h2) {
+                                       float lap_scale) {
   const float s = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp));
-  return __fmul_rn(__fmaf_rn(-4.0f, c, s), inv_h2);
+  return __fmul_rn(__fmaf_rn(-4.0f, c, s), lap_scale);
 }
 
 __device__ __forceinline__ float lap3d(float c, float xm, float xp, float ym, float yp,
-                                       float zm, float zp, float inv_h2) {
+                                       float zm, float zp, float lap_scale) {
   const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
-  return __fmul_rn(__fmaf_rn(-6.0f, c, s), inv_h2);
+  return __fmul_rn(__fmaf_rn(-6.0f, c, s), lap_scale);
+}
+
+// Isotropic 9-point: (4 (axial) + (diagonal) - 20 c) / (6 h^2)
+__device__ __forceinline__ float lap2d_iso(float c, float xm, float xp, float ym, float yp,
+                                           float d0, float d1, float d2, float d3, float scale) {
+  const float ax = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp));
+  const float dg = __fadd_rn(__fadd_rn(d0, d1), __fadd_rn(d2, d3));
+  return __fmul_rn(__fmaf_rn(-20.0f, c, __fmaf_rn(4.0f, ax, dg)), scale);
+}
+
+// Fourth-order 9-point: sum over axes of (16 (x[+1] + x[-1]) - (x[+2] + x[-2])) - 60 c,
+// over 12 h^2
+__device__ __forceinline__ float lap2d_o4(float c, float xm, float xp, float xm2, float xp2,
+                                          float ym, float yp, float ym2, float yp2, float scale) {
+  const float ax = __fmaf_rn(16.0f, __fadd_rn(xm, xp), -__fadd_rn(xm2, xp2));
+  const float ay = __fmaf_rn(16.0f, __fadd_rn(ym, yp), -__fadd_rn(ym2, yp2));
+  return __fmul_rn(__fmaf_rn(-60.0f, c, __fadd_rn(ax, ay)), scale);
+}
+
+// Isotropic 19-point: (2 (6 faces) + (12 edges) - 24 c) / (6 h^2); callers pass the sums.
+__device__ __forceinline__ float lap3d_iso(float c, float faces, float edges, float scale) {
+  return __fmul_rn(__fmaf_rn(-24.0f, c, __fmaf_rn(2.0f, faces, edges)), scale);
 }
 
 // Model A: phi + dt (lap + c1 phi - c2 phi^3)

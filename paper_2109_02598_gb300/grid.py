@@ -92,6 +92,13 @@ class Grid:
         self.dt = float(dt)
         return self
 
+    def set_stencil(self, stencil: str = "std"):
+        """Laplacian stencil: "std" (5/7-point), "iso" (isotropic 9/19-point) or "4th"
+        (fourth-order 9-point, 2D)."""
+        check(self._lib.pf_set_stencil(self._h, _lib.STENCIL_IDS[stencil]))
+        self.stencil = stencil
+        return self
+
     # ---------------------------------------------------------------- fields
     def write_field(self, field: int, data):
         """Copy in a dense float32 array of ``shape``: numpy (host) or torch (host/CUDA)."""

@@ -350,3 +350,72 @@ def test_model_c_invariants_and_energy(pf, shape):
     g.close()
     ref = oracle.run("c", x0, COEFFS["c"], DT["c"], 200)
     assert rel_l2(got, ref) <= 1e-4
+
+
+# ---------------------------------------------------------------- further stencils
+
+STENCIL_MAP = {"iso": "9iso", "4th": "9o4"}
+
+
+def gpu_run_st(pf, model, fields, n, stencil, dt, h=1.0, tuning=None):
+    g = pf.Grid(fields[0].shape, n_fields=len(fields), h=h)
+    g.set_stencil(stencil)
+    g.set_model(model, COEFFS[model], dt, force=True)
+    if tuning is not None:
+        g.set_tuning(*tuning)
+    g.write_fields(fields)
+    g.step(n)
+    out = g.read_fields()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("stencil", ["iso", "4th"])
+@pytest.mark.parametrize("shape", [(37, 150), (70, 33), (5, 7)])
+def test_2d_stencils_single_step_and_bitwise(pf, model, stencil, shape):
+    x0 = init_fields(model, shape, seed=21)
+    dt, h = DT[model] * 0.5, 0.9
+    ref = oracle.euler_step(model, x0, COEFFS[model], dt, h, stencil=STENCIL_MAP[stencil])
+    got = gpu_run_st(pf, model, x0, 1, stencil, dt, h)
+    assert rel_linf(got, ref) <= 1e-6
+    # every supported tile and depth gives the same bits
+    base = gpu_run_st(pf, model, x0, 6, stencil, dt, h, tuning=(64, 16, 1))
+    for t in [(64, 16, 2), (128, 32, 1), (128, 32, 2)]:
+        got = gpu_run_st(pf, model, x0, 6, stencil, dt, h, tuning=t)
+        for a, b in zip(base, got):
+            assert np.array_equal(a, b), t
+    ref6 = oracle.run(model, x0, COEFFS[model], dt, 6, h, stencil=STENCIL_MAP[stencil])
+    assert rel_linf(base, ref6) <= 1e-5
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("shape", [(9, 20, 70), (4, 4, 4), (6, 17, 33)])
+def test_3d_isotropic_stencil(pf, model, shape):
+    x0 = init_fields(model, shape, seed=22)
+    dt, h = DT[model] * 0.5, 0.9
+    ref = oracle.euler_step(model, x0, COEFFS[model], dt, h, stencil="19iso")
+    got = gpu_run_st(pf, model, x0, 1, "iso", dt, h)
+    assert rel_linf(got, ref) <= 1e-6
+    a = gpu_run_st(pf, model, x0, 5, "iso", dt, h, tuning=(32, 16, 1))
+    b = gpu_run_st(pf, model, x0, 5, "iso", dt, h, tuning=(64, 8, 1))
+    for p, q in zip(a, b):
+        assert np.array_equal(p, q)
+    ref5 = oracle.run(model, x0, COEFFS[model], dt, 5, h, stencil="19iso")
+    assert rel_linf(a, ref5) <= 1e-5
+
+
+def test_stencil_rules(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((8, 16, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
+    with pytest.raises(PfError):
+        g.set_stencil("4th")  # 2D only
+    g.set_stencil("iso")
+    assert g.tuning == (32, 16, 1)  # the general 3D kernel
+    with pytest.raises(PfError):
+        g.set_tuning(64, 16, 1)  # no TMA kernel with this stencil
+    g.close()
+    h = pf.Grid((64, 64), 1).set_model("ch", (1.0, 1.0, 1.0), 0.03, force=True)
+    with pytest.raises(PfError, match="stability"):
+        h.set_stencil("4th")  # dt beyond the fourth-order bound
+    h.close()
