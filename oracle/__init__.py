@@ -308,3 +308,104 @@ def gray_scott_final_and_loss(u0, v0, coeffs, dt, n_steps, u_target, v_target, h
     """Forward run then loss; returns (u_N, v_N, L)."""
     uN, vN = run("gs", (u0, v0), coeffs, dt, n_steps, h)
     return uN, vN, gray_scott_loss(uN, vN, u_target, v_target)
+
+
+# ------------------------------------------- semi-implicit Fourier spectral solver (Sec. 2.4.2)
+#
+# The paper's second solver: write dpsi/dt = L psi + sum_i N_i f_i(psi) with L and N_i linear
+# operators; in Fourier space (grad -> i k, lap -> -|k|^2) integrate the linear part exactly
+# over a step and hold the nonlinear terms fixed:
+#   psi_k(t + dt) = A psi_k(t) + B sum_i N_i(k) f_i(psi)_k,  A = exp(L dt),  B = (A - 1) / L
+# (B -> dt where L = 0).  Splits used here, all on the periodic grid of spacing h:
+#   Model A: L = -k^2 + c1,             N = 1,       f = -c2 psi^3
+#   Model B: L = M (-k^4 + c1 k^2),     N = -M k^2,  f = c2 m^3
+#   Model C: psi: L = -k^2 + c1, N = 1, f = -c2 psi^3 + 2 c5 psi m;
+#            m:   L = -k^4 + c3 k^2, N = -k^2, f = c4 m^3 - c5 psi^2
+
+def wavenumber_sq(shape, h: float = 1.0):
+    """|k|^2 on the real-to-complex FFT grid of ``shape`` (last axis halved)."""
+    ks = [2.0 * np.pi * np.fft.fftfreq(n, d=h) for n in shape[:-1]]
+    ks.append(2.0 * np.pi * np.fft.rfftfreq(shape[-1], d=h))
+    grids = np.meshgrid(*ks, indexing="ij")
+    return sum(g * g for g in grids)
+
+
+def _phi_b(Ldt, dt):
+    """(A, B) = (exp(L dt), (exp(L dt) - 1) / L) with the L -> 0 limit B = dt."""
+    A = np.exp(Ldt)
+    small = np.abs(Ldt) < 1e-12
+    B = np.where(small, dt * (1.0 + 0.5 * Ldt), np.expm1(Ldt) / np.where(small, 1.0, Ldt / dt))
+    return A, B
+
+
+def spectral_operators(model: str, shape, coeffs, dt: float, h: float = 1.0):
+    """Per field (A(k), B(k) N(k)) arrays of the semi-implicit scheme."""
+    k2 = wavenumber_sq(shape, h)
+    if model == "ac":
+        c1, c2 = coeffs
+        A, B = _phi_b((-k2 + c1) * dt, dt)
+        return [(A, B)]
+    if model == "ch":
+        c1, c2, M = coeffs
+        A, B = _phi_b(M * (-k2 * k2 + c1 * k2) * dt, dt)
+        return [(A, B * (-M * k2))]
+    if model == "c":
+        c1, c2, c3, c4, c5 = coeffs
+        Ap, Bp = _phi_b((-k2 + c1) * dt, dt)
+        Am, Bm = _phi_b((-k2 * k2 + c3 * k2) * dt, dt)
+        return [(Ap, Bp), (Am, Bm * (-k2))]
+    raise ValueError(f"the spectral solver takes models ac, ch, c (got {model!r})")
+
+
+def spectral_nonlinear(model: str, fields, coeffs):
+    """The nonlinear terms f_i (real space), one per field."""
+    if model == "ac":
+        c1, c2 = coeffs
+        return [-c2 * fields[0] ** 3]
+    if model == "ch":
+        c1, c2, M = coeffs
+        return [c2 * fields[0] ** 3]
+    c1, c2, c3, c4, c5 = coeffs
+    psi, m = fields
+    return [-c2 * psi ** 3 + 2.0 * c5 * psi * m, c4 * m ** 3 - c5 * psi ** 2]
+
+
+def spectral_run(model: str, fields, coeffs, dt: float, n_steps: int, h: float = 1.0):
+    """``n_steps`` semi-implicit spectral steps (Sec. 2.4.2) in FP64."""
+    x = tuple(_f64(f) for f in fields)
+    shape = x[0].shape
+    ops = spectral_operators(model, shape, coeffs, dt, h)
+    axes = tuple(range(len(shape)))
+    for _ in range(int(n_steps)):
+        nl = spectral_nonlinear(model, x, coeffs)
+        new = []
+        for xi, fi, (A, BN) in zip(x, nl, ops):
+            xk = np.fft.rfftn(xi, axes=axes)
+            fk = np.fft.rfftn(fi, axes=axes)
+            new.append(np.fft.irfftn(A * xk + BN * fk, s=shape, axes=axes))
+        x = tuple(new)
+    return x
+
+
+def structure_factor(psi, h: float = 1.0, n_bins: int = 32):
+    """Radially averaged S(k) = |rho_k|^2 / N of rho = 1 where psi > 0, else 0 (Sec. 3).
+
+    Uses the full (not half) spectrum; bins of width k_max / n_bins over |k| in
+    (0, k_max], k_max = pi / h * sqrt(d).  Returns (bin centres, mean S per bin, counts).
+    """
+    psi = _f64(psi)
+    rho = (psi > 0).astype(np.float64)
+    rk = np.fft.fftn(rho)
+    S = (rk * np.conj(rk)).real / rho.size
+    ks = np.meshgrid(*[2.0 * np.pi * np.fft.fftfreq(n, d=h) for n in psi.shape], indexing="ij")
+    kmag = np.sqrt(sum(k * k for k in ks))
+    kmax = np.pi / h * np.sqrt(psi.ndim)
+    idx = np.floor(kmag / kmax * n_bins).astype(np.int64)
+    idx = np.minimum(idx, n_bins - 1)
+    valid = kmag > 0
+    sums = np.bincount(idx[valid], weights=S[valid], minlength=n_bins)
+    counts = np.bincount(idx[valid], minlength=n_bins)
+    centres = (np.arange(n_bins) + 0.5) * kmax / n_bins
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
+    return centres, mean, counts
