@@ -242,6 +242,14 @@ int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval);
 int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int on_device,
                     float* dLdu0, float* dLdv0, double* dtheta);
 
+/* ------------------------------------------------------------------- self-test */
+
+/* Self-test of the bounded waits inside the TMA kernels: launches one CTA that waits on an
+ * mbarrier phase nothing completes, with a budget of budget_cycles SM clocks (in [1, 4e9]);
+ * the wait gives up, the kernel records it and the call returns PF_ERR_TIMEOUT, which is the
+ * expected result. Any other status means the path is broken. The GPU stays usable. */
+int pf_selftest_wait_timeout(int64_t budget_cycles, void* stream);
+
 /* ------------------------------------------------------- reduction without allocation */
 
 /* Mass or free energy (PF_REDUCE_*) of one caller-owned device field, written to a

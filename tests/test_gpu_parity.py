@@ -419,3 +419,18 @@ def test_stencil_rules(pf):
     with pytest.raises(PfError, match="stability"):
         h.set_stencil("4th")  # dt beyond the fourth-order bound
     h.close()
+
+
+def test_bounded_wait_times_out_and_reports(pf):
+    # a wait that nothing completes gives up after its budget and the status says so;
+    # the context stays usable afterwards
+    import torch
+    from paper_2109_02598_gb300 import _lib
+    lib = _lib.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.pf_selftest_wait_timeout(200000, None) == _lib.PF_ERR_TIMEOUT
+    assert b"bounded wait ran out" in lib.pf_last_error()
+    assert lib.pf_selftest_wait_timeout(200000, stream) == _lib.PF_ERR_TIMEOUT
+    x0 = init_fields("gs", (6, 16, 64), seed=30)
+    ref = oracle.euler_step("gs", x0, COEFFS["gs"], DT["gs"])
+    assert rel_linf(gpu_run(pf, "gs", x0, 1), ref) <= 1e-6
