@@ -242,6 +242,76 @@ int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval);
 int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int on_device,
                     float* dLdu0, float* dLdv0, double* dtheta);
 
+/* -------------------------------------------- semi-implicit Fourier spectral solver */
+
+/* The paper's second solver (Sec. 2.4.2). Each field's equation of motion is split into a
+ * linear part L(k) and a nonlinear part N(k) f_hat(psi) in Fourier space; one step is
+ *     psi_hat^{n+1}(k) = A(k) psi_hat^n(k) + B(k) N(k) f_hat(psi^n)(k),
+ *     A = exp(L dt),  B = (exp(L dt) - 1) / L   (B = dt where L = 0),
+ * with A and B N computed once, before the first step (Sec. 2.4.2). The splits, with
+ * |k|^2 the wavenumber of the periodic grid of spacing h:
+ *     Model A   L = -|k|^2 + c1,            N = 1,        f = -c2 psi^3;
+ *     Model B   L = M(-|k|^4 + c1 |k|^2),   N = -M |k|^2, f = c2 psi^3;
+ *     Model C   psi: L = -|k|^2 + c1,       N = 1,        f = -c2 psi^3 + 2 c5 psi m;
+ *               m:   L = -|k|^4 + c3 |k|^2, N = -|k|^2,   f = c4 m^3 - c5 psi^2.
+ * Fourier transforms are cuFFT's (loaded at the first call; PF_ERR_CUDA names it if it is
+ * missing); the nonlinear terms, the k-space update and the tables are this library's
+ * kernels. Arithmetic is float32; the tables are computed in float64 and rounded once.
+ * The state lives in Fourier space on the device; fields cross the boundary in real space
+ * as dense float32 arrays in the layout of pf_write_field. */
+typedef struct pf_spectral_s* pf_spectral_t;
+
+/* Create a spectral solver.
+ *   dim, n    as in pf_create_grid, with nx >= 2 and nx * ny * nz <= 2^30;
+ *   h         grid spacing, > 0;
+ *   model     PF_MODEL_AC, PF_MODEL_CH or PF_MODEL_C (coefficients as for pf_set_model);
+ *   dt        time step, > 0 (the scheme has no stability check: the nonlinear part is
+ *             explicit, and too large a dt blows up as it would on the CPU);
+ *   stream    cudaStream_t for all work (NULL = legacy default stream);
+ *   out       receives the handle. Fields start at zero.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_CUDA. */
+int pf_spectral_create(int dim, const int64_t* n, double h, int model, const double* coeffs,
+                       int n_coeffs, double dt, void* stream, pf_spectral_t* out);
+void pf_spectral_destroy(pf_spectral_t s);
+
+/* Replace field `field` (0 = psi or phi, 1 = m for Model C) by a dense float32 array,
+ * host or device. Host copies complete before the call returns; device copies are
+ * enqueued. Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
+int pf_spectral_write_field(pf_spectral_t s, int field, const float* src, int src_on_device);
+
+/* Real-space value of field `field` (an inverse transform of the state) into a dense
+ * float32 array; host destinations synchronize the stream. Errors as above. */
+int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_device);
+
+/* Advance n_steps >= 0 steps (asynchronous). Runs of 32 steps replay a recorded CUDA graph.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
+int pf_spectral_step(pf_spectral_t s, int64_t n_steps);
+int pf_spectral_synchronize(pf_spectral_t s);
+
+/* ----------------------------------------------------------------- structure factor */
+
+/* Radially averaged structure factor of the phase indicator rho = 1 where psi > 0, else 0,
+ * the analysis of the phase-separated systems of Sec. 3:
+ *     S(k) = |rho_hat(k)|^2 / N over the full spectrum (N = nx ny nz sites), binned by |k|
+ *     in (0, k_max], k_max = (pi / h) sqrt(dim), into n_bins bins of equal width; bin
+ *     b = min(floor(|k| / k_max * n_bins), n_bins - 1); k = 0 is left out.
+ *   dim, n, pitch  as in pf_reduce_noalloc (psi: float32 [nz][ny][pitch] on the device),
+ *                  with nx >= 2 and nx * ny * nz <= 2^30;
+ *   h              grid spacing, > 0;
+ *   n_bins         in [1, 1024];
+ *   centres, mean  host arrays of n_bins doubles: bin centres (b + 1/2) k_max / n_bins and the
+ *                  mean of S over the modes in the bin (0 for an empty bin);
+ *   counts         host array of n_bins int64: modes per bin (a mode and its mirror -k count
+ *                  separately, as in the full spectrum);
+ *   stream         cudaStream_t (NULL = legacy default stream); synchronized on return.
+ * The transform is a float64 cuFFT; |k| and the bin index are float64 in a fixed order of
+ * correctly rounded operations; the per-bin sums are in a fixed order, so the result is the
+ * same on every run. Scratch (about 16 bytes per site) is allocated and freed by the call.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_CUDA. */
+int pf_structure_factor(int dim, const int64_t* n, int64_t pitch, const float* psi, double h,
+                        int n_bins, double* centres, double* mean, int64_t* counts,
+                        void* stream);
+
 /* ------------------------------------------------------------------- self-test */
 
 /* Self-test of the bounded waits inside the TMA kernels: launches one CTA that waits on an

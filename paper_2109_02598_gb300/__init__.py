@@ -1,5 +1,6 @@
-"""GB300-native explicit forward-Euler step for phase-field (Allen-Cahn, Cahn-Hilliard)
-and reaction-diffusion (Gray-Scott) models on periodic 2D/3D grids (arxiv 2109.02598).
+"""GB300-native explicit forward-Euler step for phase-field (Allen-Cahn, Cahn-Hilliard,
+Model C) and reaction-diffusion (Gray-Scott) models on periodic 2D/3D grids, plus the
+semi-implicit Fourier spectral solver and the structure factor (arxiv 2109.02598).
 
 The compute path is libpfgpu.so (hand-written CUDA for sm_103a behind the C ABI of
 ``include/pfgpu.h``); this package only marshals arguments to it.
@@ -9,7 +10,7 @@ from .grid import Grid  # noqa: F401
 from .adjoint import (GrayScottAdjoint, PhaseFieldAdjoint, adjoint_backward,  # noqa: F401
                       adjoint_forward)
 from .batch import Batch, shard_instances  # noqa: F401
+from .spectral import Spectral, structure_factor  # noqa: F401
 
 __all__ = ["Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PhaseFieldAdjoint", "PfError",
-           "adjoint_backward",
-           "adjoint_forward", "load"]
+           "Spectral", "adjoint_backward", "adjoint_forward", "load", "structure_factor"]

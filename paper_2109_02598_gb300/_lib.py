@@ -78,6 +78,17 @@ SIGNATURES = {
     "pf_batch_info": (ctypes.c_int, [_vp, _c_int64_p, _c_int64_p]),
     "pf_adj_forward": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
     "pf_adj_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _c_double_p]),
+    "pf_spectral_create": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_double, ctypes.c_int,
+                                          _c_double_p, ctypes.c_int, ctypes.c_double, _vp,
+                                          ctypes.POINTER(_vp)]),
+    "pf_spectral_destroy": (None, [_vp]),
+    "pf_spectral_write_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_spectral_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_spectral_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pf_spectral_synchronize": (ctypes.c_int, [_vp]),
+    "pf_structure_factor": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int64, _vp,
+                                           ctypes.c_double, ctypes.c_int, _c_double_p,
+                                           _c_double_p, _c_int64_p, _vp]),
     "pf_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _vp]),
     "pf_reduce_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_int64_p, ctypes.c_int64,
                                          _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -33,6 +33,20 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpfgpu")
 
 
+def _cuda_libdir(nvcc: str) -> str:
+    """The toolkit directory holding libcufft.so.12 (cuFFT is loaded from there at run time
+    if the loader's search path does not have it)."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    cands = [os.path.join(root, "lib64"), os.path.join(root, "lib")]
+    tdir = os.path.join(root, "targets")
+    if os.path.isdir(tdir):
+        cands += [os.path.join(tdir, t, "lib") for t in sorted(os.listdir(tdir))]
+    for c in cands:
+        if os.path.exists(os.path.join(c, "libcufft.so.12")):
+            return c
+    return ""
+
+
 def _sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -54,12 +68,13 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     """Compile and link the library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     stamp_file = os.path.join(BUILD, "stamp.txt")
-    stamp = _stamp(extra_flags)
+    stamp = _stamp(list(extra_flags) + [_cuda_libdir(_nvcc())])
     if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
         if open(stamp_file).read().strip() == stamp:
             return LIB
     nvcc = _nvcc()
     srcs = _sources()
+    extra_flags = list(extra_flags) + [f'-DPF_CUDA_LIBDIR="{_cuda_libdir(nvcc)}"']
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
@@ -74,7 +89,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

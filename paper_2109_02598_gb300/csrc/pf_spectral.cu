@@ -1,0 +1,499 @@
+// Semi-implicit Fourier spectral solver (Sec. 2.4.2) for Models A, B and C (Sec. 3).
+//
+// State: the half spectrum psi_hat of every field, float2 [nf][cs] on the device (nk modes
+// per field, cs = nk rounded up to 32 so that every field starts on 256 bytes; real-space
+// fields likewise sit rs = nsite rounded up to 64 floats apart). Padding is zero and stays
+// zero: the transforms neither read nor write it and the kernels map zero to zero. One step:
+//   1. inverse transform of work = psi_hat / N  -> real, the fields in real space;
+//   2. nonlinear terms f(psi) in place on real (one pass over every field at each site);
+//   3. forward transform real -> work = f_hat;
+//   4. psi_hat <- A psi_hat + (B N) f_hat, and work <- psi_hat / N for the next step.
+// Keeping psi_hat (not psi) as the state costs two transforms per field and step instead of
+// three; work is rewritten by step 4 because cuFFT's complex-to-real transform overwrites
+// its input.  A and B N are computed once, in float64, and stored as float2 per mode.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "pf_cufft.h"
+#include "pf_internal.h"
+
+namespace pf {
+int invalid(const char* fmt, ...);
+}
+
+struct pf_spectral_s {
+  uint32_t magic;
+  int dim, model, nf;
+  int64_t d[3];       // C-order dims: (ny, nx) or (nz, ny, nx)
+  int64_t nsite, nk;  // real sites and half-spectrum modes per field
+  int64_t rs, cs;     // padded per-field strides of the real (floats) and complex arrays
+  double h, dt, coeffs[5];
+  float cf[5];        // coefficients rounded to float32 once
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  float2* state = nullptr;
+  float2* work = nullptr;
+  float2* table = nullptr;
+  float* real = nullptr;
+  void* fft_work = nullptr;
+  cufftHandle r2c_all = -1, c2r_all = -1, r2c_one = -1, c2r_one = -1;
+  cudaGraphExec_t chunk = nullptr;
+  bool graph_failed = false;
+  const pf::CufftApi* api = nullptr;
+};
+
+namespace pf {
+namespace {
+
+constexpr uint32_t kSpectralMagic = 0x53504543u;
+constexpr int kChunkSteps = 32;
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 8;
+
+struct SpecGeom {
+  int rank;
+  int64_t d[3];
+  int64_t nxh;  // d[rank-1] / 2 + 1
+  int64_t nk, cs;
+};
+
+// np.fft.fftfreq numerator of index i on an axis of n points: i, or i - n past the middle.
+__device__ __forceinline__ double fft_index(int64_t i, int64_t n) {
+  return (double)(i <= (n - 1) / 2 ? i : i - n);
+}
+
+// 2 pi f / (n h), as 2 pi * (f * (1 / (n h))).
+__device__ __forceinline__ double wavenumber(double f, int64_t n, double h) {
+  const double val = __ddiv_rn(1.0, __dmul_rn((double)n, h));
+  return __dmul_rn(2.0 * 3.141592653589793, __dmul_rn(f, val));
+}
+
+// |k|^2 of half-spectrum mode i (x the halved, fastest axis).
+__device__ double mode_k2(const SpecGeom& g, int64_t i, double h) {
+  const int64_t ix = i % g.nxh;
+  const int64_t rest = i / g.nxh;
+  const double kx = wavenumber((double)ix, g.d[g.rank - 1], h);
+  const int64_t ny = g.d[g.rank - 2];
+  const double ky = wavenumber(fft_index(rest % ny, ny), ny, h);
+  double s = __dmul_rn(ky, ky);
+  if (g.rank == 3) {
+    const double kz = wavenumber(fft_index(rest / ny, g.d[0]), g.d[0], h);
+    s = __dadd_rn(__dmul_rn(kz, kz), s);
+  }
+  return __dadd_rn(s, __dmul_rn(kx, kx));
+}
+
+// (A, B N) per mode and field, in float64, rounded to float32 (Sec. 2.4.2).
+__global__ void spectral_table_kernel(int model, SpecGeom g, double h, double dt, double c1,
+                                      double c3, double M, int nf, float2* __restrict__ table) {
+  const int64_t total = g.nk * nf;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(t / g.nk);
+    const int64_t i = t % g.nk;
+    const double k2 = mode_k2(g, i, h);
+    double L, N;
+    if (model == PF_MODEL_AC || (model == PF_MODEL_C && f == 0)) {
+      L = c1 - k2;
+      N = 1.0;
+    } else if (model == PF_MODEL_CH) {
+      L = M * (c1 * k2 - k2 * k2);
+      N = -M * k2;
+    } else {  // Model C, m
+      L = c3 * k2 - k2 * k2;
+      N = -k2;
+    }
+    const double Ldt = L * dt;
+    const double A = exp(Ldt);
+    const double B = fabs(Ldt) < 1e-12 ? dt * (1.0 + 0.5 * Ldt) : expm1(Ldt) / (Ldt / dt);
+    table[f * g.cs + i] = make_float2((float)A, (float)(B * N));
+  }
+}
+
+// Nonlinear terms in place (Sec. 3 equations, the part left after the linear split).
+template <int MODEL>
+__device__ __forceinline__ void nonlinear_site(float& p, float& m, const float* c) {
+  if (MODEL == PF_MODEL_AC) {  // -c2 psi^3
+    p = __fmul_rn(__fmul_rn(c[0], p), __fmul_rn(p, p));
+  } else if (MODEL == PF_MODEL_CH) {  // c2 psi^3
+    p = __fmul_rn(__fmul_rn(c[0], p), __fmul_rn(p, p));
+  } else {  // psi: psi (2 c5 m - c2 psi^2);  m: c4 m^3 - c5 psi^2
+    const float p2 = __fmul_rn(p, p);
+    const float fp = __fmul_rn(p, __fmaf_rn(c[1], m, __fmul_rn(c[0], p2)));
+    const float fm = __fmaf_rn(__fmul_rn(c[2], __fmul_rn(m, m)), m, __fmul_rn(c[3], p2));
+    p = fp;
+    m = fm;
+  }
+}
+
+struct NlCoeffs {
+  float c[4];
+};
+
+// Over rs / 4 float4 groups of every field (padding included: zero in, zero out).
+template <int MODEL>
+__global__ void spectral_nonlinear_kernel(float* __restrict__ real, int64_t rs, NlCoeffs k) {
+  float4* p4 = reinterpret_cast<float4*>(real);
+  float4* m4 = reinterpret_cast<float4*>(real + rs);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rs / 4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 p = p4[i];
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODEL == PF_MODEL_C) m = m4[i];
+    nonlinear_site<MODEL>(p.x, m.x, k.c);
+    nonlinear_site<MODEL>(p.y, m.y, k.c);
+    nonlinear_site<MODEL>(p.z, m.z, k.c);
+    nonlinear_site<MODEL>(p.w, m.w, k.c);
+    p4[i] = p;
+    if (MODEL == PF_MODEL_C) m4[i] = m;
+  }
+}
+
+__device__ __forceinline__ void update_mode(float2& s, float2& w, float A, float BN, float inv_n) {
+  s.x = __fmaf_rn(A, s.x, __fmul_rn(BN, w.x));
+  s.y = __fmaf_rn(A, s.y, __fmul_rn(BN, w.y));
+  w.x = __fmul_rn(s.x, inv_n);
+  w.y = __fmul_rn(s.y, inv_n);
+}
+
+// psi_hat <- A psi_hat + (B N) f_hat (f_hat arrives in work); work <- psi_hat / N.
+// Modes are taken two at a time (16-byte accesses); `total` (padding included) is even.
+__global__ void spectral_update_kernel(float2* __restrict__ state, float2* __restrict__ work,
+                                       const float2* __restrict__ table, int64_t total,
+                                       float inv_n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float4* s4 = reinterpret_cast<float4*>(state);
+  float4* w4 = reinterpret_cast<float4*>(work);
+  const float4* t4 = reinterpret_cast<const float4*>(table);
+  for (int64_t j = t0; j < total / 2; j += stride) {
+    const float4 tb = t4[j];
+    const float4 sv = s4[j];
+    const float4 wv = w4[j];
+    float2 sa = make_float2(sv.x, sv.y), sb = make_float2(sv.z, sv.w);
+    float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
+    update_mode(sa, wa, tb.x, tb.y, inv_n);
+    update_mode(sb, wb, tb.z, tb.w, inv_n);
+    s4[j] = make_float4(sa.x, sa.y, sb.x, sb.y);
+    w4[j] = make_float4(wa.x, wa.y, wb.x, wb.y);
+  }
+}
+
+__global__ void spectral_scale_kernel(const float2* __restrict__ src, float2* __restrict__ dst,
+                                      int64_t count, float inv_n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    dst[i] = make_float2(__fmul_rn(v.x, inv_n), __fmul_rn(v.y, inv_n));
+  }
+}
+
+int blocks_for(int64_t work_items) {
+  int64_t b = (work_items + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  return (int)(b < kMaxBlocks ? b : kMaxBlocks);
+}
+
+float inv_sites(const pf_spectral_s* s) { return (float)(1.0 / (double)s->nsite); }
+
+SpecGeom spec_geom(const pf_spectral_s* s) {
+  SpecGeom g{};
+  g.rank = s->dim;
+  for (int i = 0; i < s->dim; ++i) g.d[i] = s->d[i];
+  g.nxh = s->d[s->dim - 1] / 2 + 1;
+  g.nk = s->nk;
+  g.cs = s->cs;
+  return g;
+}
+
+cudaError_t launch_nonlinear(const pf_spectral_s* s, cudaStream_t st) {
+  NlCoeffs k{};
+  const int blocks = blocks_for(s->rs / 4);
+  if (s->model == PF_MODEL_AC) {
+    k.c[0] = -s->cf[1];  // -c2
+    spectral_nonlinear_kernel<PF_MODEL_AC><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
+  } else if (s->model == PF_MODEL_CH) {
+    k.c[0] = s->cf[1];  // c2
+    spectral_nonlinear_kernel<PF_MODEL_CH><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
+  } else {
+    k.c[0] = -s->cf[1];                    // -c2
+    k.c[1] = (float)(2.0 * s->coeffs[4]);  // 2 c5
+    k.c[2] = s->cf[3];                     // c4
+    k.c[3] = -s->cf[4];                    // -c5
+    spectral_nonlinear_kernel<PF_MODEL_C><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const float2* src, float2* dst, int64_t count, float inv_n,
+                         cudaStream_t st) {
+  spectral_scale_kernel<<<blocks_for(count), kThreads, 0, st>>>(src, dst, count, inv_n);
+  return cudaGetLastError();
+}
+
+// Enqueue one step on stream st.
+int enqueue_step(pf_spectral_s* s, cudaStream_t st) {
+  const CufftApi* api = s->api;
+  cufftResult r = api->set_stream(s->c2r_all, st);
+  if (r == CUFFT_SUCCESS)
+    r = api->exec_c2r(s->c2r_all, reinterpret_cast<cufftComplex*>(s->work), s->real);
+  if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_step inverse transform");
+  PF_CUDA_TRY(launch_nonlinear(s, st));
+  r = api->set_stream(s->r2c_all, st);
+  if (r == CUFFT_SUCCESS)
+    r = api->exec_r2c(s->r2c_all, s->real, reinterpret_cast<cufftComplex*>(s->work));
+  if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_step forward transform");
+  const int64_t total = s->cs * s->nf;
+  spectral_update_kernel<<<blocks_for(total / 2), kThreads, 0, st>>>(
+      s->state, s->work, s->table, total, inv_sites(s));
+  PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
+
+// Record kChunkSteps steps into a graph (once). A capture that fails leaves the solver on
+// direct launches (same kernels, same results).
+void ensure_chunk_graph(pf_spectral_s* s) {
+  if (s->chunk != nullptr || s->graph_failed) return;
+  if (s->capture == nullptr &&
+      cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    s->graph_failed = true;
+    cudaGetLastError();
+    return;
+  }
+  if (cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    s->graph_failed = true;
+    cudaGetLastError();
+    return;
+  }
+  int rc = PF_OK;
+  for (int i = 0; i < kChunkSteps && rc == PF_OK; ++i) rc = enqueue_step(s, s->capture);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->capture, &graph);
+  if (rc == PF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&s->chunk, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != PF_OK || e != cudaSuccess) {
+    s->chunk = nullptr;
+    s->graph_failed = true;
+    cudaGetLastError();
+  }
+}
+
+int check_spectral(pf_spectral_s* s) {
+  if (s == nullptr || s->magic != kSpectralMagic) return invalid("invalid spectral handle");
+  return PF_OK;
+}
+
+void release(pf_spectral_s* s) {
+  if (s->chunk) cudaGraphExecDestroy(s->chunk);
+  if (s->api) {
+    for (cufftHandle p : {s->r2c_all, s->c2r_all, s->r2c_one, s->c2r_one})
+      if (p != -1) s->api->destroy(p);
+  }
+  cudaFree(s->state);
+  cudaFree(s->work);
+  cudaFree(s->table);
+  cudaFree(s->real);
+  cudaFree(s->fft_work);
+  if (s->capture) cudaStreamDestroy(s->capture);
+  s->magic = 0;
+  delete s;
+}
+
+}  // namespace
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" {
+
+int pf_spectral_create(int dim, const int64_t* n, double h, int model, const double* coeffs,
+                       int n_coeffs, double dt, void* stream, pf_spectral_t* out) {
+  if (out == nullptr || n == nullptr) return invalid("pf_spectral_create: NULL argument");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return invalid("dim must be 2 or 3 (got %d)", dim);
+  const int64_t nx = n[0], ny = n[1], nz = dim == 3 ? n[2] : 1;
+  const int64_t lim = (int64_t)1 << 30;
+  if (nx < 2 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim || nx * ny > lim ||
+      nx * ny * nz > lim)
+    return invalid("sizes must be nx >= 2, ny, nz >= 1, with at most 2^30 sites (got %lld x "
+                   "%lld x %lld)", (long long)nx, (long long)ny, (long long)nz);
+  if (!(h > 0.0) || !std::isfinite(h)) return invalid("h must be finite and > 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("dt must be finite and > 0");
+  int want = 0, nf = 1;
+  if (model == PF_MODEL_AC) want = 2;
+  else if (model == PF_MODEL_CH) want = 3;
+  else if (model == PF_MODEL_C) want = 5, nf = 2;
+  else return invalid("the spectral solver takes Models A, B and C (got model %d)", model);
+  if (coeffs == nullptr || n_coeffs != want)
+    return invalid("model %d takes %d coefficients (got %d)", model, want, n_coeffs);
+  for (int i = 0; i < want; ++i)
+    if (!std::isfinite(coeffs[i])) return invalid("coefficient %d is not finite", i);
+  if (model == PF_MODEL_CH && !(coeffs[2] > 0.0)) return invalid("mobility M must be > 0");
+
+  const CufftApi* api = cufft_api();
+  if (api == nullptr) return PF_ERR_CUDA;
+
+  pf_spectral_s* s = new (std::nothrow) pf_spectral_s();
+  if (s == nullptr) return invalid("host allocation failed");
+  s->magic = kSpectralMagic;
+  s->dim = dim;
+  s->model = model;
+  s->nf = nf;
+  if (dim == 2) {
+    s->d[0] = ny;
+    s->d[1] = nx;
+  } else {
+    s->d[0] = nz;
+    s->d[1] = ny;
+    s->d[2] = nx;
+  }
+  s->nsite = nx * ny * nz;
+  s->nk = (nx / 2 + 1) * ny * nz;
+  s->rs = (s->nsite + 63) / 64 * 64;
+  s->cs = (s->nk + 31) / 32 * 32;
+  s->h = h;
+  s->dt = dt;
+  for (int i = 0; i < 5; ++i) s->coeffs[i] = i < want ? coeffs[i] : 0.0;
+  for (int i = 0; i < 5; ++i) s->cf[i] = (float)s->coeffs[i];
+  s->stream = (cudaStream_t)stream;
+  s->api = api;
+
+  const size_t cbytes = sizeof(float2) * (size_t)(s->cs * nf);
+  const size_t rbytes = sizeof(float) * (size_t)(s->rs * nf);
+  cudaError_t e = cudaMalloc(&s->state, cbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->work, cbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->table, cbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->real, rbytes);
+  if (e != cudaSuccess) {
+    int rc = e == cudaErrorMemoryAllocation ? (set_error("pf_spectral_create: out of device memory"), PF_ERR_OOM)
+                                            : cuda_fail(e, "pf_spectral_create allocation");
+    cudaGetLastError();
+    release(s);
+    return rc;
+  }
+  // Plans: all fields at once for the steps, one field for reads and writes; one shared
+  // work area (every transform runs on the solver's stream, one after another).
+  size_t w[4] = {0, 0, 0, 0};
+  int rc = cufft_plan(api, &s->r2c_all, dim, s->d, CUFFT_R2C, nf, s->rs, s->cs, 0, &w[0]);
+  if (rc == PF_OK)
+    rc = cufft_plan(api, &s->c2r_all, dim, s->d, CUFFT_C2R, nf, s->rs, s->cs, 0, &w[1]);
+  if (rc == PF_OK && nf > 1)
+    rc = cufft_plan(api, &s->r2c_one, dim, s->d, CUFFT_R2C, 1, s->rs, s->cs, 0, &w[2]);
+  if (rc == PF_OK && nf > 1)
+    rc = cufft_plan(api, &s->c2r_one, dim, s->d, CUFFT_C2R, 1, s->rs, s->cs, 0, &w[3]);
+  if (rc != PF_OK) {
+    release(s);
+    return rc;
+  }
+  size_t wmax = 0;
+  for (size_t x : w) wmax = x > wmax ? x : wmax;
+  if (wmax > 0) {
+    e = cudaMalloc(&s->fft_work, wmax);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pf_spectral_create: out of device memory (transform work area)");
+      release(s);
+      return PF_ERR_OOM;
+    }
+  }
+  for (cufftHandle p : {s->r2c_all, s->c2r_all, s->r2c_one, s->c2r_one}) {
+    if (p == -1) continue;
+    cufftResult r = api->set_work_area(p, s->fft_work);
+    if (r != CUFFT_SUCCESS) {
+      rc = cufft_fail(r, "cufftSetWorkArea");
+      release(s);
+      return rc;
+    }
+  }
+  // Tables, zero state.
+  const SpecGeom g = spec_geom(s);
+  const double M = model == PF_MODEL_CH ? s->coeffs[2] : 1.0;
+  e = cudaMemsetAsync(s->table, 0, cbytes, s->stream);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "pf_spectral_create tables");
+    release(s);
+    return rc;
+  }
+  spectral_table_kernel<<<blocks_for(s->nk * nf), kThreads, 0, s->stream>>>(
+      model, g, h, dt, s->coeffs[0], model == PF_MODEL_C ? s->coeffs[2] : 0.0, M, nf, s->table);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->state, 0, cbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->work, 0, cbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->real, 0, rbytes, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "pf_spectral_create tables");
+    release(s);
+    return rc;
+  }
+  *out = s;
+  return PF_OK;
+}
+
+void pf_spectral_destroy(pf_spectral_t s) {
+  if (s == nullptr || s->magic != kSpectralMagic) return;
+  cudaStreamSynchronize(s->stream);
+  release(s);
+}
+
+int pf_spectral_write_field(pf_spectral_t s, int field, const float* src, int src_on_device) {
+  if (int rc = check_spectral(s)) return rc;
+  if (field < 0 || field >= s->nf) return invalid("field %d out of range [0, %d)", field, s->nf);
+  if (src == nullptr) return invalid("src is NULL");
+  float* real = s->real + field * s->rs;
+  float2* st = s->state + field * s->cs;
+  PF_CUDA_TRY(cudaMemcpyAsync(real, src, sizeof(float) * (size_t)s->nsite,
+                              src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              s->stream));
+  const cufftHandle plan = s->nf > 1 ? s->r2c_one : s->r2c_all;
+  cufftResult r = s->api->set_stream(plan, s->stream);
+  if (r == CUFFT_SUCCESS) r = s->api->exec_r2c(plan, real, reinterpret_cast<cufftComplex*>(st));
+  if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_write_field transform");
+  PF_CUDA_TRY(launch_scale(st, s->work + field * s->cs, s->nk, inv_sites(s), s->stream));
+  if (!src_on_device) PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_device) {
+  if (int rc = check_spectral(s)) return rc;
+  if (field < 0 || field >= s->nf) return invalid("field %d out of range [0, %d)", field, s->nf);
+  if (dst == nullptr) return invalid("dst is NULL");
+  float* real = s->real + field * s->rs;
+  float2* wk = s->work + field * s->cs;
+  const cufftHandle plan = s->nf > 1 ? s->c2r_one : s->c2r_all;
+  cufftResult r = s->api->set_stream(plan, s->stream);
+  if (r == CUFFT_SUCCESS) r = s->api->exec_c2r(plan, reinterpret_cast<cufftComplex*>(wk), real);
+  if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_read_field transform");
+  PF_CUDA_TRY(cudaMemcpyAsync(dst, real, sizeof(float) * (size_t)s->nsite,
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              s->stream));
+  // the inverse transform consumed work: restore psi_hat / N
+  PF_CUDA_TRY(launch_scale(s->state + field * s->cs, wk, s->nk, inv_sites(s), s->stream));
+  if (!dst_on_device) PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+int pf_spectral_step(pf_spectral_t s, int64_t n_steps) {
+  if (int rc = check_spectral(s)) return rc;
+  if (n_steps < 0) return invalid("n_steps must be >= 0");
+  int64_t left = n_steps;
+  if (left >= kChunkSteps) ensure_chunk_graph(s);
+  if (s->chunk != nullptr) {
+    for (; left >= kChunkSteps; left -= kChunkSteps)
+      PF_CUDA_TRY(cudaGraphLaunch(s->chunk, s->stream));
+  }
+  for (; left > 0; --left)
+    if (int rc = enqueue_step(s, s->stream)) return rc;
+  return PF_OK;
+}
+
+int pf_spectral_synchronize(pf_spectral_t s) {
+  if (int rc = check_spectral(s)) return rc;
+  PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+}  // extern "C"

@@ -177,3 +177,13 @@ class Grid:
         check(self._lib.pf_autotune(self._h, probe_launches, ctypes.byref(a), ctypes.byref(b),
                                     ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    # ---------------------------------------------------------------- analysis
+    def structure_factor(self, field: int = 0, n_bins: int = 32):
+        """Radially averaged S(|k|) of [field > 0] (Sec. 3), read in place on the GPU."""
+        from .spectral import structure_factor_view
+        ptr, pitch, plane = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.pf_field_view(self._h, field, ctypes.byref(ptr), ctypes.byref(pitch),
+                                      ctypes.byref(plane)))
+        return structure_factor_view(ptr.value, self.shape, pitch.value, self.h, n_bins,
+                                     self.stream)

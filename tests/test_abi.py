@@ -60,3 +60,34 @@ def test_loader_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = saved
+
+
+def test_spectral_and_structure_factor_reject_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(16, 16, 16)
+    c2 = (ctypes.c_double * 5)(1.0, 1.0, 1.0, 1.0, 1.0)
+    INV = _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_spectral_create(2, n, 1.0, 3, c2, 4, 0.1, None, ctypes.byref(h)) == INV
+    assert "Models A, B and C" in _err(lib)
+    assert lib.pf_spectral_create(2, n, 1.0, 1, c2, 3, 0.1, None, ctypes.byref(h)) == INV
+    assert lib.pf_spectral_create(2, n, 1.0, 1, c2, 2, 0.0, None, ctypes.byref(h)) == INV
+    assert lib.pf_spectral_create(2, n, 0.0, 1, c2, 2, 0.1, None, ctypes.byref(h)) == INV
+    assert lib.pf_spectral_create(4, n, 1.0, 1, c2, 2, 0.1, None, ctypes.byref(h)) == INV
+    big = (ctypes.c_int64 * 3)(1 << 15, 1 << 15, 2)
+    assert lib.pf_spectral_create(3, big, 1.0, 1, c2, 2, 0.1, None, ctypes.byref(h)) == INV
+    thin = (ctypes.c_int64 * 3)(1, 16, 1)
+    assert lib.pf_spectral_create(2, thin, 1.0, 1, c2, 2, 0.1, None, ctypes.byref(h)) == INV
+    assert lib.pf_spectral_step(None, 1) == INV
+    assert lib.pf_spectral_write_field(None, 0, None, 0) == INV
+    assert lib.pf_spectral_read_field(None, 0, None, 0) == INV
+    assert lib.pf_spectral_synchronize(None) == INV
+    lib.pf_spectral_destroy(None)  # no-op
+    cen = (ctypes.c_double * 8)()
+    mean = (ctypes.c_double * 8)()
+    cnt = (ctypes.c_int64 * 8)()
+    fake = ctypes.c_void_p(256)  # never dereferenced: every call below fails validation
+    assert lib.pf_structure_factor(2, n, 16, fake, 1.0, 0, cen, mean, cnt, None) == INV
+    assert lib.pf_structure_factor(2, n, 16, fake, 1.0, 1025, cen, mean, cnt, None) == INV
+    assert lib.pf_structure_factor(2, n, 15, fake, 1.0, 8, cen, mean, cnt, None) == INV
+    assert lib.pf_structure_factor(2, n, 16, None, 1.0, 8, cen, mean, cnt, None) == INV
+    assert lib.pf_structure_factor(2, n, 16, fake, -1.0, 8, cen, mean, cnt, None) == INV
