@@ -140,10 +140,10 @@ def paper_timing_init(model: str, shape, seed: int = 6):
     return (f0, uniform(seed, 31, n, -1.0, 1.0).reshape(shape).astype(np.float32))
 
 
-# The paper's performance workloads (Sec. 3.1 table), run here with the forward-Euler
-# solver: Models A and C on 128^2, 512^2 and 64^3 for 10^4 iterations.  `paper_best_s` is
-# the fastest whole-program time the paper reports for that case (min over its three CPUs,
-# semi-implicit spectral solver) -- context, not a like-for-like target.
+# The paper's performance workloads (Sec. 3.1 table), run here with both solvers: Models A
+# and C on 128^2, 512^2 and 64^3 for 10^4 iterations.  `paper_best_s` is the fastest
+# whole-program time the paper reports for that case (min over its three CPUs, semi-implicit
+# spectral solver) -- context from other hardware, not a target.
 PAPER_TABLE = [
     dict(model="ac", shape=(128, 128), coeffs=(1.0, 1.0), dt=0.05, paper_best_s=1.7),
     dict(model="ac", shape=(512, 512), coeffs=(1.0, 1.0), dt=0.05, paper_best_s=32.6),
