@@ -33,6 +33,8 @@ Parity status: every function here is pinned by the tests in ``tests/test_oracle
 """
 from __future__ import annotations
 
+import itertools
+
 import numpy as np
 
 MODELS = ("ac", "ch", "gs", "c")
@@ -60,13 +62,15 @@ def laplacian(phi, h: float = 1.0):
 
 
 # Further Laplacian stencils of Sec. 2.2.2 (second-order isotropic 9-point in 2D and
-# 19-point in 3D; fourth-order 9-point in 2D), written from their weights:
+# 19- and 27-point in 3D; fourth-order 9-point in 2D), written from their weights:
 #   "9iso":  (1/6h^2) [4 (axial neighbours) + (diagonal neighbours) - 20 phi]
 #   "9o4":   (1/12h^2) sum over axes [16 (phi[+1] + phi[-1]) - (phi[+2] + phi[-2]) - 30 phi]
 #   "19iso": (1/6h^2) [2 (face neighbours) + (edge neighbours) - 24 phi]
+#   "27iso": (1/30h^2) [14 (face neighbours) + 3 (edge neighbours) + (corner neighbours)
+#            - 128 phi]
 # "std" is the 5-point (2D) / 7-point (3D) stencil above.
 STENCILS_2D = ("std", "9iso", "9o4")
-STENCILS_3D = ("std", "19iso")
+STENCILS_3D = ("std", "19iso", "27iso")
 
 
 def laplacian_stencil(phi, h: float = 1.0, stencil: str = "std"):
@@ -98,6 +102,19 @@ def laplacian_stencil(phi, h: float = 1.0, stencil: str = "std"):
                     for sb in (1, -1):
                         edges += np.roll(np.roll(phi, sa, axis=a), sb, axis=b)
         return (2.0 * faces + edges - 24.0 * phi) / (6.0 * h * h)
+    if stencil == "27iso" and d == 3:
+        faces = np.zeros_like(phi)
+        edges = np.zeros_like(phi)
+        corners = np.zeros_like(phi)
+        for o in itertools.product((-1, 0, 1), repeat=3):
+            nz = sum(1 for x in o if x != 0)
+            if nz == 1:
+                faces += sh(phi, *o)
+            elif nz == 2:
+                edges += sh(phi, *o)
+            elif nz == 3:
+                corners += sh(phi, *o)
+        return (14.0 * faces + 3.0 * edges + corners - 128.0 * phi) / (30.0 * h * h)
     raise ValueError(f"stencil {stencil!r} is not defined for {d}D")
 
 

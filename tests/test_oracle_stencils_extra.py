@@ -1,5 +1,6 @@
 """Pins of the oracle's further Laplacian stencils (Sec. 2.2.2: the isotropic 9-point 2D and
-19-point 3D second-order stencils, the fourth-order 9-point 2D stencil) against closed forms:
+19- and 27-point 3D second-order stencils, the fourth-order 9-point 2D stencil) against
+closed forms:
 Fourier symbols, exactness on polynomials, isotropy of the leading error, and the structure
 of the stencil matrix."""
 import itertools
@@ -21,11 +22,17 @@ def _symbol(stencil, k, h):
     if stencil == "19iso":
         c = [np.cos(t) for t in a]
         return (4.0 * sum(c) + 4.0 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]) - 24.0) / (6.0 * h * h)
+    if stencil == "27iso":
+        # faces 2 cos, edges 4 cos cos per axis pair, corners 8 cos cos cos
+        c = [np.cos(t) for t in a]
+        pairs = c[0] * c[1] + c[0] * c[2] + c[1] * c[2]
+        return (28.0 * sum(c) + 12.0 * pairs + 8.0 * c[0] * c[1] * c[2] - 128.0) / (30.0 * h * h)
     return -(4.0 / (h * h)) * sum(np.sin(t / 2) ** 2 for t in a)
 
 
 @pytest.mark.parametrize("stencil,shape,h", [("9iso", (16, 12), 0.7), ("9o4", (14, 18), 1.3),
-                                             ("19iso", (8, 10, 6), 0.9), ("std", (8, 6, 10), 1.0)])
+                                             ("19iso", (8, 10, 6), 0.9), ("std", (8, 6, 10), 1.0),
+                                             ("27iso", (6, 8, 10), 1.1)])
 def test_fourier_symbol(stencil, shape, h):
     rng = np.random.default_rng(1)
     coords = np.meshgrid(*[np.arange(n) * h for n in shape], indexing="ij")
@@ -53,8 +60,9 @@ def test_second_order_stencils_are_exact_on_quadratics():
                                    atol=1e-9)
     z, y, x = np.meshgrid(*[np.arange(20) * h] * 3, indexing="ij")
     g = x * x + 2.0 * y * y - z * z + x * y + y * z
-    lap = oracle.laplacian_stencil(g, h, "19iso")
-    np.testing.assert_allclose(lap[_interior(g.shape, 1)], 2 + 4 - 2, rtol=0, atol=1e-9)
+    for st in ("19iso", "27iso"):
+        lap = oracle.laplacian_stencil(g, h, st)
+        np.testing.assert_allclose(lap[_interior(g.shape, 1)], 2 + 4 - 2, rtol=0, atol=1e-9)
 
 
 def test_fourth_order_stencil_is_exact_on_quartics():
@@ -69,7 +77,8 @@ def test_fourth_order_stencil_is_exact_on_quartics():
     assert np.abs(oracle.laplacian_stencil(f, h, "std")[sl] - exact[sl]).max() > 1e-3
 
 
-@pytest.mark.parametrize("iso,std,dim", [("9iso", "std", 2), ("19iso", "std", 3)])
+@pytest.mark.parametrize("iso,std,dim", [("9iso", "std", 2), ("19iso", "std", 3),
+                                         ("27iso", "std", 3)])
 def test_isotropic_stencils_have_isotropic_leading_error(iso, std, dim):
     # eigenvalue along an axis vs along a diagonal at the same |k|: the isotropic stencils
     # agree to O(k^6), the standard one differs at O(k^4)
@@ -81,10 +90,17 @@ def test_isotropic_stencils_have_isotropic_leading_error(iso, std, dim):
     assert aniso_iso < 1e-6 < aniso_std
     # and both approximate -k^2
     assert abs(_symbol(iso, diag, 1.0) + kk * kk) < 1e-4
+    # isotropy at O(k^4) holds along every direction, not only the two above
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        u = rng.standard_normal(dim)
+        u *= kk / np.linalg.norm(u)
+        assert abs(_symbol(iso, u, 1.0) - _symbol(iso, axis, 1.0)) < 1e-6
 
 
 @pytest.mark.parametrize("stencil,shape,points", [("9iso", (6, 7), 9), ("9o4", (7, 6), 9),
-                                                  ("19iso", (5, 5, 6), 19)])
+                                                  ("19iso", (5, 5, 6), 19),
+                                                  ("27iso", (5, 6, 5), 27)])
 def test_stencil_matrix_support_symmetry_and_zero_row_sums(stencil, shape, points):
     n = int(np.prod(shape))
     L = np.zeros((n, n))
@@ -107,3 +123,16 @@ def test_allen_cahn_linear_closed_form_with_isotropic_stencil():
     out, = oracle.run("ac", (phi0,), (c1, 0.0), dt, n, h, stencil="9iso")
     g = 1.0 + dt * (_symbol("9iso", k, h) + c1)
     np.testing.assert_allclose(out, g ** n * phi0, rtol=0, atol=1e-12)
+
+
+def test_27_point_weights_by_direction_class():
+    # a unit impulse: the stencil's value at each offset is its weight; 14/3/1 per face, edge
+    # and corner neighbour and -128 at the centre, over 30 h^2
+    h = 0.5
+    e = np.zeros((5, 5, 5))
+    e[2, 2, 2] = 1.0
+    L = oracle.laplacian_stencil(e, h, "27iso") * (30.0 * h * h)
+    for o in itertools.product((-1, 0, 1), repeat=3):
+        w = {0: -128.0, 1: 14.0, 2: 3.0, 3: 1.0}[sum(1 for x in o if x)]
+        assert L[2 + o[0], 2 + o[1], 2 + o[2]] == w
+    assert np.count_nonzero(L) == 27
