@@ -426,3 +426,23 @@ def structure_factor(psi, h: float = 1.0, n_bins: int = 32):
     with np.errstate(invalid="ignore", divide="ignore"):
         mean = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
     return centres, mean, counts
+
+
+def porod_fit(centres, mean, counts, k_lo: float, k_hi: float):
+    """Least-squares line log S = slope log k + intercept through the bins with centres in
+    [k_lo, k_hi], a non-zero count and S > 0: the Porod-law check of Sec. 3 (Eq. for Porod's
+    law, S ~ k^-(d+1)). Returns (slope, intercept, bins used)."""
+    xs, ys = [], []
+    for c, m, n in zip(centres, mean, counts):
+        if k_lo <= c <= k_hi and n > 0 and m > 0:
+            xs.append(np.log(float(c)))
+            ys.append(np.log(float(m)))
+    n = len(xs)
+    if n < 2:
+        raise ValueError("fewer than two usable bins in the window")
+    xbar = sum(xs) / n
+    ybar = sum(ys) / n
+    sxy = sum((x - xbar) * (y - ybar) for x, y in zip(xs, ys))
+    sxx = sum((x - xbar) * (x - xbar) for x in xs)
+    slope = sxy / sxx
+    return slope, ybar - slope * xbar, n
