@@ -436,7 +436,7 @@ def paper_table_spectral(stream):
                              stream=stream)
             sp.write_fields(x0)
             sp.step(nsteps)
-            sp.read_fields()
+            final = sp.read_fields()
             e2e_s = time.perf_counter() - t0
             sp.close()
             sites = int(np.prod(case["shape"]))
@@ -446,7 +446,9 @@ def paper_table_spectral(stream):
                          "us_per_step": dev_ms * 1e3 / nsteps,
                          "mlups": sites * nsteps / (dev_ms * 1e-3) / 1e6,
                          "paper_best_cpu_s": case["paper_best_s"],
-                         "paper_best_over_e2e": case["paper_best_s"] / e2e_s})
+                         "paper_best_over_e2e": case["paper_best_s"] / e2e_s,
+                         "final_finite": bool(all(np.isfinite(x).all() for x in final)),
+                         "final_max_abs": float(max(np.abs(x).max() for x in final))})
     return {"rows": rows,
             "note": "same solver, sizes, step count and initial conditions as the paper's "
                     "table; its times are whole-program runs on 2016-2017 desktop CPUs"}

@@ -68,6 +68,8 @@ extern "C" {
                             (2 faces, 1 edges, -24)/6h^2                     (Sec. 2.2.2) */
 #define PF_STENCIL_4TH 2 /* fourth order, 9-point (2D only): per axis
                             (-1, 16, -30, 16, -1)/12h^2                     (Sec. 2.2.2) */
+#define PF_STENCIL_ISO27 3 /* second order, isotropic leading error, 27-point (3D only):
+                              (14 faces, 3 edges, 1 corners, -128)/30h^2   (Sec. 2.2.2) */
 
 /* ---------------------------------------------------------------- reductions */
 #define PF_REDUCE_MASS 1   /* h^d * sum_x phi_x of one field                         */
@@ -141,7 +143,8 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out);
  * stencil families). Model B and Model C apply it twice. The tuning returns to the default
  * for the stencil. The isotropic and fourth-order stencils run with 2D tiles 64x16 or
  * 128x32 (k <= 2) and with the general 3D kernel (k = 1); the batch and the adjoint use the
- * standard stencil. Errors: PF_ERR_INVALID_ARG (unknown stencil; fourth order in 3D),
+ * standard stencil. Errors: PF_ERR_INVALID_ARG (unknown stencil; fourth order in 3D;
+ * 27-point in 2D),
  * PF_ERR_UNSTABLE_DT (the current dt exceeds the bound for the new stencil; nothing changed). */
 int pf_set_stencil(pf_grid_t g, int stencil);
 
@@ -311,6 +314,19 @@ int pf_spectral_synchronize(pf_spectral_t s);
 int pf_structure_factor(int dim, const int64_t* n, int64_t pitch, const float* psi, double h,
                         int n_bins, double* centres, double* mean, int64_t* counts,
                         void* stream);
+
+/* Porod-law check (Sec. 3, Porod's law S ~ (L k^(d+1))^-1): the least-squares line
+ *     log S = slope * log k + intercept
+ * through the bins of a pf_structure_factor result whose centre lies in [k_lo, k_hi], whose
+ * count is > 0 and whose mean S is > 0 (slope near -(d+1) in the scaling regime).
+ *   n_bins, centres, mean, counts  host arrays as pf_structure_factor returns them;
+ *   slope, intercept, n_used       receive the fit and the number of bins it used.
+ * Host arithmetic in float64 only (no device work): sums in bin order, then
+ * slope = sum (x - xbar)(y - ybar) / sum (x - xbar)^2.
+ * Errors: PF_ERR_INVALID_ARG (NULL pointer, n_bins < 1, k_lo >= k_hi, fewer than two usable
+ * bins). */
+int pf_porod_fit(int n_bins, const double* centres, const double* mean, const int64_t* counts,
+                 double k_lo, double k_hi, double* slope, double* intercept, int* n_used);
 
 /* ------------------------------------------------------------------- self-test */
 

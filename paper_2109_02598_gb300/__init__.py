@@ -10,7 +10,8 @@ from .grid import Grid  # noqa: F401
 from .adjoint import (GrayScottAdjoint, PhaseFieldAdjoint, adjoint_backward,  # noqa: F401
                       adjoint_forward)
 from .batch import Batch, shard_instances  # noqa: F401
-from .spectral import Spectral, structure_factor  # noqa: F401
+from .spectral import Spectral, porod_fit, structure_factor  # noqa: F401
 
 __all__ = ["Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PhaseFieldAdjoint", "PfError",
-           "Spectral", "adjoint_backward", "adjoint_forward", "load", "structure_factor"]
+           "Spectral", "adjoint_backward", "adjoint_forward", "load", "porod_fit",
+           "structure_factor"]

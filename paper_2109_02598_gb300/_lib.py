@@ -29,7 +29,7 @@ PF_MODEL_C = 4
 MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS, "c": PF_MODEL_C}
 MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2, "c": 2}
 
-STENCIL_IDS = {"std": 0, "iso": 1, "4th": 2}
+STENCIL_IDS = {"std": 0, "iso": 1, "4th": 2, "iso27": 3}
 
 PF_REDUCE_MASS = 1
 PF_REDUCE_ENERGY = 2
@@ -89,6 +89,9 @@ SIGNATURES = {
     "pf_structure_factor": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int64, _vp,
                                            ctypes.c_double, ctypes.c_int, _c_double_p,
                                            _c_double_p, _c_int64_p, _vp]),
+    "pf_porod_fit": (ctypes.c_int, [ctypes.c_int, _c_double_p, _c_double_p, _c_int64_p,
+                                    ctypes.c_double, ctypes.c_double, _c_double_p, _c_double_p,
+                                    _c_int_p]),
     "pf_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _vp]),
     "pf_reduce_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_int64_p, ctypes.c_int64,
                                          _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -23,7 +23,8 @@ LIB = os.path.join(BUILD, "libpfgpu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE,
+              "-I", CSRC]
 
 
 def _nvcc() -> str:

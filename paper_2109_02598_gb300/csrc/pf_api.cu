@@ -60,6 +60,7 @@ int model_ncoeffs(int model) {
 double stencil_lmax(int dim, int stencil) {
   if (stencil == PF_ST_ISO) return 16.0 / 3.0;               // 9-point (pi,pi); 19-point (pi,pi,0)
   if (stencil == PF_ST_O4) return 32.0 / 3.0;                // fourth order, both axes at pi
+  if (stencil == PF_ST_ISO27) return 92.0 / 15.0;            // 27-point (pi,pi,pi): 184/30
   return 4.0 * dim;                                          // 5- / 7-point
 }
 
@@ -91,7 +92,10 @@ double stable_dt_limit(int model, int dim, double h, const double* c, int stenci
 ModelParams make_params(int model, const double* c, double dt, double h, int stencil) {
   ModelParams m{};
   m.dt = (float)dt;
-  const double denom = stencil == PF_ST_ISO ? 6.0 : (stencil == PF_ST_O4 ? 12.0 : 1.0);
+  const double denom = stencil == PF_ST_ISO     ? 6.0
+                       : stencil == PF_ST_O4    ? 12.0
+                       : stencil == PF_ST_ISO27 ? 30.0
+                                                : 1.0;
   m.lap_scale = (float)(1.0 / (denom * h * h));
   switch (model) {
     case PF_MODEL_AC:
@@ -500,8 +504,11 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out) {
 
 int pf_set_stencil(pf_grid_t g, int stencil) {
   if (int rc = check_grid(g)) return rc;
-  if (stencil != PF_STENCIL_STD && stencil != PF_STENCIL_ISO && stencil != PF_STENCIL_4TH)
+  if (stencil != PF_STENCIL_STD && stencil != PF_STENCIL_ISO && stencil != PF_STENCIL_4TH &&
+      stencil != PF_STENCIL_ISO27)
     return invalid("unknown stencil %d", stencil);
+  if (stencil == PF_STENCIL_ISO27 && g->dim != 3)
+    return invalid("the 27-point stencil is defined for 3D grids only");
   if (stencil == PF_STENCIL_4TH && g->dim != 2)
     return invalid("the fourth-order stencil is defined for 2D grids only");
   if (g->model_set && stencil != g->stencil) {

@@ -48,7 +48,8 @@ __device__ __forceinline__ void load_plane3d(const FieldPtrs& in, const Geom& g,
 }
 
 // 3D Laplacian at position p of a staged plane c (row width W) with the planes b below and
-// a above: 7-point (ST = PF_ST_STD) or isotropic 19-point (faces and edges, PF_ST_ISO).
+// a above: 7-point (ST = PF_ST_STD), isotropic 19-point (faces and edges, PF_ST_ISO) or
+// isotropic 27-point (faces, edges and corners, PF_ST_ISO27).
 template <int ST>
 __device__ __forceinline__ float lap3d_planes(const float* b, const float* c, const float* a,
                                               int p, int W, float scale) {
@@ -62,7 +63,16 @@ __device__ __forceinline__ float lap3d_planes(const float* b, const float* c, co
                                 __fadd_rn(c[p + W - 1], c[p + W + 1]));
     const float eb = __fadd_rn(__fadd_rn(b[p - 1], b[p + 1]), __fadd_rn(b[p - W], b[p + W]));
     const float ea = __fadd_rn(__fadd_rn(a[p - 1], a[p + 1]), __fadd_rn(a[p - W], a[p + W]));
-    return lap3d_iso(c[p], faces, __fadd_rn(exy, __fadd_rn(eb, ea)), scale);
+    const float edges = __fadd_rn(exy, __fadd_rn(eb, ea));
+    if constexpr (ST == PF_ST_ISO) {
+      return lap3d_iso(c[p], faces, edges, scale);
+    } else {
+      const float cb = __fadd_rn(__fadd_rn(b[p - W - 1], b[p - W + 1]),
+                                 __fadd_rn(b[p + W - 1], b[p + W + 1]));
+      const float ca = __fadd_rn(__fadd_rn(a[p - W - 1], a[p - W + 1]),
+                                 __fadd_rn(a[p + W - 1], a[p + W + 1]));
+      return lap3d_iso27(c[p], faces, edges, __fadd_rn(cb, ca), scale);
+    }
   }
 }
 
@@ -246,6 +256,10 @@ cudaError_t launch3_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
   if (stencil == PF_ST_ISO) {
     if (tile_id == 0) return launch3<MODEL, 32, 16, PF_ST_ISO>(g, in, out, m, s);
     return launch3<MODEL, 64, 8, PF_ST_ISO>(g, in, out, m, s);
+  }
+  if (stencil == PF_ST_ISO27) {
+    if (tile_id == 0) return launch3<MODEL, 32, 16, PF_ST_ISO27>(g, in, out, m, s);
+    return launch3<MODEL, 64, 8, PF_ST_ISO27>(g, in, out, m, s);
   }
   if (stencil != PF_ST_STD) return cudaErrorInvalidValue;
   if (tile_id == 0) return launch3<MODEL, 32, 16, PF_ST_STD>(g, in, out, m, s);

@@ -30,7 +30,8 @@ namespace pf {
 //   GS: a0 = Du, a1 = Dv, a2 = F, a3 = F + k
 //   C:  a0 = c1, a1 = c2, a2 = c3, a3 = c4, a4 = c5, a5 = 2 c5
 // lap_scale: the stencil's overall factor, 1/h^2 for the standard 5/7-point stencils,
-// 1/(6 h^2) for the isotropic 9/19-point ones, 1/(12 h^2) for the fourth-order 9-point one.
+// 1/(6 h^2) for the isotropic 9/19-point ones, 1/(12 h^2) for the fourth-order 9-point one,
+// 1/(30 h^2) for the isotropic 27-point one.
 struct ModelParams {
   float a0, a1, a2, a3, a4, a5;
   float dt;
@@ -41,9 +42,10 @@ struct ModelParams {
 #define PF_ST_STD 0  // 5-point (2D) / 7-point (3D), second order
 #define PF_ST_ISO 1  // isotropic 9-point (2D) / 19-point (3D), second order
 #define PF_ST_O4 2   // fourth-order 9-point (2D): +-1 and +-2 along each axis
+#define PF_ST_ISO27 3  // isotropic 27-point (3D), second order
 
 static_assert(PF_ST_STD == PF_STENCIL_STD && PF_ST_ISO == PF_STENCIL_ISO &&
-                  PF_ST_O4 == PF_STENCIL_4TH,
+                  PF_ST_O4 == PF_STENCIL_4TH && PF_ST_ISO27 == PF_STENCIL_ISO27,
               "internal stencil ids follow the public ones");
 
 template <int ST>
@@ -106,6 +108,13 @@ __device__ __forceinline__ float lap2d_o4(float c, float xm, float xp, float xm2
 // Isotropic 19-point: (2 (6 faces) + (12 edges) - 24 c) / (6 h^2); callers pass the sums.
 __device__ __forceinline__ float lap3d_iso(float c, float faces, float edges, float scale) {
   return __fmul_rn(__fmaf_rn(-24.0f, c, __fmaf_rn(2.0f, faces, edges)), scale);
+}
+
+// Isotropic 27-point: (14 (6 faces) + 3 (12 edges) + (8 corners) - 128 c) / (30 h^2).
+__device__ __forceinline__ float lap3d_iso27(float c, float faces, float edges, float corners,
+                                             float scale) {
+  const float s = __fmaf_rn(14.0f, faces, __fmaf_rn(3.0f, edges, corners));
+  return __fmul_rn(__fmaf_rn(-128.0f, c, s), scale);
 }
 
 // Model A: phi + dt (lap + c1 phi - c2 phi^3)

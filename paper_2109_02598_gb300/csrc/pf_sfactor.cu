@@ -251,3 +251,40 @@ extern "C" int pf_structure_factor(int dim, const int64_t* n, int64_t pitch, con
   for (int b = 0; b < n_bins; ++b) centres[b] = ((double)b + 0.5) * g.kmax / (double)n_bins;
   return PF_OK;
 }
+
+extern "C" int pf_porod_fit(int n_bins, const double* centres, const double* mean,
+                            const int64_t* counts, double k_lo, double k_hi, double* slope,
+                            double* intercept, int* n_used) {
+  if (centres == nullptr || mean == nullptr || counts == nullptr || slope == nullptr ||
+      intercept == nullptr || n_used == nullptr)
+    return invalid("pf_porod_fit: NULL argument");
+  if (n_bins < 1) return invalid("n_bins must be >= 1");
+  if (!(k_lo < k_hi)) return invalid("the window needs k_lo < k_hi");
+  // two passes over the usable bins in bin order: the means, then the centred sums
+  int n = 0;
+  double sx = 0.0, sy = 0.0;
+  auto usable = [&](int b) {
+    return centres[b] >= k_lo && centres[b] <= k_hi && counts[b] > 0 && mean[b] > 0.0;
+  };
+  for (int b = 0; b < n_bins; ++b) {
+    if (!usable(b)) continue;
+    sx += std::log(centres[b]);
+    sy += std::log(mean[b]);
+    ++n;
+  }
+  if (n < 2) return invalid("fewer than two usable bins in [%g, %g]", k_lo, k_hi);
+  const double xbar = sx / n, ybar = sy / n;
+  double sxy = 0.0, sxx = 0.0;
+  for (int b = 0; b < n_bins; ++b) {
+    if (!usable(b)) continue;
+    const double dx = std::log(centres[b]) - xbar;
+    const double dy = std::log(mean[b]) - ybar;
+    sxy += dx * dy;
+    sxx += dx * dx;
+  }
+  if (!(sxx > 0.0)) return invalid("the usable bins share one centre");
+  *slope = sxy / sxx;
+  *intercept = ybar - *slope * xbar;
+  *n_used = n;
+  return PF_OK;
+}

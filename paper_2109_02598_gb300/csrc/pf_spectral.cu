@@ -1,16 +1,25 @@
 // Semi-implicit Fourier spectral solver (Sec. 2.4.2) for Models A, B and C (Sec. 3).
 //
-// State: the half spectrum psi_hat of every field, float2 [nf][cs] on the device (nk modes
-// per field, cs = nk rounded up to 32 so that every field starts on 256 bytes; real-space
-// fields likewise sit rs = nsite rounded up to 64 floats apart). Padding is zero and stays
-// zero: the transforms neither read nor write it and the kernels map zero to zero. One step:
-//   1. inverse transform of work = psi_hat / N  -> real, the fields in real space;
-//   2. nonlinear terms f(psi) in place on real (one pass over every field at each site);
-//   3. forward transform real -> work = f_hat;
-//   4. psi_hat <- A psi_hat + (B N) f_hat, and work <- psi_hat / N for the next step.
-// Keeping psi_hat (not psi) as the state costs two transforms per field and step instead of
-// three; work is rewritten by step 4 because cuFFT's complex-to-real transform overwrites
-// its input.  A and B N are computed once, in float64, and stored as float2 per mode.
+// Buffers (nk modes and nsite sites per field; cs = nk rounded up to 32 and rs = nsite
+// rounded up to 64, so that every slice starts on 256 bytes):
+//   spec  float2 [2 nf][cs]: the state psi_hat (slices 0..nf-1) and f_hat (nf..2nf-1);
+//   work  float2 [nf][cs]:   psi_hat / N, the input of the next inverse transform;
+//   real  float  [nf][rs]:   the fields in real space, then their nonlinear terms.
+// One step:
+//   1. inverse transform work -> real (cuFFT's complex-to-real transform overwrites work);
+//   2. nonlinear terms f(psi) in place on real (all fields of a site at once);
+//   3. forward transform real -> spec[nf..2nf) = f_hat;
+//   4. psi_hat <- A psi_hat + (B N) f_hat and work <- psi_hat / N.
+// The state stays in Fourier space: two transforms per field and step, and no round-trip
+// rounding on it. The spectrum of a real field is Hermitian, psi_hat(-k) = conj psi_hat(k);
+// on the planes kx = 0 and kx = nx/2 (even nx) the half spectrum holds both k and -k, and
+// the forward transform meets this only to rounding. Step 4 therefore uses, on those
+// planes, the Hermitian part (f_hat(k) + conj f_hat(-k)) / 2. With A and B N even in k and
+// the products rounded symmetrically, the state then stays exactly Hermitian; the
+// rounding-level remainder would otherwise build up unseen (the inverse transform ignores
+// it) and grow wherever A > 1, e.g. |k|^2 < c1 in Model A. A and B N are computed once,
+// in float64, and stored as float2 per mode. Padding is zero and stays zero: the
+// transforms neither read nor write it and the kernels map zero to zero.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,12 +43,12 @@ struct pf_spectral_s {
   float cf[5];        // coefficients rounded to float32 once
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
-  float2* state = nullptr;
+  float2* spec = nullptr;
   float2* work = nullptr;
   float2* table = nullptr;
   float* real = nullptr;
   void* fft_work = nullptr;
-  cufftHandle r2c_all = -1, c2r_all = -1, r2c_one = -1, c2r_one = -1;
+  cufftHandle c2r_all = -1, r2c_all = -1, r2c_one = -1, c2r_one = -1;
   cudaGraphExec_t chunk = nullptr;
   bool graph_failed = false;
   const pf::CufftApi* api = nullptr;
@@ -133,7 +142,7 @@ struct NlCoeffs {
   float c[4];
 };
 
-// Over rs / 4 float4 groups of every field (padding included: zero in, zero out).
+// In place over rs / 4 float4 groups of every field (padding included: zero in, zero out).
 template <int MODEL>
 __global__ void spectral_nonlinear_kernel(float* __restrict__ real, int64_t rs, NlCoeffs k) {
   float4* p4 = reinterpret_cast<float4*>(real);
@@ -152,42 +161,69 @@ __global__ void spectral_nonlinear_kernel(float* __restrict__ real, int64_t rs, 
   }
 }
 
-__device__ __forceinline__ void update_mode(float2& s, float2& w, float A, float BN, float inv_n) {
-  s.x = __fmaf_rn(A, s.x, __fmul_rn(BN, w.x));
-  s.y = __fmaf_rn(A, s.y, __fmul_rn(BN, w.y));
-  w.x = __fmul_rn(s.x, inv_n);
-  w.y = __fmul_rn(s.y, inv_n);
+// Half-spectrum index of -k for mode i on a self-conjugate plane (same kx).
+__device__ __forceinline__ int64_t mirror_mode(const SpecGeom& g, int64_t i) {
+  const int64_t ix = i % g.nxh, rest = i / g.nxh;
+  const int64_t ny = g.d[g.rank - 2];
+  const int64_t iy = rest % ny, iz = rest / ny;
+  const int64_t nz = g.rank == 3 ? g.d[0] : 1;
+  const int64_t my = iy == 0 ? 0 : ny - iy, mz = iz == 0 ? 0 : nz - iz;
+  return (mz * ny + my) * g.nxh + ix;
 }
 
-// psi_hat <- A psi_hat + (B N) f_hat (f_hat arrives in work); work <- psi_hat / N.
-// Modes are taken two at a time (16-byte accesses); `total` (padding included) is even.
-__global__ void spectral_update_kernel(float2* __restrict__ state, float2* __restrict__ work,
-                                       const float2* __restrict__ table, int64_t total,
-                                       float inv_n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float4* s4 = reinterpret_cast<float4*>(state);
-  float4* w4 = reinterpret_cast<float4*>(work);
+__device__ __forceinline__ bool self_conjugate_plane(const SpecGeom& g, int64_t i) {
+  const int64_t ix = i % g.nxh;
+  return ix == 0 || 2 * ix == g.d[g.rank - 1];
+}
+
+// The Hermitian part of v on the self-conjugate planes: (v(k) + conj v(-k)) / 2, with the
+// sums taken in an order that gives exactly conjugate values at k and -k.
+__device__ __forceinline__ float2 hermitian_part(const SpecGeom& g, const float2* v, int64_t i,
+                                                 float2 vi) {
+  if (i >= g.nk || !self_conjugate_plane(g, i)) return vi;
+  const float2 vm = v[mirror_mode(g, i)];
+  return make_float2(__fmul_rn(0.5f, __fadd_rn(vi.x, vm.x)), __fmul_rn(0.5f, __fsub_rn(vi.y, vm.y)));
+}
+
+__device__ __forceinline__ float2 update_mode(float2 s, float2 f, float A, float BN) {
+  return make_float2(__fmaf_rn(A, s.x, __fmul_rn(BN, f.x)), __fmaf_rn(A, s.y, __fmul_rn(BN, f.y)));
+}
+
+// psi_hat <- A psi_hat + (B N) f_hat and work <- psi_hat / N, over modes t < total = nf cs
+// (field t / cs, mode t % cs); psi_hat at spec[t], f_hat at spec[total + t]. Modes are taken
+// two at a time (16-byte accesses); total and cs are even, so a pair never spans two fields.
+__global__ void spectral_update_kernel(float2* __restrict__ spec, float2* __restrict__ work,
+                                       const float2* __restrict__ table, SpecGeom g,
+                                       int64_t total, float inv_n) {
+  float4* s4 = reinterpret_cast<float4*>(spec);
+  const float4* f4 = reinterpret_cast<const float4*>(spec + total);
   const float4* t4 = reinterpret_cast<const float4*>(table);
-  for (int64_t j = t0; j < total / 2; j += stride) {
+  float4* w4 = reinterpret_cast<float4*>(work);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total / 2;
+       j += (int64_t)gridDim.x * blockDim.x) {
     const float4 tb = t4[j];
     const float4 sv = s4[j];
-    const float4 wv = w4[j];
-    float2 sa = make_float2(sv.x, sv.y), sb = make_float2(sv.z, sv.w);
-    float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
-    update_mode(sa, wa, tb.x, tb.y, inv_n);
-    update_mode(sb, wb, tb.z, tb.w, inv_n);
-    s4[j] = make_float4(sa.x, sa.y, sb.x, sb.y);
-    w4[j] = make_float4(wa.x, wa.y, wb.x, wb.y);
+    const float4 fv = f4[j];
+    const int64_t f = (2 * j) / g.cs, i = (2 * j) % g.cs;
+    const float2* fh = reinterpret_cast<const float2*>(f4) + f * g.cs;
+    const float2 fa = hermitian_part(g, fh, i, make_float2(fv.x, fv.y));
+    const float2 fb = hermitian_part(g, fh, i + 1, make_float2(fv.z, fv.w));
+    const float2 a = update_mode(make_float2(sv.x, sv.y), fa, tb.x, tb.y);
+    const float2 b = update_mode(make_float2(sv.z, sv.w), fb, tb.z, tb.w);
+    s4[j] = make_float4(a.x, a.y, b.x, b.y);
+    w4[j] = make_float4(__fmul_rn(a.x, inv_n), __fmul_rn(a.y, inv_n), __fmul_rn(b.x, inv_n),
+                        __fmul_rn(b.y, inv_n));
   }
 }
 
-__global__ void spectral_scale_kernel(const float2* __restrict__ src, float2* __restrict__ dst,
-                                      int64_t count, float inv_n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+// A freshly transformed field: state <- the Hermitian part of raw, work <- state / N.
+__global__ void spectral_load_kernel(const float2* __restrict__ raw, float2* __restrict__ state,
+                                     float2* __restrict__ work, SpecGeom g, float inv_n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.nk;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = src[i];
-    dst[i] = make_float2(__fmul_rn(v.x, inv_n), __fmul_rn(v.y, inv_n));
+    const float2 v = hermitian_part(g, raw, i, raw[i]);
+    state[i] = v;
+    work[i] = make_float2(__fmul_rn(v.x, inv_n), __fmul_rn(v.y, inv_n));
   }
 }
 
@@ -228,12 +264,6 @@ cudaError_t launch_nonlinear(const pf_spectral_s* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale(const float2* src, float2* dst, int64_t count, float inv_n,
-                         cudaStream_t st) {
-  spectral_scale_kernel<<<blocks_for(count), kThreads, 0, st>>>(src, dst, count, inv_n);
-  return cudaGetLastError();
-}
-
 // Enqueue one step on stream st.
 int enqueue_step(pf_spectral_s* s, cudaStream_t st) {
   const CufftApi* api = s->api;
@@ -242,13 +272,13 @@ int enqueue_step(pf_spectral_s* s, cudaStream_t st) {
     r = api->exec_c2r(s->c2r_all, reinterpret_cast<cufftComplex*>(s->work), s->real);
   if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_step inverse transform");
   PF_CUDA_TRY(launch_nonlinear(s, st));
+  const int64_t total = s->cs * s->nf;
   r = api->set_stream(s->r2c_all, st);
   if (r == CUFFT_SUCCESS)
-    r = api->exec_r2c(s->r2c_all, s->real, reinterpret_cast<cufftComplex*>(s->work));
+    r = api->exec_r2c(s->r2c_all, s->real, reinterpret_cast<cufftComplex*>(s->spec + total));
   if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_step forward transform");
-  const int64_t total = s->cs * s->nf;
   spectral_update_kernel<<<blocks_for(total / 2), kThreads, 0, st>>>(
-      s->state, s->work, s->table, total, inv_sites(s));
+      s->spec, s->work, s->table, spec_geom(s), total, inv_sites(s));
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
@@ -289,10 +319,10 @@ int check_spectral(pf_spectral_s* s) {
 void release(pf_spectral_s* s) {
   if (s->chunk) cudaGraphExecDestroy(s->chunk);
   if (s->api) {
-    for (cufftHandle p : {s->r2c_all, s->c2r_all, s->r2c_one, s->c2r_one})
+    for (cufftHandle p : {s->c2r_all, s->r2c_all, s->r2c_one, s->c2r_one})
       if (p != -1) s->api->destroy(p);
   }
-  cudaFree(s->state);
+  cudaFree(s->spec);
   cudaFree(s->work);
   cudaFree(s->table);
   cudaFree(s->real);
@@ -361,11 +391,12 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
   s->stream = (cudaStream_t)stream;
   s->api = api;
 
-  const size_t cbytes = sizeof(float2) * (size_t)(s->cs * nf);
+  const size_t tbytes = sizeof(float2) * (size_t)(s->cs * nf);
+  const size_t cbytes = 2 * tbytes;
   const size_t rbytes = sizeof(float) * (size_t)(s->rs * nf);
-  cudaError_t e = cudaMalloc(&s->state, cbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&s->work, cbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&s->table, cbytes);
+  cudaError_t e = cudaMalloc(&s->spec, cbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->work, tbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->table, tbytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->real, rbytes);
   if (e != cudaSuccess) {
     int rc = e == cudaErrorMemoryAllocation ? (set_error("pf_spectral_create: out of device memory"), PF_ERR_OOM)
@@ -377,9 +408,9 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
   // Plans: all fields at once for the steps, one field for reads and writes; one shared
   // work area (every transform runs on the solver's stream, one after another).
   size_t w[4] = {0, 0, 0, 0};
-  int rc = cufft_plan(api, &s->r2c_all, dim, s->d, CUFFT_R2C, nf, s->rs, s->cs, 0, &w[0]);
+  int rc = cufft_plan(api, &s->c2r_all, dim, s->d, CUFFT_C2R, nf, s->rs, s->cs, 0, &w[0]);
   if (rc == PF_OK)
-    rc = cufft_plan(api, &s->c2r_all, dim, s->d, CUFFT_C2R, nf, s->rs, s->cs, 0, &w[1]);
+    rc = cufft_plan(api, &s->r2c_all, dim, s->d, CUFFT_R2C, nf, s->rs, s->cs, 0, &w[1]);
   if (rc == PF_OK && nf > 1)
     rc = cufft_plan(api, &s->r2c_one, dim, s->d, CUFFT_R2C, 1, s->rs, s->cs, 0, &w[2]);
   if (rc == PF_OK && nf > 1)
@@ -399,7 +430,7 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
       return PF_ERR_OOM;
     }
   }
-  for (cufftHandle p : {s->r2c_all, s->c2r_all, s->r2c_one, s->c2r_one}) {
+  for (cufftHandle p : {s->c2r_all, s->r2c_all, s->r2c_one, s->c2r_one}) {
     if (p == -1) continue;
     cufftResult r = api->set_work_area(p, s->fft_work);
     if (r != CUFFT_SUCCESS) {
@@ -411,7 +442,7 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
   // Tables, zero state.
   const SpecGeom g = spec_geom(s);
   const double M = model == PF_MODEL_CH ? s->coeffs[2] : 1.0;
-  e = cudaMemsetAsync(s->table, 0, cbytes, s->stream);
+  e = cudaMemsetAsync(s->table, 0, tbytes, s->stream);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "pf_spectral_create tables");
     release(s);
@@ -420,8 +451,8 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
   spectral_table_kernel<<<blocks_for(s->nk * nf), kThreads, 0, s->stream>>>(
       model, g, h, dt, s->coeffs[0], model == PF_MODEL_C ? s->coeffs[2] : 0.0, M, nf, s->table);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->state, 0, cbytes, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->work, 0, cbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->spec, 0, cbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->work, 0, tbytes, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->real, 0, rbytes, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
@@ -444,15 +475,17 @@ int pf_spectral_write_field(pf_spectral_t s, int field, const float* src, int sr
   if (field < 0 || field >= s->nf) return invalid("field %d out of range [0, %d)", field, s->nf);
   if (src == nullptr) return invalid("src is NULL");
   float* real = s->real + field * s->rs;
-  float2* st = s->state + field * s->cs;
+  float2* raw = s->spec + (s->nf + field) * s->cs;  // the f_hat slice, free between steps
   PF_CUDA_TRY(cudaMemcpyAsync(real, src, sizeof(float) * (size_t)s->nsite,
                               src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               s->stream));
   const cufftHandle plan = s->nf > 1 ? s->r2c_one : s->r2c_all;
   cufftResult r = s->api->set_stream(plan, s->stream);
-  if (r == CUFFT_SUCCESS) r = s->api->exec_r2c(plan, real, reinterpret_cast<cufftComplex*>(st));
+  if (r == CUFFT_SUCCESS) r = s->api->exec_r2c(plan, real, reinterpret_cast<cufftComplex*>(raw));
   if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_write_field transform");
-  PF_CUDA_TRY(launch_scale(st, s->work + field * s->cs, s->nk, inv_sites(s), s->stream));
+  spectral_load_kernel<<<blocks_for(s->nk), kThreads, 0, s->stream>>>(
+      raw, s->spec + field * s->cs, s->work + field * s->cs, spec_geom(s), inv_sites(s));
+  PF_CUDA_TRY(cudaGetLastError());
   if (!src_on_device) PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return PF_OK;
 }
@@ -461,17 +494,19 @@ int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_de
   if (int rc = check_spectral(s)) return rc;
   if (field < 0 || field >= s->nf) return invalid("field %d out of range [0, %d)", field, s->nf);
   if (dst == nullptr) return invalid("dst is NULL");
+  // the inverse transform overwrites its input: transform a copy of psi_hat / N, made in
+  // the field's f_hat slice (free between steps)
+  float2* copy = s->spec + (s->nf + field) * s->cs;
   float* real = s->real + field * s->rs;
-  float2* wk = s->work + field * s->cs;
+  PF_CUDA_TRY(cudaMemcpyAsync(copy, s->work + field * s->cs, sizeof(float2) * (size_t)s->nk,
+                              cudaMemcpyDeviceToDevice, s->stream));
   const cufftHandle plan = s->nf > 1 ? s->c2r_one : s->c2r_all;
   cufftResult r = s->api->set_stream(plan, s->stream);
-  if (r == CUFFT_SUCCESS) r = s->api->exec_c2r(plan, reinterpret_cast<cufftComplex*>(wk), real);
+  if (r == CUFFT_SUCCESS) r = s->api->exec_c2r(plan, reinterpret_cast<cufftComplex*>(copy), real);
   if (r != CUFFT_SUCCESS) return cufft_fail(r, "pf_spectral_read_field transform");
   PF_CUDA_TRY(cudaMemcpyAsync(dst, real, sizeof(float) * (size_t)s->nsite,
                               dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               s->stream));
-  // the inverse transform consumed work: restore psi_hat / N
-  PF_CUDA_TRY(launch_scale(s->state + field * s->cs, wk, s->nk, inv_sites(s), s->stream));
   if (!dst_on_device) PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return PF_OK;
 }

@@ -93,8 +93,8 @@ class Grid:
         return self
 
     def set_stencil(self, stencil: str = "std"):
-        """Laplacian stencil: "std" (5/7-point), "iso" (isotropic 9/19-point) or "4th"
-        (fourth-order 9-point, 2D)."""
+        """Laplacian stencil: "std" (5/7-point), "iso" (isotropic 9/19-point), "4th"
+        (fourth-order 9-point, 2D) or "iso27" (isotropic 27-point, 3D)."""
         check(self._lib.pf_set_stencil(self._h, _lib.STENCIL_IDS[stencil]))
         self.stencil = stencil
         return self

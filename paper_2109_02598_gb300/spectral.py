@@ -1,5 +1,5 @@
-"""Semi-implicit Fourier spectral solver and structure factor (argument marshalling over
-include/pfgpu.h's pf_spectral_* and pf_structure_factor calls).
+"""Semi-implicit Fourier spectral solver, structure factor and Porod fit (argument marshalling
+over include/pfgpu.h's pf_spectral_*, pf_structure_factor and pf_porod_fit calls).
 
 ``Spectral`` is the paper's second solver (Sec. 2.4.2) for Models A, B and C (Sec. 3): each
 equation of motion split into a linear part, integrated exactly over a step in Fourier
@@ -144,3 +144,22 @@ def structure_factor(psi, h: float = 1.0, n_bins: int = 32, stream=None):
     if stream is None:
         stream = torch.cuda.current_stream()
     return structure_factor_view(t.data_ptr(), tuple(t.shape), t.shape[-1], h, n_bins, stream)
+
+
+def porod_fit(centres, mean, counts, k_lo: float, k_hi: float):
+    """Least-squares slope and intercept of log S against log k over the bins in
+    [k_lo, k_hi] (Porod's law, Sec. 3: slope -(d+1) in the scaling regime); returns
+    (slope, intercept, bins used)."""
+    lib = _lib.load()
+    c = np.ascontiguousarray(centres, dtype=np.float64)
+    m = np.ascontiguousarray(mean, dtype=np.float64)
+    n = np.ascontiguousarray(counts, dtype=np.int64)
+    if not (len(c) == len(m) == len(n)):
+        raise ValueError("centres, mean and counts must have the same length")
+    dp = ctypes.POINTER(ctypes.c_double)
+    slope, icpt, used = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    check(lib.pf_porod_fit(len(c), c.ctypes.data_as(dp), m.ctypes.data_as(dp),
+                           n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(k_lo),
+                           float(k_hi), ctypes.byref(slope), ctypes.byref(icpt),
+                           ctypes.byref(used)))
+    return slope.value, icpt.value, used.value

@@ -391,17 +391,18 @@ def test_2d_stencils_single_step_and_bitwise(pf, model, stencil, shape):
 
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("shape", [(9, 20, 70), (4, 4, 4), (6, 17, 33)])
-def test_3d_isotropic_stencil(pf, model, shape):
+@pytest.mark.parametrize("stencil,oname", [("iso", "19iso"), ("iso27", "27iso")])
+def test_3d_isotropic_stencil(pf, model, shape, stencil, oname):
     x0 = init_fields(model, shape, seed=22)
     dt, h = DT[model] * 0.5, 0.9
-    ref = oracle.euler_step(model, x0, COEFFS[model], dt, h, stencil="19iso")
-    got = gpu_run_st(pf, model, x0, 1, "iso", dt, h)
+    ref = oracle.euler_step(model, x0, COEFFS[model], dt, h, stencil=oname)
+    got = gpu_run_st(pf, model, x0, 1, stencil, dt, h)
     assert rel_linf(got, ref) <= 1e-6
-    a = gpu_run_st(pf, model, x0, 5, "iso", dt, h, tuning=(32, 16, 1))
-    b = gpu_run_st(pf, model, x0, 5, "iso", dt, h, tuning=(64, 8, 1))
+    a = gpu_run_st(pf, model, x0, 5, stencil, dt, h, tuning=(32, 16, 1))
+    b = gpu_run_st(pf, model, x0, 5, stencil, dt, h, tuning=(64, 8, 1))
     for p, q in zip(a, b):
         assert np.array_equal(p, q)
-    ref5 = oracle.run(model, x0, COEFFS[model], dt, 5, h, stencil="19iso")
+    ref5 = oracle.run(model, x0, COEFFS[model], dt, 5, h, stencil=oname)
     assert rel_linf(a, ref5) <= 1e-5
 
 
@@ -412,12 +413,16 @@ def test_stencil_rules(pf):
         g.set_stencil("4th")  # 2D only
     g.set_stencil("iso")
     assert g.tuning == (32, 16, 1)  # the general 3D kernel
+    g.set_stencil("iso27")
+    assert g.tuning == (32, 16, 1)
     with pytest.raises(PfError):
         g.set_tuning(64, 16, 1)  # no TMA kernel with this stencil
     g.close()
     h = pf.Grid((64, 64), 1).set_model("ch", (1.0, 1.0, 1.0), 0.03, force=True)
     with pytest.raises(PfError, match="stability"):
         h.set_stencil("4th")  # dt beyond the fourth-order bound
+    with pytest.raises(PfError, match="3D grids only"):
+        h.set_stencil("iso27")
     h.close()
 
 

@@ -96,6 +96,24 @@ def test_graph_replay_equals_direct_launches(pf, model):
         assert np.array_equal(u, v)
 
 
+@pytest.mark.parametrize("model,shape,dt,steps", [("ac", (128, 128), 0.2, 2000),
+                                                  ("c", (512, 512), 0.005, 10000),
+                                                  ("c", (64, 64, 64), 0.005, 10000)])
+def test_long_runs_stay_bounded(pf, model, shape, dt, steps):
+    # the paper's run length: the fields stay finite and within reach of the wells, and
+    # Model C's m keeps its mean (the k = 0 mode of a conserved field never changes).
+    # Wells with all coefficients 1: Model A psi = +-1; Model C m = 1.879 (largest root of
+    # m^3 - 3m - 1, from the equal chemical potentials) and psi^2 = 1 + 2m, |psi| = 2.175
+    bound = 1.01 if model == "ac" else 2.25
+    x0 = synthetic.paper_timing_init(model, shape)
+    out = gpu_spectral(pf, model, x0, steps, dt=dt)
+    for x in out:
+        assert np.isfinite(x).all()
+        assert np.abs(x).max() < bound
+    if model == "c":
+        assert abs(out[1].astype(np.float64).mean() - x0[1].astype(np.float64).mean()) < 1e-5
+
+
 @pytest.mark.parametrize("model,coeffs", [("ac", (0.7, 0.0)), ("ch", (0.9, 0.0, 1.3))])
 def test_linear_mode_evolves_by_exp_of_L_dt(pf, model, coeffs):
     shape, h, dt, n = (32, 48), 0.8, 0.4, 25
@@ -181,3 +199,28 @@ def test_paper_sizes_one_step_every_site(pf, model, shape):
     x0 = synthetic.paper_timing_init(model, shape)
     ref = oracle.spectral_run(model, x0, COEFFS[model], DT[model], 1)
     assert rel_linf(gpu_spectral(pf, model, x0, 1), ref) <= 2e-6
+
+
+@pytest.mark.parametrize("solver,dim,n,dt,steps,seeds", [
+    ("spectral", 2, 512, 0.2, 500, 4), ("spectral", 3, 96, 0.2, 300, 2),
+    ("euler", 2, 512, 0.05, 2000, 4)])
+def test_porod_law(pf, solver, dim, n, dt, steps, seeds):
+    # the paper's validation (Sec. 3): Model A quenched from U(-1, 1) to t = 100 (2D) or 60
+    # (3D); the radially averaged S(k), averaged over independent runs, falls off as
+    # k^-(d+1) between twice the peak wavenumber and k = 1.5
+    shape = (n,) * dim
+    Ss = []
+    for seed in range(seeds):
+        x0 = synthetic.paper_timing_init("ac", shape, seed=seed)
+        if solver == "spectral":
+            s = pf.Spectral(shape, "ac", COEFFS["ac"], dt).write_fields(x0).step(steps)
+            c, m, cnt = pf.structure_factor(s.read_field(0, device=True), 1.0, 64)
+        else:
+            s = pf.Grid(shape, 1).set_model("ac", COEFFS["ac"], dt).write_fields(x0)
+            s.step(steps)
+            c, m, cnt = s.structure_factor(0, n_bins=64)
+        s.close()
+        Ss.append(m)
+    slope, _, used = pf.porod_fit(c, np.mean(Ss, axis=0), cnt, 0.4, 1.5)
+    assert used >= 8
+    assert abs(slope + (dim + 1)) < 0.3, slope
