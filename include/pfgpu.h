@@ -286,10 +286,32 @@ int pf_spectral_write_field(pf_spectral_t s, int field, const float* src, int sr
  * float32 array; host destinations synchronize the stream. Errors as above. */
 int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_device);
 
-/* Advance n_steps >= 0 steps (asynchronous). Runs of 32 steps replay a recorded CUDA graph.
+/* Advance n_steps >= 0 steps (asynchronous). The cuFFT engine replays a recorded CUDA graph
+ * per 32 steps; the fused engine runs all n_steps in one cooperative launch.
  * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
 int pf_spectral_step(pf_spectral_t s, int64_t n_steps);
+
+/* Wait for the solver's stream. Errors: PF_ERR_CUDA; PF_ERR_TIMEOUT if a grid-barrier wait
+ * of the fused engine ran out (its kernel then stopped early and the state is invalid; the
+ * barrier is reset for the next launch). Host reads report the same. */
 int pf_spectral_synchronize(pf_spectral_t s);
+
+/* Engines of pf_spectral_step; both compute the same scheme (float32, to rounding):
+ *   PF_SPECTRAL_ENGINE_CUFFT  cuFFT transforms with this library's kernels between them;
+ *   PF_SPECTRAL_ENGINE_FUSED  2D grids with power-of-two sides in [4, 1024]: the whole run
+ *                             in one cooperative launch, two phases per step (rows: inverse
+ *                             x transform, nonlinear terms, forward x transform; columns:
+ *                             forward y transform, update, inverse y transform) with this
+ *                             library's shared-memory FFTs and a bounded grid barrier;
+ *   PF_SPECTRAL_ENGINE_AUTO   (default) fused where it was measured faster: sides up to 256,
+ *                             and one-field models up to 512; else cuFFT. */
+#define PF_SPECTRAL_ENGINE_AUTO 0
+#define PF_SPECTRAL_ENGINE_CUFFT 1
+#define PF_SPECTRAL_ENGINE_FUSED 2
+/* Errors: PF_ERR_INVALID_ARG (unknown engine; fused on a grid it does not take). */
+int pf_spectral_set_engine(pf_spectral_t s, int engine);
+/* The engine pf_spectral_step uses now (CUFFT or FUSED). */
+int pf_spectral_get_engine(pf_spectral_t s, int* engine);
 
 /* ----------------------------------------------------------------- structure factor */
 

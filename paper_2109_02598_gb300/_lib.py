@@ -86,6 +86,8 @@ SIGNATURES = {
     "pf_spectral_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "pf_spectral_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pf_spectral_synchronize": (ctypes.c_int, [_vp]),
+    "pf_spectral_set_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "pf_spectral_get_engine": (ctypes.c_int, [_vp, _c_int_p]),
     "pf_structure_factor": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int64, _vp,
                                            ctypes.c_double, ctypes.c_int, _c_double_p,
                                            _c_double_p, _c_int64_p, _vp]),

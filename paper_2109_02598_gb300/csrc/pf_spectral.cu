@@ -28,31 +28,11 @@
 
 #include "pf_cufft.h"
 #include "pf_internal.h"
+#include "pf_spectral.h"
 
 namespace pf {
 int invalid(const char* fmt, ...);
 }
-
-struct pf_spectral_s {
-  uint32_t magic;
-  int dim, model, nf;
-  int64_t d[3];       // C-order dims: (ny, nx) or (nz, ny, nx)
-  int64_t nsite, nk;  // real sites and half-spectrum modes per field
-  int64_t rs, cs;     // padded per-field strides of the real (floats) and complex arrays
-  double h, dt, coeffs[5];
-  float cf[5];        // coefficients rounded to float32 once
-  cudaStream_t stream = nullptr;
-  cudaStream_t capture = nullptr;
-  float2* spec = nullptr;
-  float2* work = nullptr;
-  float2* table = nullptr;
-  float* real = nullptr;
-  void* fft_work = nullptr;
-  cufftHandle c2r_all = -1, r2c_all = -1, r2c_one = -1, c2r_one = -1;
-  cudaGraphExec_t chunk = nullptr;
-  bool graph_failed = false;
-  const pf::CufftApi* api = nullptr;
-};
 
 namespace pf {
 namespace {
@@ -122,25 +102,6 @@ __global__ void spectral_table_kernel(int model, SpecGeom g, double h, double dt
   }
 }
 
-// Nonlinear terms in place (Sec. 3 equations, the part left after the linear split).
-template <int MODEL>
-__device__ __forceinline__ void nonlinear_site(float& p, float& m, const float* c) {
-  if (MODEL == PF_MODEL_AC) {  // -c2 psi^3
-    p = __fmul_rn(__fmul_rn(c[0], p), __fmul_rn(p, p));
-  } else if (MODEL == PF_MODEL_CH) {  // c2 psi^3
-    p = __fmul_rn(__fmul_rn(c[0], p), __fmul_rn(p, p));
-  } else {  // psi: psi (2 c5 m - c2 psi^2);  m: c4 m^3 - c5 psi^2
-    const float p2 = __fmul_rn(p, p);
-    const float fp = __fmul_rn(p, __fmaf_rn(c[1], m, __fmul_rn(c[0], p2)));
-    const float fm = __fmaf_rn(__fmul_rn(c[2], __fmul_rn(m, m)), m, __fmul_rn(c[3], p2));
-    p = fp;
-    m = fm;
-  }
-}
-
-struct NlCoeffs {
-  float c[4];
-};
 
 // In place over rs / 4 float4 groups of every field (padding included: zero in, zero out).
 template <int MODEL>
@@ -246,22 +207,30 @@ SpecGeom spec_geom(const pf_spectral_s* s) {
 }
 
 cudaError_t launch_nonlinear(const pf_spectral_s* s, cudaStream_t st) {
-  NlCoeffs k{};
+  const NlCoeffs k = nl_coeffs(s);
   const int blocks = blocks_for(s->rs / 4);
-  if (s->model == PF_MODEL_AC) {
-    k.c[0] = -s->cf[1];  // -c2
+  if (s->model == PF_MODEL_AC)
     spectral_nonlinear_kernel<PF_MODEL_AC><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
-  } else if (s->model == PF_MODEL_CH) {
-    k.c[0] = s->cf[1];  // c2
+  else if (s->model == PF_MODEL_CH)
     spectral_nonlinear_kernel<PF_MODEL_CH><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
-  } else {
-    k.c[0] = -s->cf[1];                    // -c2
-    k.c[1] = (float)(2.0 * s->coeffs[4]);  // 2 c5
-    k.c[2] = s->cf[3];                     // c4
-    k.c[3] = -s->cf[4];                    // -c5
+  else
     spectral_nonlinear_kernel<PF_MODEL_C><<<blocks, kThreads, 0, st>>>(s->real, s->rs, k);
-  }
   return cudaGetLastError();
+}
+
+// AUTO takes the fused engine where it was measured faster than cuFFT on GB300: sides up
+// to 256, and one-field models at 512 (per step, fused vs cuFFT: 64^2 9.7 vs 10.6 us, 128^2
+// 12.0 vs 13.8, 256^2 13.1 vs 13.7, Model A 512^2 15.9 vs 16.7; but Model C 512^2 23.0 vs
+// 18.9 and 1024^2 40.6 vs 32.9).
+bool auto_prefers_fused(const pf_spectral_s* s) {
+  if (!s->fused_ok) return false;
+  const int64_t nmax = s->d[0] > s->d[1] ? s->d[0] : s->d[1];
+  return nmax <= 256 || (nmax <= 512 && s->nf == 1);
+}
+
+bool use_fused(const pf_spectral_s* s) {
+  if (s->engine == PF_SPECTRAL_ENGINE_FUSED) return true;
+  return s->engine == PF_SPECTRAL_ENGINE_AUTO && auto_prefers_fused(s);
 }
 
 // Enqueue one step on stream st.
@@ -317,6 +286,7 @@ int check_spectral(pf_spectral_s* s) {
 }
 
 void release(pf_spectral_s* s) {
+  spectral_fused_release(s);
   if (s->chunk) cudaGraphExecDestroy(s->chunk);
   if (s->api) {
     for (cufftHandle p : {s->c2r_all, s->r2c_all, s->r2c_one, s->c2r_one})
@@ -460,6 +430,7 @@ int pf_spectral_create(int dim, const int64_t* n, double h, int model, const dou
     release(s);
     return rc;
   }
+  s->fused_ok = spectral_fused_supported(s);
   *out = s;
   return PF_OK;
 }
@@ -507,13 +478,17 @@ int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_de
   PF_CUDA_TRY(cudaMemcpyAsync(dst, real, sizeof(float) * (size_t)s->nsite,
                               dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               s->stream));
-  if (!dst_on_device) PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (!dst_on_device) {
+    PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (int rc = spectral_fused_check(s)) return rc;
+  }
   return PF_OK;
 }
 
 int pf_spectral_step(pf_spectral_t s, int64_t n_steps) {
   if (int rc = check_spectral(s)) return rc;
   if (n_steps < 0) return invalid("n_steps must be >= 0");
+  if (use_fused(s)) return spectral_fused_run(s, n_steps);
   int64_t left = n_steps;
   if (left >= kChunkSteps) ensure_chunk_graph(s);
   if (s->chunk != nullptr) {
@@ -528,6 +503,24 @@ int pf_spectral_step(pf_spectral_t s, int64_t n_steps) {
 int pf_spectral_synchronize(pf_spectral_t s) {
   if (int rc = check_spectral(s)) return rc;
   PF_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return spectral_fused_check(s);
+}
+
+int pf_spectral_set_engine(pf_spectral_t s, int engine) {
+  if (int rc = check_spectral(s)) return rc;
+  if (engine != PF_SPECTRAL_ENGINE_AUTO && engine != PF_SPECTRAL_ENGINE_CUFFT &&
+      engine != PF_SPECTRAL_ENGINE_FUSED)
+    return invalid("unknown spectral engine %d", engine);
+  if (engine == PF_SPECTRAL_ENGINE_FUSED && !s->fused_ok)
+    return invalid("the fused engine takes 2D grids with power-of-two sides in [4, 1024]");
+  s->engine = engine;
+  return PF_OK;
+}
+
+int pf_spectral_get_engine(pf_spectral_t s, int* engine) {
+  if (int rc = check_spectral(s)) return rc;
+  if (engine == nullptr) return invalid("engine is NULL");
+  *engine = use_fused(s) ? PF_SPECTRAL_ENGINE_FUSED : PF_SPECTRAL_ENGINE_CUFFT;
   return PF_OK;
 }
 

@@ -114,6 +114,19 @@ class Spectral:
         check(self._lib.pf_spectral_step(self._h, int(n_steps)))
         return self
 
+    ENGINES = {"auto": 0, "cufft": 1, "fused": 2}
+
+    def set_engine(self, engine: str = "auto"):
+        """"cufft", "fused" (2D, power-of-two sides in [4, 1024]) or "auto"."""
+        check(self._lib.pf_spectral_set_engine(self._h, self.ENGINES[engine]))
+        return self
+
+    @property
+    def engine(self) -> str:
+        e = ctypes.c_int()
+        check(self._lib.pf_spectral_get_engine(self._h, ctypes.byref(e)))
+        return {1: "cufft", 2: "fused"}[e.value]
+
     def synchronize(self):
         check(self._lib.pf_spectral_synchronize(self._h))
 

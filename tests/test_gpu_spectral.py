@@ -41,9 +41,10 @@ def init(model, shape, seed=0):
     return synthetic.paper_timing_init("ac" if model != "c" else "c", shape, seed=50 + seed)
 
 
-def gpu_spectral(pf, model, fields, n, coeffs=None, dt=None, h=1.0, chunks=None):
+def gpu_spectral(pf, model, fields, n, coeffs=None, dt=None, h=1.0, chunks=None, engine="auto"):
     s = pf.Spectral(fields[0].shape, model, COEFFS[model] if coeffs is None else coeffs,
                     DT[model] if dt is None else dt, h=h)
+    s.set_engine(engine)
     s.write_fields(fields)
     for k in (chunks or [n]):
         s.step(k)
@@ -67,7 +68,54 @@ def rel_l2(got, ref):
 def test_single_step(pf, model, shape):
     x0 = init(model, shape)
     ref = oracle.spectral_run(model, x0, COEFFS[model], DT[model], 1)
-    assert rel_linf(gpu_spectral(pf, model, x0, 1), ref) <= 2e-6
+    assert rel_linf(gpu_spectral(pf, model, x0, 1, engine="cufft"), ref) <= 2e-6
+
+
+# the fused engine: power-of-two sides, from the smallest it takes (4 x 2) to 1024
+FUSED_SHAPES = [(2, 4), (16, 16), (32, 64), (64, 8), (128, 128), (256, 1024)]
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+def test_fused_engine_single_and_twenty_steps(pf, model, shape):
+    x0 = init(model, shape, seed=9)
+    for n, bar in ((1, 2e-6), (20, 2e-5)):
+        ref = oracle.spectral_run(model, x0, COEFFS[model], DT[model], n)
+        assert rel_linf(gpu_spectral(pf, model, x0, n, engine="fused"), ref) <= bar, n
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_fused_and_cufft_engines_agree_and_interleave(pf, model):
+    x0 = init(model, (64, 128), seed=10)
+    a = gpu_spectral(pf, model, x0, 60, engine="fused")
+    b = gpu_spectral(pf, model, x0, 60, engine="cufft")
+    assert rel_linf(a, b) <= 2e-5
+    # engines can alternate on one solver: the state is shared
+    s = pf.Spectral((64, 128), model, COEFFS[model], DT[model]).write_fields(x0)
+    for i in range(6):
+        s.set_engine("fused" if i % 2 else "cufft").step(10)
+    c = s.read_fields()
+    s.close()
+    assert rel_linf(c, b) <= 2e-5
+
+
+def test_engine_selection(pf):
+    s = pf.Spectral((64, 32), "ac", COEFFS["ac"], 0.05)
+    assert s.engine == "fused"
+    assert s.set_engine("cufft").engine == "cufft"
+    s.close()
+    # auto: fused up to 256 per side, and up to 512 for one-field models
+    for shape, model, want in [((256, 256), "c", "fused"), ((512, 512), "ac", "fused"),
+                               ((512, 512), "c", "cufft"), ((1024, 1024), "ac", "cufft")]:
+        s = pf.Spectral(shape, model, COEFFS[model], DT[model])
+        assert s.engine == want, (shape, model)
+        s.close()
+    for shape in [(48, 40), (16, 12, 20), (2048, 8)]:
+        s = pf.Spectral(shape, "ac", COEFFS["ac"], 0.05)
+        assert s.engine == "cufft"
+        with pytest.raises(pf.PfError, match="power-of-two"):
+            s.set_engine("fused")
+        s.close()
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -75,23 +123,26 @@ def test_single_step(pf, model, shape):
 def test_twenty_steps(pf, model, shape):
     x0 = init(model, shape, seed=1)
     ref = oracle.spectral_run(model, x0, COEFFS[model], DT[model], 20)
-    assert rel_linf(gpu_spectral(pf, model, x0, 20), ref) <= 2e-5
+    assert rel_linf(gpu_spectral(pf, model, x0, 20, engine="cufft"), ref) <= 2e-5
 
 
 @pytest.mark.parametrize("model,shape,dt", [("ac", (128, 128), 0.05), ("ch", (64, 64), 0.05),
-                                            ("c", (32, 32, 32), 0.05)])
-def test_two_hundred_steps(pf, model, shape, dt):
+                                            ("c", (32, 32, 32), 0.05), ("c", (128, 64), 0.02)])
+@pytest.mark.parametrize("engine", ["cufft", "auto"])
+def test_two_hundred_steps(pf, model, shape, dt, engine):
     x0 = init(model, shape, seed=2)
     ref = oracle.spectral_run(model, x0, COEFFS[model], dt, 200)
-    assert rel_l2(gpu_spectral(pf, model, x0, 200, dt=dt), ref) <= 1e-3
+    assert rel_l2(gpu_spectral(pf, model, x0, 200, dt=dt, engine=engine), ref) <= 1e-3
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_graph_replay_equals_direct_launches(pf, model):
-    # 70 steps: two recorded 32-step graphs and 6 direct steps, against 70 single calls
-    x0 = init(model, (24, 40), seed=3)
-    a = gpu_spectral(pf, model, x0, 70)
-    b = gpu_spectral(pf, model, x0, 70, chunks=[1] * 70)
+@pytest.mark.parametrize("shape,engine", [((24, 40), "cufft"), ((32, 64), "fused")])
+def test_one_call_equals_single_steps(pf, model, shape, engine):
+    # cuFFT: two recorded 32-step graphs and 6 direct steps against 70 single calls; fused:
+    # one 70-step launch against 70 one-step launches
+    x0 = init(model, shape, seed=3)
+    a = gpu_spectral(pf, model, x0, 70, engine=engine)
+    b = gpu_spectral(pf, model, x0, 70, chunks=[1] * 70, engine=engine)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
 
