@@ -454,6 +454,32 @@ def paper_table_spectral(stream):
                     "table; its times are whole-program runs on 2016-2017 desktop CPUs"}
 
 
+def run_spectral_case(spec: str):
+    """One spectral case: paper initial conditions, Delta t of the paper-table runs, STEPS
+    steps timed with CUDA events after one untimed call of the same length."""
+    import torch
+    import paper_2109_02598_gb300 as pf
+    parts = spec.split(":")
+    model, shape, steps = parts[0], tuple(int(v) for v in parts[1].split("x")), int(parts[2])
+    engine = parts[3] if len(parts) > 3 else "auto"
+    shape = shape[::-1]  # given as NX x NY [x NZ]; arrays are (NZ,) NY, NX
+    coeffs = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "c": (1.0,) * 5}[model]
+    dt = {"ac": 0.05, "ch": 0.05, "c": 0.005}[model]
+    x0 = synthetic.paper_timing_init("ac" if model == "ch" else model, shape)[:1 if model != "c" else 2]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sp = pf.Spectral(shape, model, coeffs, dt, stream=stream).set_engine(engine)
+        sp.write_fields(x0)
+        sp.step(steps)
+        ms = _time(stream, lambda: sp.step(steps))
+        final = sp.read_fields()
+        used = sp.engine
+        sp.close()
+    print(json.dumps({"spectral": spec, "engine": used, "steps": steps,
+                      "us_per_step": ms * 1e3 / steps,
+                      "final_finite": bool(all(np.isfinite(x).all() for x in final))}))
+
+
 def _launch_schedule(n, k):
     left = n
     while left > 0:
@@ -475,7 +501,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-companions", action="store_true",
                     help="skip the batched / adjoint / CH / AC measurements")
+    ap.add_argument("--spectral", metavar="MODEL:NXxNY[xNZ]:STEPS[:ENGINE]",
+                    help="time one spectral-solver case alone (e.g. c:512x512:200:cufft) "
+                         "and print its JSON line instead of the bench line")
     args = ap.parse_args()
+    if args.spectral:
+        run_spectral_case(args.spectral)
+        return
     if args.impl == "reference":
         rank, world, _ = _dist_init(False)
         run_reference(args, rank, world)
