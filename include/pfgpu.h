@@ -153,15 +153,22 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * Unsupported combinations are rejected with PF_ERR_INVALID_ARG.
  * Supported: 2D tiles 64x16, 128x16, 32x32, 128x32; k in {1, 2, 4} (CH, C: {1, 2});
  * 3D tiles 32x16, 64x8 (general kernel, every model and size) and 64x16, 128x8, 128x16
- * (TMA-staged kernel: AC and GS with nx % tile_x == 0 and ny % tile_y == 0); k = 1. */
+ * (TMA-staged kernel: AC and GS with nx % tile_x == 0 and ny % tile_y == 0); k = 1;
+ * 3D k = 2 with tile nx x 8 (nx = 128 or 256; AC and GS).
+ * 2D tile nx x (ny / CS) selects the on-chip cluster kernel (standard stencil, nx % 4 == 0,
+ * ny % CS == 0, the grid in CS CTAs' shared memory; CS = 16 where the device allows clusters
+ * of 16, else 8): one thread-block cluster holds the whole grid, exchanges k-row halos
+ * between its CTAs through distributed shared memory, and runs all steps of a pf_step call
+ * in one launch. Results are bitwise identical to the tiled kernels. */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
 
 /* The tuning in effect (after defaults are resolved). */
 int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps);
 
-/* Time every supported (tile, k) for this grid and model on `probe_launches` launches
- * each (CUDA events), keep the fastest and report it. The state is not changed: probe
- * launches read the current buffer and write the spare one.
+/* Time every supported (tile, k) for this grid and model (CUDA events), keep the fastest
+ * and report it: tiled kernels as a replayed CUDA graph of max(probe_launches, 8) launches
+ * (as pf_step runs them), the cluster kernel as one launch of 16 k probe_launches steps.
+ * The state is not changed: probe launches read the current buffer and write the spare one.
  * Errors: PF_ERR_STATE (no model), PF_ERR_CUDA. */
 int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps);
 

@@ -146,7 +146,12 @@ int resolve_tuning(pf_grid_s* g) {
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
     g->k = g->req_k > 0 ? g->req_k : 1;
     if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
-    if (!fe2d_stencil_supported(g->stencil, g->tile, g->k)) {
+    if (g->tile == kTileCluster2D) {
+      if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
+        g->tile = def;
+        g->k = 1;
+      }
+    } else if (!fe2d_stencil_supported(g->stencil, g->tile, g->k)) {
       g->tile = def;
       g->k = 1;
     }
@@ -173,6 +178,8 @@ int resolve_tuning(pf_grid_s* g) {
 }
 
 bool tile_supported(pf_grid_s* g, int tile, int k) {
+  if (g->dim == 2 && tile == kTileCluster2D)
+    return g->stencil == PF_ST_STD && fe2d_cluster_supported(g->model, k, grid_geom(g));
   if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
   if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
   int tx, ty;
@@ -218,6 +225,8 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
     out.f[f] = g->buf[dst][f];
   }
   const Geom q = grid_geom(g);
+  if (g->dim == 2 && tile == kTileCluster2D)
+    return launch_fe2d_cluster(g->model, k, q, in, out, g->params, k, st);
   if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
   if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
   if (k == 2) {
@@ -432,6 +441,19 @@ int pf_step(pf_grid_t g, int64_t n_steps) {
   }
   if (n_steps < 0) return invalid("n_steps must be >= 0");
   if (n_steps == 0) return PF_OK;
+  if (g->dim == 2 && g->tile == kTileCluster2D) {
+    // the whole run in one launch of the on-chip cluster kernel
+    FieldPtrs in{};
+    FieldOut out{};
+    for (int f = 0; f < g->nf; ++f) {
+      in.f[f] = g->buf[g->cur][f];
+      out.f[f] = g->buf[1 - g->cur][f];
+    }
+    PF_CUDA_TRY(launch_fe2d_cluster(g->model, g->k, grid_geom(g), in, out, g->params, n_steps,
+                                    g->stream));
+    g->cur = 1 - g->cur;
+    return PF_OK;
+  }
   if (count_launches(n_steps, g->k) >= kGraphMinLaunches) {
     // replay a recorded graph of the whole launch sequence (one host call)
     pf_grid_s::StepGraph* hit = nullptr;
@@ -533,7 +555,18 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
   if (tile_x == 0 && tile_y == 0) {
     tile = -1;
   } else if (g->dim == 2) {
-    tile = tile2d_id(tile_x, tile_y);
+    const int cs = fe2d_cluster_size();
+    if (tile_x == g->nx && g->ny % cs == 0 && tile_y == g->ny / cs) {
+      tile = kTileCluster2D;  // the on-chip cluster kernel: full rows, ny / CS rows per CTA
+      const int kk = k_steps > 0 ? k_steps : 1;
+      if (g->stencil != PF_ST_STD ||
+          !(g->model_set && fe2d_cluster_supported(g->model, kk, grid_geom(g))))
+        return invalid("the on-chip cluster kernel (tile %dx%d) needs a model set, the standard "
+                       "stencil, nx %% 4 == 0 and the grid in %d CTAs' shared memory with "
+                       "k %d", tile_x, tile_y, cs, kk);
+    } else {
+      tile = tile2d_id(tile_x, tile_y);
+    }
     if (tile < 0) return invalid("unsupported 2D tile %dx%d", tile_x, tile_y);
   } else {
     tile = tile3d_id(tile_x, tile_y);
@@ -552,7 +585,7 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
   }
-  if (g->stencil != PF_ST_STD) {
+  if (g->stencil != PF_ST_STD && tile != kTileCluster2D) {
     const int t = tile >= 0 ? tile : 0;
     const int kk = k_steps > 0 ? k_steps : 1;
     const bool ok = g->dim == 2 ? fe2d_stencil_supported(g->stencil, t, kk)
@@ -574,10 +607,14 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
 int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps) {
   if (int rc = check_grid(g)) return rc;
   int tx, ty;
-  if (g->dim == 2)
+  if (g->dim == 2 && g->tile == kTileCluster2D) {
+    tx = g->nx;
+    ty = g->ny / fe2d_cluster_size();
+  } else if (g->dim == 2) {
     tile2d_shape(g->tile, &tx, &ty);
-  else
+  } else {
     tile3d_shape(g->tile, &tx, &ty);
+  }
   if (tile_x) *tile_x = tx;
   if (tile_y) *tile_y = ty;
   if (k_steps) *k_steps = g->k;
@@ -596,26 +633,59 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   PF_CUDA_TRY(cudaEventCreate(&e1));
   float best = INFINITY;
   int best_tile = g->tile, best_k = g->k;
-  const int ntiles = g->dim == 2 ? kNumTiles2D : kNumTiles3D;
+  const int ntiles = g->dim == 2 ? kNumTiles2D + 1 : kNumTiles3D;  // 2D: + the cluster kernel
   static const int ks[3] = {1, 2, 4};
   int rc = PF_OK;
   for (int t = 0; t < ntiles && rc == PF_OK; ++t) {
     for (int ki = 0; ki < 3 && rc == PF_OK; ++ki) {
       const int k = ks[ki];
       if (!tile_supported(g, t, k)) continue;
+      // the cluster kernel runs a whole pf_step in one launch: probe it that way
+      const bool cluster = g->dim == 2 && t == kTileCluster2D;
+      const int64_t probe_steps = cluster ? (int64_t)probe_launches * k * 16 : 0;
+      // Every probe reads buffer cur and writes 1 - cur, so the state is left as it was.
+      // Tiled candidates run as a replayed graph of n_l launches, as pf_step runs them.
+      const int n_l = probe_launches > 8 ? probe_launches : 8;
+      cudaGraphExec_t probe = nullptr;
       cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur, g->stream);  // warm-up
+      if (!cluster && e == cudaSuccess) {
+        if (g->capture == nullptr)
+          e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+          cudaError_t el = cudaSuccess;
+          for (int i = 0; i < n_l && el == cudaSuccess; ++i)
+            el = launch_step(g, t, k, g->cur, 1 - g->cur, g->capture);
+          cudaGraph_t graph = nullptr;
+          e = cudaStreamEndCapture(g->capture, &graph);
+          if (e == cudaSuccess) e = el;
+          if (e == cudaSuccess) e = cudaGraphInstantiate(&probe, graph, 0);
+          if (graph) cudaGraphDestroy(graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(probe, g->stream);  // warm-up replay
+      }
       if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
-      for (int i = 0; i < probe_launches && e == cudaSuccess; ++i)
-        e = launch_step(g, t, k, g->cur, 1 - g->cur, g->stream);
+      if (cluster && e == cudaSuccess) {
+        FieldPtrs in{};
+        FieldOut out{};
+        for (int f = 0; f < g->nf; ++f) {
+          in.f[f] = g->buf[g->cur][f];
+          out.f[f] = g->buf[1 - g->cur][f];
+        }
+        e = launch_fe2d_cluster(g->model, k, grid_geom(g), in, out, g->params, probe_steps,
+                                g->stream);
+      }
+      if (!cluster && e == cudaSuccess) e = cudaGraphLaunch(probe, g->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (probe) cudaGraphExecDestroy(probe);
       float ms = 0;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (e != cudaSuccess) {
         rc = cuda_fail(e, "pf_autotune probe");
         break;
       }
-      const float per_step = ms / (probe_launches * k);
+      const float per_step = cluster ? ms / probe_steps : ms / ((float)n_l * k);
       if (per_step < best) {
         best = per_step;
         best_tile = t;

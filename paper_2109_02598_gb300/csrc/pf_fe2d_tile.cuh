@@ -95,6 +95,63 @@ __device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float 
   return o;
 }
 
+// Chemical potential of four sites at p of a staged region (Model B: of field 0; Model C:
+// of m, field 1, coupled to psi, field 0), into mu at p. Rows are ws floats apart and
+// fields pl floats apart. Shared by every 2D kernel, so all compute identical arithmetic.
+template <int MODEL, int ST>
+__device__ __forceinline__ void site4_mu(const float* src, int p, int ws, int pl,
+                                         const ModelParams& m, float* mu) {
+  if constexpr (MODEL == PF_MODEL_CH) {
+    const float4 c = *reinterpret_cast<const float4*>(src + p);
+    const float4 l = lap2d_x4<ST>(src, p, ws, m.lap_scale);
+    *reinterpret_cast<float4*>(mu + p) =
+        make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
+                    ch_mu(c.w, l.w, m));
+  } else {  // Model C: chemical potential of m (field 1), coupled to psi (field 0)
+    const float4 ps = *reinterpret_cast<const float4*>(src + p);
+    const float4 c = *reinterpret_cast<const float4*>(src + pl + p);
+    const float4 l = lap2d_x4<ST>(src + pl, p, ws, m.lap_scale);
+    *reinterpret_cast<float4*>(mu + p) =
+        make_float4(mc_mu(ps.x, c.x, l.x, m), mc_mu(ps.y, c.y, l.y, m),
+                    mc_mu(ps.z, c.z, l.z, m), mc_mu(ps.w, c.w, l.w, m));
+  }
+}
+
+// One forward-Euler update of four sites at p for every field: val[f] receives field f.
+template <int MODEL, int ST>
+__device__ __forceinline__ void site4_update(const float* src, const float* mu, int p, int ws,
+                                             int pl, const ModelParams& m, float4* val) {
+  if constexpr (MODEL == PF_MODEL_AC) {
+    const float4 c = *reinterpret_cast<const float4*>(src + p);
+    const float4 l = lap2d_x4<ST>(src, p, ws, m.lap_scale);
+    val[0] = make_float4(ac_update(c.x, l.x, m), ac_update(c.y, l.y, m),
+                         ac_update(c.z, l.z, m), ac_update(c.w, l.w, m));
+  } else if constexpr (MODEL == PF_MODEL_CH) {
+    const float4 c = *reinterpret_cast<const float4*>(src + p);
+    const float4 l = lap2d_x4<ST>(mu, p, ws, m.lap_scale);
+    val[0] = make_float4(ch_update(c.x, l.x, m), ch_update(c.y, l.y, m),
+                         ch_update(c.z, l.z, m), ch_update(c.w, l.w, m));
+  } else if constexpr (MODEL == PF_MODEL_C) {
+    const float4 ps = *reinterpret_cast<const float4*>(src + p);
+    const float4 c = *reinterpret_cast<const float4*>(src + pl + p);
+    const float4 lp = lap2d_x4<ST>(src, p, ws, m.lap_scale);
+    const float4 lm = lap2d_x4<ST>(mu, p, ws, m.lap_scale);
+    mc_update(ps.x, c.x, lp.x, lm.x, m, val[0].x, val[1].x);
+    mc_update(ps.y, c.y, lp.y, lm.y, m, val[0].y, val[1].y);
+    mc_update(ps.z, c.z, lp.z, lm.z, m, val[0].z, val[1].z);
+    mc_update(ps.w, c.w, lp.w, lm.w, m, val[0].w, val[1].w);
+  } else {
+    const float4 u = *reinterpret_cast<const float4*>(src + p);
+    const float4 v = *reinterpret_cast<const float4*>(src + pl + p);
+    const float4 lu = lap2d_x4<ST>(src, p, ws, m.lap_scale);
+    const float4 lv = lap2d_x4<ST>(src + pl, p, ws, m.lap_scale);
+    gs_update(u.x, v.x, lu.x, lv.x, m, val[0].x, val[1].x);
+    gs_update(u.y, v.y, lu.y, lv.y, m, val[0].y, val[1].y);
+    gs_update(u.z, v.z, lu.z, lv.z, m, val[0].z, val[1].z);
+    gs_update(u.w, v.w, lu.w, lv.w, m, val[0].w, val[1].w);
+  }
+}
+
 // k forward-Euler sub-steps of one tile; the last one is written to `out` (sites beyond
 // nx, ny are computed on periodic images and not stored).
 template <int MODEL, int K, int TX, int TY, int ST = PF_ST_STD>
@@ -121,20 +178,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
         const int rr = i / nch;
         const int r = rlo + rr;
         const int p = r * WS + 4 * (clo + i - rr * nch);
-        if constexpr (MODEL == PF_MODEL_CH) {
-          const float4 c = *reinterpret_cast<const float4*>(src + p);
-          const float4 l = lap2d_x4<ST>(src, p, WS, m.lap_scale);
-          *reinterpret_cast<float4*>(mu + p) =
-              make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m), ch_mu(c.z, l.z, m),
-                          ch_mu(c.w, l.w, m));
-        } else {  // Model C: chemical potential of m (field 1), coupled to psi (field 0)
-          const float4 ps = *reinterpret_cast<const float4*>(src + p);
-          const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
-          const float4 l = lap2d_x4<ST>(src + PL, p, WS, m.lap_scale);
-          *reinterpret_cast<float4*>(mu + p) =
-              make_float4(mc_mu(ps.x, c.x, l.x, m), mc_mu(ps.y, c.y, l.y, m),
-                          mc_mu(ps.z, c.z, l.z, m), mc_mu(ps.w, c.w, l.w, m));
-        }
+        site4_mu<MODEL, ST>(src, p, WS, PL, m, mu);
       }
       __syncthreads();
     }
@@ -149,35 +193,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
       const int j = clo + i - rr * nch;
       const int p = r * WS + 4 * j;
       float4 val[C::NF];
-      if constexpr (MODEL == PF_MODEL_AC) {
-        const float4 c = *reinterpret_cast<const float4*>(src + p);
-        const float4 l = lap2d_x4<ST>(src, p, WS, m.lap_scale);
-        val[0] = make_float4(ac_update(c.x, l.x, m), ac_update(c.y, l.y, m),
-                             ac_update(c.z, l.z, m), ac_update(c.w, l.w, m));
-      } else if constexpr (MODEL == PF_MODEL_CH) {
-        const float4 c = *reinterpret_cast<const float4*>(src + p);
-        const float4 l = lap2d_x4<ST>(mu, p, WS, m.lap_scale);
-        val[0] = make_float4(ch_update(c.x, l.x, m), ch_update(c.y, l.y, m),
-                             ch_update(c.z, l.z, m), ch_update(c.w, l.w, m));
-      } else if constexpr (MODEL == PF_MODEL_C) {
-        const float4 ps = *reinterpret_cast<const float4*>(src + p);
-        const float4 c = *reinterpret_cast<const float4*>(src + PL + p);
-        const float4 lp = lap2d_x4<ST>(src, p, WS, m.lap_scale);
-        const float4 lm = lap2d_x4<ST>(mu, p, WS, m.lap_scale);
-        mc_update(ps.x, c.x, lp.x, lm.x, m, val[0].x, val[1].x);
-        mc_update(ps.y, c.y, lp.y, lm.y, m, val[0].y, val[1].y);
-        mc_update(ps.z, c.z, lp.z, lm.z, m, val[0].z, val[1].z);
-        mc_update(ps.w, c.w, lp.w, lm.w, m, val[0].w, val[1].w);
-      } else {
-        const float4 u = *reinterpret_cast<const float4*>(src + p);
-        const float4 v = *reinterpret_cast<const float4*>(src + PL + p);
-        const float4 lu = lap2d_x4<ST>(src, p, WS, m.lap_scale);
-        const float4 lv = lap2d_x4<ST>(src + PL, p, WS, m.lap_scale);
-        gs_update(u.x, v.x, lu.x, lv.x, m, val[0].x, val[1].x);
-        gs_update(u.y, v.y, lu.y, lv.y, m, val[0].y, val[1].y);
-        gs_update(u.z, v.z, lu.z, lv.z, m, val[0].z, val[1].z);
-        gs_update(u.w, v.w, lu.w, lv.w, m, val[0].w, val[1].w);
-      }
+      site4_update<MODEL, ST>(src, mu, p, WS, PL, m, val);
       if (last) {
         const int gx = x0 + 4 * j - C::HP;
         const int gy = y0 + r - C::H;

@@ -69,6 +69,15 @@ cudaError_t launch_fe2d_stencil(int stencil, int model, int tile_id, int k, cons
                                 FieldPtrs in, FieldOut out, const ModelParams& m,
                                 cudaStream_t s);
 
+// ---- 2D grids held on chip by one thread-block cluster (pf_fe2d_cluster.cu) --------
+// Tile id kTileCluster2D: each CTA of a cluster of fe2d_cluster_size() CTAs keeps a band of
+// full rows in shared memory; one launch runs all n_steps (k steps per halo exchange).
+constexpr int kTileCluster2D = kNumTiles2D;
+int fe2d_cluster_size();
+bool fe2d_cluster_supported(int model, int k, const Geom& q);
+cudaError_t launch_fe2d_cluster(int model, int k, const Geom& q, FieldPtrs in, FieldOut out,
+                                const ModelParams& m, int64_t n_steps, cudaStream_t st);
+
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
 //           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);

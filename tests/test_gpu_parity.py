@@ -439,3 +439,58 @@ def test_bounded_wait_times_out_and_reports(pf):
     x0 = init_fields("gs", (6, 16, 64), seed=30)
     ref = oracle.euler_step("gs", x0, COEFFS["gs"], DT["gs"])
     assert rel_linf(gpu_run(pf, "gs", x0, 1), ref) <= 1e-6
+
+
+def set_cluster_tuning(g, k):
+    """Select the on-chip cluster kernel (tile = full rows x ny / CS); CS is 16 or 8."""
+    from paper_2109_02598_gb300 import PfError
+    ny, nx = g.shape
+    for cs in (16, 8):
+        if ny % cs:
+            continue
+        try:
+            g.set_tuning(nx, ny // cs, k)
+            return cs
+        except PfError:
+            continue
+    raise AssertionError("no cluster tuning accepted")
+
+
+@pytest.mark.parametrize("model,k", [("ac", 1), ("ac", 2), ("ac", 4), ("gs", 1), ("gs", 4),
+                                     ("ch", 1), ("ch", 2), ("c", 1), ("c", 2)])
+@pytest.mark.parametrize("shape", [(128, 128), (64, 96)])
+def test_cluster_kernel_bitwise_and_oracle(pf, model, k, shape):
+    # 37 steps: super-steps of k and a shorter last one; same bits as the tiled kernel
+    x0 = init_fields(model, shape, seed=40)
+    n = 37
+    g = pf.Grid(shape, n_fields=len(x0)).set_model(model, COEFFS[model], DT[model], force=True)
+    set_cluster_tuning(g, k)
+    assert g.tuning[0] == shape[1]
+    g.write_fields(x0)
+    g.step(n)
+    a = g.read_fields()
+    g.close()
+    b = gpu_run(pf, model, x0, n, tuning=(64, 16, 1))
+    for p, q in zip(a, b):
+        assert np.array_equal(p, q)
+    ref = oracle.run(model, x0, COEFFS[model], DT[model], n)
+    assert rel_linf(a, ref) <= 1e-5
+
+
+def test_cluster_kernel_rules_and_autotune(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((128, 128), 1).set_model("ac", COEFFS["ac"], DT["ac"])
+    g.write_fields(init_fields("ac", (128, 128), seed=41))
+    t = g.autotune(3)  # the cluster kernel is a candidate
+    g.step(10)
+    g.close()
+    h = pf.Grid((128, 128), 1).set_model("ac", COEFFS["ac"], DT["ac"]).set_stencil("iso")
+    with pytest.raises(PfError, match="cluster"):
+        set_cluster_tuning_strict(h)
+    h.close()
+    assert len(t) == 3
+
+
+def set_cluster_tuning_strict(g):
+    ny, nx = g.shape
+    g.set_tuning(nx, ny // 16, 1)
