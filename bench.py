@@ -343,7 +343,7 @@ def companions(stream, hbm):
         g = pf.Grid((4096, 4096), 2, stream=stream).set_model("gs", (0.2, 0.1, 0.04, 0.06), 0.5)
         g.write_fields((u, v))
         t2 = g.autotune(3)
-        g.step(20)
+        g.step(200)  # records the graph of this run length
         ms = _time(stream, lambda: g.step(200))
         pglups = 4096 * 4096 * 200 / (ms * 1e-3) / 1e9
         out["plain_gs2d_4096"] = {"glups": pglups, "tuning": list(t2)}
@@ -354,7 +354,7 @@ def companions(stream, hbm):
         u0, v0 = synthetic.workload_init("gs2d_adjoint_512")
         g = pf.Grid((512, 512), 2, stream=stream).set_model("gs", w["coeffs"], w["dt"])
         g.write_fields((u0, v0))
-        g.step(10)
+        g.step(2000)  # records the graph of this run length
         plain = _time(stream, lambda: g.step(2000))
         g.write_fields((u0, v0))
         fwd = _time(stream, lambda: pf.adjoint_forward(g, 2000))
@@ -374,7 +374,7 @@ def companions(stream, hbm):
             g = pf.Grid(w["shape"], 1, stream=stream).set_model(w["model"], w["coeffs"], w["dt"])
             g.write_fields(x0)
             t = g.autotune(5)
-            g.step(steps // 10)
+            g.step(steps)  # records the graph of this run length
             ms = _time(stream, lambda: g.step(steps))
             sites = int(np.prod(w["shape"]))
             out[name] = {"steps": steps, "glups": sites * steps / (ms * 1e-3) / 1e9,
@@ -480,6 +480,38 @@ def run_spectral_case(spec: str):
                       "final_finite": bool(all(np.isfinite(x).all() for x in final))}))
 
 
+def run_euler_case(spec: str):
+    """One forward-Euler case: the paper's U(-1, 1) initial fields (Gray-Scott: seeded
+    squares), the coefficients and Delta t of the parity tests, STEPS steps timed with CUDA
+    events after one untimed call of the same length."""
+    import torch
+    import paper_2109_02598_gb300 as pf
+    parts = spec.split(":")
+    model, shape, steps = parts[0], tuple(int(v) for v in parts[1].split("x"))[::-1], int(parts[2])
+    coeffs = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06),
+              "c": (1.0,) * 5}[model]
+    dt = {"ac": 0.05, "ch": 0.01, "gs": 0.5, "c": 0.005}[model]
+    if model == "gs":
+        x0 = synthetic.gray_scott_init(shape, seed=3, n_seeds=8, side=8)
+    else:
+        x0 = tuple(0.5 * x for x in synthetic.paper_timing_init("c" if model == "c" else "ac", shape))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = pf.Grid(shape, len(x0), stream=stream).set_model(model, coeffs, dt).write_fields(x0)
+        if len(parts) >= 6:
+            g.set_tuning(int(parts[3]), int(parts[4]), int(parts[5]))
+        else:
+            g.autotune(3)
+        g.step(steps)
+        ms = _time(stream, lambda: g.step(steps))
+        tuning = g.tuning
+        g.close()
+    sites = int(np.prod(shape))
+    print(json.dumps({"euler": spec, "tuning": list(tuning), "steps": steps,
+                      "us_per_step": ms * 1e3 / steps,
+                      "glups": sites * steps / (ms * 1e-3) / 1e9}))
+
+
 def _launch_schedule(n, k):
     left = n
     while left > 0:
@@ -504,9 +536,15 @@ def main():
     ap.add_argument("--spectral", metavar="MODEL:NXxNY[xNZ]:STEPS[:ENGINE]",
                     help="time one spectral-solver case alone (e.g. c:512x512:200:cufft) "
                          "and print its JSON line instead of the bench line")
+    ap.add_argument("--euler", metavar="MODEL:NXxNY[xNZ]:STEPS[:TX:TY:K]",
+                    help="time one forward-Euler case alone (autotuned unless a tuning is "
+                         "given; e.g. ac:128x128:1000) and print its JSON line")
     args = ap.parse_args()
     if args.spectral:
         run_spectral_case(args.spectral)
+        return
+    if args.euler:
+        run_euler_case(args.euler)
         return
     if args.impl == "reference":
         rank, world, _ = _dist_init(False)

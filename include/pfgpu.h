@@ -157,9 +157,10 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * 3D k = 2 with tile nx x 8 (nx = 128 or 256; AC and GS).
  * 2D tile nx x (ny / CS) selects the on-chip cluster kernel (standard stencil, nx % 4 == 0,
  * ny % CS == 0, the grid in CS CTAs' shared memory; CS = 16 where the device allows clusters
- * of 16, else 8): one thread-block cluster holds the whole grid, exchanges k-row halos
- * between its CTAs through distributed shared memory, and runs all steps of a pf_step call
- * in one launch. Results are bitwise identical to the tiled kernels. */
+ * of 16, else 8; k in {1, 2, 4, 8} for AC and GS, {1, 2} for CH and C, with k R <= ny / CS):
+ * one thread-block cluster holds the whole grid, exchanges k-row halos between its CTAs
+ * through distributed shared memory, and runs all steps of a pf_step call in one launch.
+ * Results are bitwise identical to the tiled kernels. */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
 
 /* The tuning in effect (after defaults are resolved). */

@@ -145,7 +145,7 @@ int resolve_tuning(pf_grid_s* g) {
     const int def = g->stencil == PF_ST_STD ? 1 : 0;  // 128 x 16; other stencils 64 x 16
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
     g->k = g->req_k > 0 ? g->req_k : 1;
-    if (g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
+    if (g->tile != kTileCluster2D && g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
     if (g->tile == kTileCluster2D) {
       if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
         g->tile = def;
@@ -580,7 +580,7 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (!(g->model_set && fe3d_tb2_supported(g->model, tx, ty, grid_geom(g))))
       return invalid("3D k = 2 needs an AC/GS model, tile nx x 8 with nx = 128 or 256, ny %% 8 == 0");
   }
-  if (k_steps > 0 && g->dim == 2) {
+  if (k_steps > 0 && g->dim == 2 && tile != kTileCluster2D) {
     const int model = g->model_set ? g->model : PF_MODEL_AC;
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
@@ -634,10 +634,10 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   float best = INFINITY;
   int best_tile = g->tile, best_k = g->k;
   const int ntiles = g->dim == 2 ? kNumTiles2D + 1 : kNumTiles3D;  // 2D: + the cluster kernel
-  static const int ks[3] = {1, 2, 4};
+  static const int ks[4] = {1, 2, 4, 8};  // 8: the cluster kernel only
   int rc = PF_OK;
   for (int t = 0; t < ntiles && rc == PF_OK; ++t) {
-    for (int ki = 0; ki < 3 && rc == PF_OK; ++ki) {
+    for (int ki = 0; ki < 4 && rc == PF_OK; ++ki) {
       const int k = ks[ki];
       if (!tile_supported(g, t, k)) continue;
       // the cluster kernel runs a whole pf_step in one launch: probe it that way

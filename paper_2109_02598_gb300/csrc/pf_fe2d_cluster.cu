@@ -5,20 +5,22 @@
 // kept in the tile layout of the 2D tile body with full rows: WS = nx + 2 HP floats per row
 // (HP halo columns per side, which hold periodic copies of the row's other end) and
 // HT = B + 2H rows (H = K R halo rows per side). A super-step advances K steps:
-//   1. the halo rows come from the neighbouring bands through distributed shared memory:
-//      each CTA reads the H edge rows its neighbours exported at the end of the previous
-//      super-step (the first super-step stages everything from global memory instead);
-//   2. the halo columns of every row are refreshed from the row's other end;
-//   3. K sub-steps on shrinking regions, exactly as the tiled kernels do them (the same
+//   1. the halo rows are copied from this CTA's receive buffer, into which the neighbouring
+//      bands stored their H edge rows at the end of the previous super-step (the first
+//      super-step stages everything from global memory instead);
+//   2. K sub-steps on shrinking regions, exactly as the tiled kernels do them (the same
 //      per-site functions, so every path gives the same bits);
-//   4. the band's top and bottom H rows are exported to a parity-indexed buffer, and the
-//      cluster synchronises (barrier.cluster: all CTAs of a cluster are co-scheduled and run
-//      the same number of super-steps, so it always completes).
-// Exports are double-buffered by parity, so one cluster barrier per super-step suffices: a
-// neighbour reads parity p during super-step s while this CTA writes parity 1 - p.
-// After the last super-step each CTA writes its band to global memory, and the cluster
-// synchronises once more, so that no CTA exits while a neighbour may still be reading its
-// exports.
+//   3. the band's top H rows are stored into the receive buffer of the band above, its
+//      bottom H rows into that of the band below (remote stores to distributed shared
+//      memory), and the cluster synchronises (barrier.cluster with release / acquire: all
+//      CTAs of a cluster are co-scheduled and run the same number of super-steps, so it
+//      always completes, and the stores are visible after it).
+// Receive buffers are double-buffered by parity, so one cluster barrier per super-step
+// suffices: a CTA reads parity p during super-step s while its neighbours store parity
+// 1 - p. The halo columns are never refreshed in a pass of their own: every write of a value
+// whose column lies within HP of a row end (staging, halo rows, the last sub-step) also
+// writes its periodic copy. After the last super-step each CTA writes its band to global
+// memory; no distributed shared memory access follows the last barrier.
 #include <cooperative_groups.h>
 
 #include "pf_fe2d_tile.cuh"
@@ -47,16 +49,28 @@ struct CfgCl {
   static constexpr bool MU = MODEL == PF_MODEL_CH || MODEL == PF_MODEL_C;
 };
 
+constexpr int kNTC = 512;  // threads per CTA
+
 // Floats of shared memory: two work buffers of NF fields, the chemical potential, and the
-// exports [2 parities][2 sides][NF][H rows][nx].
+// receive buffers [2 parities][2 sides][NF][H rows][nx] (side 0: the rows above the band).
 template <int MODEL, int K>
 size_t cluster_smem_floats(const ClGeom& g) {
   using C = CfgCl<MODEL, K>;
   return (size_t)2 * C::NF * g.pl + (C::MU ? g.pl : 0) + (size_t)4 * C::NF * C::H * g.nx;
 }
 
+// Store the float4 at staged column 4j + HP of a row, and its periodic copy when the column
+// lies within HP of either row end.
+template <int HP>
+__device__ __forceinline__ void put_row4(float* row, int j, int nx, float4 v) {
+  const int c = 4 * j;
+  *reinterpret_cast<float4*>(row + HP + c) = v;
+  if (c < HP) *reinterpret_cast<float4*>(row + HP + nx + c) = v;
+  if (c >= nx - HP) *reinterpret_cast<float4*>(row + c - (nx - HP)) = v;
+}
+
 template <int MODEL, int K>
-__global__ void __launch_bounds__(kNT2, 1)
+__global__ void __launch_bounds__(kNTC, 1)
     fe2d_cluster_kernel(FieldPtrs in, FieldOut out, ClGeom g, ModelParams m, int64_t n_steps) {
   using C = CfgCl<MODEL, K>;
   constexpr int NF = C::NF, R = C::R, RS = C::RS, H = C::H, HP = C::HP;
@@ -69,19 +83,19 @@ __global__ void __launch_bounds__(kNT2, 1)
   float* cur = sm;
   float* alt = sm + NF * PL;
   float* mu = sm + 2 * NF * PL;
-  float* exports = mu + (C::MU ? PL : 0);  // [parity][side][f][r][x], side 0 = top rows
-  const int EXF = H * NX;                   // floats per (parity, side, field)
+  float* recv = mu + (C::MU ? PL : 0);  // [parity][side][f][r][x]
+  const int EXF = H * NX;                // floats per (parity, side, field)
   const int y0 = rank * B;
   const int nx4 = NX / 4;
 
   // stage rows y0 - H .. y0 + B + H - 1 (periodic in y) with their halo columns
-  for (int i = threadIdx.x; i < HT * nx4; i += kNT2) {
+  for (int i = threadIdx.x; i < HT * nx4; i += kNTC) {
     const int r = i / nx4, j = i - r * nx4;
     const int gy = wrap_index(y0 - H + r, g.ny);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-      *reinterpret_cast<float4*>(cur + f * PL + r * WS + HP + 4 * j) =
-          __ldg(reinterpret_cast<const float4*>(in.f[f] + gy * g.pitch + 4 * j));
+      put_row4<HP>(cur + f * PL + r * WS, j, NX,
+                   __ldg(reinterpret_cast<const float4*>(in.f[f] + gy * g.pitch + 4 * j)));
   }
   __syncthreads();
 
@@ -90,40 +104,21 @@ __global__ void __launch_bounds__(kNT2, 1)
   for (int64_t left = n_steps; left > 0;) {
     const int keff = left >= K ? K : (int)left;
     if (!first) {
-      // 1. halo rows from the neighbours' exports (distributed shared memory)
-      const float* ex_up = cluster.map_shared_rank(exports, (rank + cs - 1) % cs);
-      const float* ex_dn = cluster.map_shared_rank(exports, (rank + 1) % cs);
-      for (int i = threadIdx.x; i < NF * H * nx4; i += kNT2) {
+      // 1. halo rows from the receive buffer (parity par), with their periodic copies
+      for (int i = threadIdx.x; i < NF * H * nx4; i += kNTC) {
         const int f = i / (H * nx4);
         const int rem = i - f * H * nx4;
         const int r = rem / nx4, j = rem - r * nx4;
         const int eo = f * EXF + r * NX + 4 * j;
-        // the band above exported its bottom rows (side 1); the band below its top rows
-        const float4 top = *reinterpret_cast<const float4*>(ex_up + (par * 2 + 1) * NF * EXF + eo);
-        const float4 bot = *reinterpret_cast<const float4*>(ex_dn + (par * 2 + 0) * NF * EXF + eo);
-        *reinterpret_cast<float4*>(cur + f * PL + r * WS + HP + 4 * j) = top;
-        *reinterpret_cast<float4*>(cur + f * PL + (H + B + r) * WS + HP + 4 * j) = bot;
+        put_row4<HP>(cur + f * PL + r * WS, j, NX,
+                     *reinterpret_cast<const float4*>(recv + (par * 2 + 0) * NF * EXF + eo));
+        put_row4<HP>(cur + f * PL + (H + B + r) * WS, j, NX,
+                     *reinterpret_cast<const float4*>(recv + (par * 2 + 1) * NF * EXF + eo));
       }
       __syncthreads();
     }
     first = false;
-    // 2. halo columns: left HP columns copy the row's last HP values, right HP its first
-    for (int i = threadIdx.x; i < NF * HT * (HP / 4) * 2; i += kNT2) {
-      const int side = i & 1;
-      const int q = i >> 1;
-      const int f = q / (HT * (HP / 4));
-      const int rem = q - f * HT * (HP / 4);
-      const int r = rem / (HP / 4), j = rem - r * (HP / 4);
-      float* row = cur + f * PL + r * WS;
-      if (side == 0)
-        *reinterpret_cast<float4*>(row + 4 * j) =
-            *reinterpret_cast<const float4*>(row + NX + 4 * j);
-      else
-        *reinterpret_cast<float4*>(row + HP + NX + 4 * j) =
-            *reinterpret_cast<const float4*>(row + HP + 4 * j);
-    }
-    __syncthreads();
-    // 3. keff sub-steps; with keff < K the regions start as if K - keff sub-steps had run
+    // 2. keff sub-steps; with keff < K the regions start as if K - keff sub-steps had run
     for (int s = 0; s < keff; ++s) {
       const int e = s + (K - keff);
       const bool last = (s == keff - 1);
@@ -132,7 +127,7 @@ __global__ void __launch_bounds__(kNT2, 1)
         const int clo = (HP - H + R * e + RS) / 4;
         const int chi = (WS - (HP - H + R * e + RS) + 3) / 4;
         const int nch = chi - clo;
-        for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
+        for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNTC) {
           const int rr = i / nch;
           const int p = (rlo + rr) * WS + 4 * (clo + i - rr * nch);
           site4_mu<MODEL, PF_ST_STD>(cur, p, WS, PL, m, mu);
@@ -143,13 +138,20 @@ __global__ void __launch_bounds__(kNT2, 1)
       const int clo = last ? HP / 4 : (HP - H + R * (e + 1)) / 4;
       const int chi = last ? (HP + NX) / 4 : (WS - (HP - H + R * (e + 1)) + 3) / 4;
       const int nch = chi - clo;
-      for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
+      for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNTC) {
         const int rr = i / nch;
-        const int p = (rlo + rr) * WS + 4 * (clo + i - rr * nch);
+        const int j = clo + i - rr * nch;
+        const int p = (rlo + rr) * WS + 4 * j;
         float4 val[NF];
         site4_update<MODEL, PF_ST_STD>(cur, mu, p, WS, PL, m, val);
+        if (last) {  // band interior: also the periodic copies, for the next super-step
 #pragma unroll
-        for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(alt + f * PL + p) = val[f];
+          for (int f = 0; f < NF; ++f)
+            put_row4<HP>(alt + f * PL + (rlo + rr) * WS, j - HP / 4, NX, val[f]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(alt + f * PL + p) = val[f];
+        }
       }
       __syncthreads();
       float* t = cur;
@@ -158,16 +160,19 @@ __global__ void __launch_bounds__(kNT2, 1)
     }
     left -= keff;
     if (left > 0) {
-      // 4. export the band's top and bottom H rows (parity par ^ 1), then synchronise
+      // 3. the band's top H rows into the receive buffer of the band above (its side 1),
+      // the bottom H rows into that of the band below (its side 0), parity par ^ 1
       const int np = par ^ 1;
-      for (int i = threadIdx.x; i < NF * H * nx4; i += kNT2) {
+      float* rv_up = cluster.map_shared_rank(recv, (rank + cs - 1) % cs);
+      float* rv_dn = cluster.map_shared_rank(recv, (rank + 1) % cs);
+      for (int i = threadIdx.x; i < NF * H * nx4; i += kNTC) {
         const int f = i / (H * nx4);
         const int rem = i - f * H * nx4;
         const int r = rem / nx4, j = rem - r * nx4;
         const int eo = f * EXF + r * NX + 4 * j;
-        *reinterpret_cast<float4*>(exports + (np * 2 + 0) * NF * EXF + eo) =
+        *reinterpret_cast<float4*>(rv_up + (np * 2 + 1) * NF * EXF + eo) =
             *reinterpret_cast<const float4*>(cur + f * PL + (H + r) * WS + HP + 4 * j);
-        *reinterpret_cast<float4*>(exports + (np * 2 + 1) * NF * EXF + eo) =
+        *reinterpret_cast<float4*>(rv_dn + (np * 2 + 0) * NF * EXF + eo) =
             *reinterpret_cast<const float4*>(cur + f * PL + (B + r) * WS + HP + 4 * j);
       }
       par = np;
@@ -175,14 +180,13 @@ __global__ void __launch_bounds__(kNT2, 1)
     }
   }
   // the band's rows to global memory
-  for (int i = threadIdx.x; i < B * nx4; i += kNT2) {
+  for (int i = threadIdx.x; i < B * nx4; i += kNTC) {
     const int r = i / nx4, j = i - r * nx4;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       *reinterpret_cast<float4*>(out.f[f] + (int64_t)(y0 + r) * g.pitch + 4 * j) =
           *reinterpret_cast<const float4*>(cur + f * PL + (H + r) * WS + HP + 4 * j);
   }
-  cluster.sync();  // neighbours may still read this CTA's exports until they pass here
 }
 
 template <int MODEL, int K>
@@ -214,7 +218,7 @@ int cluster_size_for_device() {
       cudaSuccess) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(kNT2);
+    cfg.blockDim = dim3(kNTC);
     cfg.dynamicSmemBytes = 0;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
@@ -253,7 +257,7 @@ cudaError_t launch_cluster(const Geom& q, FieldPtrs in, FieldOut out, const Mode
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(kNT2);
+  cfg.blockDim = dim3(kNTC);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr;
@@ -274,13 +278,15 @@ bool fe2d_cluster_supported(int model, int k, const Geom& q) {
   const int cs = cluster_size_for_device();
   switch (model) {
     case PF_MODEL_AC:
-      return k == 1 ? cluster_fits<PF_MODEL_AC, 1>(q, cs)
-                    : k == 2 ? cluster_fits<PF_MODEL_AC, 2>(q, cs)
-                             : k == 4 && cluster_fits<PF_MODEL_AC, 4>(q, cs);
+      return k == 1   ? cluster_fits<PF_MODEL_AC, 1>(q, cs)
+             : k == 2 ? cluster_fits<PF_MODEL_AC, 2>(q, cs)
+             : k == 4 ? cluster_fits<PF_MODEL_AC, 4>(q, cs)
+                      : k == 8 && cluster_fits<PF_MODEL_AC, 8>(q, cs);
     case PF_MODEL_GS:
-      return k == 1 ? cluster_fits<PF_MODEL_GS, 1>(q, cs)
-                    : k == 2 ? cluster_fits<PF_MODEL_GS, 2>(q, cs)
-                             : k == 4 && cluster_fits<PF_MODEL_GS, 4>(q, cs);
+      return k == 1   ? cluster_fits<PF_MODEL_GS, 1>(q, cs)
+             : k == 2 ? cluster_fits<PF_MODEL_GS, 2>(q, cs)
+             : k == 4 ? cluster_fits<PF_MODEL_GS, 4>(q, cs)
+                      : k == 8 && cluster_fits<PF_MODEL_GS, 8>(q, cs);
     case PF_MODEL_CH:
       return k == 1 ? cluster_fits<PF_MODEL_CH, 1>(q, cs)
                     : k == 2 && cluster_fits<PF_MODEL_CH, 2>(q, cs);
@@ -298,11 +304,13 @@ cudaError_t launch_fe2d_cluster(int model, int k, const Geom& q, FieldPtrs in, F
     case PF_MODEL_AC:
       if (k == 1) return launch_cluster<PF_MODEL_AC, 1>(q, in, out, m, n_steps, st);
       if (k == 2) return launch_cluster<PF_MODEL_AC, 2>(q, in, out, m, n_steps, st);
-      return launch_cluster<PF_MODEL_AC, 4>(q, in, out, m, n_steps, st);
+      if (k == 4) return launch_cluster<PF_MODEL_AC, 4>(q, in, out, m, n_steps, st);
+      return launch_cluster<PF_MODEL_AC, 8>(q, in, out, m, n_steps, st);
     case PF_MODEL_GS:
       if (k == 1) return launch_cluster<PF_MODEL_GS, 1>(q, in, out, m, n_steps, st);
       if (k == 2) return launch_cluster<PF_MODEL_GS, 2>(q, in, out, m, n_steps, st);
-      return launch_cluster<PF_MODEL_GS, 4>(q, in, out, m, n_steps, st);
+      if (k == 4) return launch_cluster<PF_MODEL_GS, 4>(q, in, out, m, n_steps, st);
+      return launch_cluster<PF_MODEL_GS, 8>(q, in, out, m, n_steps, st);
     case PF_MODEL_CH:
       if (k == 1) return launch_cluster<PF_MODEL_CH, 1>(q, in, out, m, n_steps, st);
       return launch_cluster<PF_MODEL_CH, 2>(q, in, out, m, n_steps, st);
