@@ -480,6 +480,34 @@ def run_spectral_case(spec: str):
                       "final_finite": bool(all(np.isfinite(x).all() for x in final))}))
 
 
+def run_adjoint_case(spec: str):
+    """The Gray-Scott adjoint workload's recipe on an N x N grid for STEPS steps: the plain
+    forward run, the checkpointed forward and the reverse pass, each timed with CUDA events
+    after one untimed call of the same length."""
+    import torch
+    import paper_2109_02598_gb300 as pf
+    n, steps = (int(v) for v in spec.split(":"))
+    w = synthetic.WORKLOADS["gs2d_adjoint_512"]
+    u0, v0 = synthetic.workload_init("gs2d_adjoint_512", shape=(n, n))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = pf.Grid((n, n), 2, stream=stream).set_model("gs", w["coeffs"], w["dt"])
+        g.write_fields((u0, v0))
+        g.step(steps)
+        plain = _time(stream, lambda: g.step(steps))
+        g.write_fields((u0, v0))
+        pf.adjoint_forward(g, steps)
+        fwd = _time(stream, lambda: pf.adjoint_forward(g, steps))
+        gu = g.read_field(0, device=True) * 0.01
+        gv = g.read_field(1, device=True) * 0.01
+        pf.adjoint_backward(g, gu, gv)
+        bwd = _time(stream, lambda: pf.adjoint_backward(g, gu, gv))
+        g.close()
+    print(json.dumps({"adjoint": spec, "plain_forward_ms": plain, "adjoint_forward_ms": fwd,
+                      "adjoint_backward_ms": bwd, "ratio_vs_plain": (fwd + bwd) / plain,
+                      "reverse_us_per_step": bwd * 1e3 / steps}))
+
+
 def run_euler_case(spec: str):
     """One forward-Euler case: the paper's U(-1, 1) initial fields (Gray-Scott: seeded
     squares), the coefficients and Delta t of the parity tests, STEPS steps timed with CUDA
@@ -539,7 +567,14 @@ def main():
     ap.add_argument("--euler", metavar="MODEL:NXxNY[xNZ]:STEPS[:TX:TY:K]",
                     help="time one forward-Euler case alone (autotuned unless a tuning is "
                          "given; e.g. ac:128x128:1000) and print its JSON line")
+    ap.add_argument("--adjoint", metavar="N:STEPS",
+                    help="time the Gray-Scott adjoint alone on an N x N grid (forward with "
+                         "checkpoints, reverse pass, and the plain forward run) and print its "
+                         "JSON line")
     args = ap.parse_args()
+    if args.adjoint:
+        run_adjoint_case(args.adjoint)
+        return
     if args.spectral:
         run_spectral_case(args.spectral)
         return

@@ -36,67 +36,104 @@ namespace {
 constexpr int kATX = 64, kATY = 16;  // adjoint tile
 constexpr int kAW = kATX + 2, kAH = kATY + 2, kAPL = kAW * kAH;
 
+// Warp sum of per-thread float partials, in float (a fixed tree, so the same bits on every
+// run), widened to double for the per-warp and per-CTA sums. FP64 arithmetic is a small
+// fraction of FP32 throughput on this GPU: a double-precision shuffle tree in every CTA of
+// every reverse step took most of the kernel's time.
+__device__ __forceinline__ double warp_sum_f(double v) {
+  float f = (float)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f = __fadd_rn(f, __shfl_down_sync(0xffffffffu, f, o));
+  return (double)f;
+}
+
+// Double-precision warp sum, for the final fixed-order sum over the CTAs' slots (once per
+// reverse pass).
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-// One reverse step on a 2D tile: stage u, v, a, b with a periodic halo of 1, update
-// (a, b) and add this tile's parameter-gradient terms to its FP64 slot.
+// One reverse step on a 64 x 16 tile: stage u, v (the state x^n) and a, b (lambda^{n+1})
+// with a periodic halo of 1 as aligned float4 groups (the forward tile body's staging), then
+// four sites per thread: update (a, b) and add the parameter-gradient terms to per-thread
+// sums, which go to this tile's FP64 slot in a fixed order.
+using AdjCfg = Cfg2<PF_MODEL_GS, 1, kATX, kATY>;
+
 __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs lam,
                                                         FieldOut lam_out, Geom g,
                                                         ModelParams m, double* gpart) {
-  __shared__ float su[kAPL], sv[kAPL], sa[kAPL], sb[kAPL];
+  constexpr int WS = AdjCfg::WS, PL = AdjCfg::PL, HP = AdjCfg::HP, H = AdjCfg::H;
+  __shared__ __align__(16) float sm[4 * PL];  // u, v, a, b
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
   const int y0 = blockIdx.y * kATY;
-  for (int i = threadIdx.x; i < kAPL; i += kNT2) {
-    const int r = i / kAW;
-    const int c = i - r * kAW;
-    const int gy = wrap_index(y0 - 1 + r, g.ny);
-    const int gx = wrap_index(x0 - 1 + c, g.nx);
-    const int64_t off = (int64_t)gy * g.pitch + gx;
-    su[i] = __ldg(x.f[0] + off);
-    sv[i] = __ldg(x.f[1] + off);
-    sa[i] = __ldg(lam.f[0] + off);
-    sb[i] = __ldg(lam.f[1] + off);
-  }
+  load_region2d<AdjCfg>(x, g.nx, g.ny, g.pitch, x0, y0, sm);
+  load_region2d<AdjCfg>(lam, g.nx, g.ny, g.pitch, x0, y0, sm + 2 * PL);
   __syncthreads();
+  const float* su = sm;
+  const float* sv = sm + PL;
+  const float* sa = sm + 2 * PL;
+  const float* sb = sm + 3 * PL;
   float pDu = 0.f, pDv = 0.f, pF = 0.f, pk = 0.f;
-  for (int i = threadIdx.x; i < kATX * kATY; i += kNT2) {
-    const int rr = i / kATX;
-    const int cc = i - rr * kATX;
-    const int gx = x0 + cc;
+  constexpr int NG = kATX / 4;  // float4 groups per tile row
+  for (int i = threadIdx.x; i < kATY * NG; i += kNT2) {
+    const int rr = i / NG, j = i - rr * NG;
     const int gy = y0 + rr;
-    if (gx >= g.nx || gy >= g.ny) continue;
-    const int p = (rr + 1) * kAW + (cc + 1);
-    const float u = su[p], v = sv[p], a = sa[p], b = sb[p];
-    const float la = lap2d(a, sa[p - 1], sa[p + 1], sa[p - kAW], sa[p + kAW], m.lap_scale);
-    const float lb = lap2d(b, sb[p - 1], sb[p + 1], sb[p - kAW], sb[p + kAW], m.lap_scale);
-    const float lu = lap2d(u, su[p - 1], su[p + 1], su[p - kAW], su[p + kAW], m.lap_scale);
-    const float lv = lap2d(v, sv[p - 1], sv[p + 1], sv[p - kAW], sv[p + kAW], m.lap_scale);
-    const float vv = __fmul_rn(v, v);
-    const float uv2 = __fmul_rn(2.0f, __fmul_rn(u, v));
-    // a' = a + dt [Du la - (v^2 + F) a + v^2 b]
-    float fa = __fmaf_rn(-__fadd_rn(vv, m.a2), a, __fmul_rn(vv, b));
-    fa = __fmaf_rn(m.a0, la, fa);
-    // b' = b + dt [Dv lb - 2uv a + (2uv - F - k) b]
-    float fb = __fmaf_rn(__fsub_rn(uv2, m.a3), b, -__fmul_rn(uv2, a));
-    fb = __fmaf_rn(m.a1, lb, fb);
+    const int gx = x0 + 4 * j;
+    if (gy >= g.ny || gx >= g.nx) continue;
+    const int p = (rr + H) * WS + HP + 4 * j;
+    const float4 u4 = *reinterpret_cast<const float4*>(su + p);
+    const float4 v4 = *reinterpret_cast<const float4*>(sv + p);
+    const float4 a4 = *reinterpret_cast<const float4*>(sa + p);
+    const float4 b4 = *reinterpret_cast<const float4*>(sb + p);
+    const float4 la4 = lap2d_x4(sa, p, WS, m.lap_scale);
+    const float4 lb4 = lap2d_x4(sb, p, WS, m.lap_scale);
+    const float4 lu4 = lap2d_x4(su, p, WS, m.lap_scale);
+    const float4 lv4 = lap2d_x4(sv, p, WS, m.lap_scale);
+    const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, vv_[4] = {v4.x, v4.y, v4.z, v4.w};
+    const float aa[4] = {a4.x, a4.y, a4.z, a4.w}, bb[4] = {b4.x, b4.y, b4.z, b4.w};
+    const float la[4] = {la4.x, la4.y, la4.z, la4.w}, lb[4] = {lb4.x, lb4.y, lb4.z, lb4.w};
+    const float lu[4] = {lu4.x, lu4.y, lu4.z, lu4.w}, lv[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+    float na[4], nb[4];
+    const int nvalid = g.nx - gx < 4 ? g.nx - gx : 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float u = uu[e], v = vv_[e], a = aa[e], b = bb[e];
+      const float vv = __fmul_rn(v, v);
+      const float uv2 = __fmul_rn(2.0f, __fmul_rn(u, v));
+      // a' = a + dt [Du la - (v^2 + F) a + v^2 b]
+      float fa = __fmaf_rn(-__fadd_rn(vv, m.a2), a, __fmul_rn(vv, b));
+      fa = __fmaf_rn(m.a0, la[e], fa);
+      // b' = b + dt [Dv lb - 2uv a + (2uv - F - k) b]
+      float fb = __fmaf_rn(__fsub_rn(uv2, m.a3), b, -__fmul_rn(uv2, a));
+      fb = __fmaf_rn(m.a1, lb[e], fb);
+      na[e] = __fmaf_rn(m.dt, fa, a);
+      nb[e] = __fmaf_rn(m.dt, fb, b);
+      if (e < nvalid) {
+        pDu = __fmaf_rn(a, lu[e], pDu);
+        pDv = __fmaf_rn(b, lv[e], pDv);
+        pF = __fadd_rn(pF, __fsub_rn(__fmul_rn(__fsub_rn(1.0f, u), a), __fmul_rn(v, b)));
+        pk = __fsub_rn(pk, __fmul_rn(v, b));
+      }
+    }
     const int64_t off = (int64_t)gy * g.pitch + gx;
-    lam_out.f[0][off] = __fmaf_rn(m.dt, fa, a);
-    lam_out.f[1][off] = __fmaf_rn(m.dt, fb, b);
-    pDu = __fmaf_rn(a, lu, pDu);
-    pDv = __fmaf_rn(b, lv, pDv);
-    pF = __fadd_rn(pF, __fsub_rn(__fmul_rn(__fsub_rn(1.0f, u), a), __fmul_rn(v, b)));
-    pk = __fsub_rn(pk, __fmul_rn(v, b));
+    if (nvalid == 4) {
+      *reinterpret_cast<float4*>(lam_out.f[0] + off) = make_float4(na[0], na[1], na[2], na[3]);
+      *reinterpret_cast<float4*>(lam_out.f[1] + off) = make_float4(nb[0], nb[1], nb[2], nb[3]);
+    } else {
+      for (int e = 0; e < nvalid; ++e) {
+        lam_out.f[0][off + e] = na[e];
+        lam_out.f[1][off + e] = nb[e];
+      }
+    }
   }
   double t[4] = {pDu, pDv, pF, pk};
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    t[q] = warp_sum_d(t[q]);
+    t[q] = warp_sum_f(t[q]);
     if (lane == 0) red[q][wid] = t[q];
   }
   __syncthreads();
@@ -115,7 +152,7 @@ __device__ __forceinline__ void add_to_slot(double (&t)[4], double (&red)[4][kNT
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NG; ++q) {
-    t[q] = warp_sum_d(t[q]);
+    t[q] = warp_sum_f(t[q]);
     if (lane == 0) red[q][wid] = t[q];
   }
   __syncthreads();
