@@ -87,6 +87,10 @@ __global__ void __launch_bounds__(kNTC, 1)
   const int EXF = H * NX;                // floats per (parity, side, field)
   const int y0 = rank * B;
   const int nx4 = NX / 4;
+  // sub-step work: thread (tr, tj) takes column groups tj, tj + ngl, ... of rows
+  // rlo + tr, rlo + tr + rstep, ... (no per-item division)
+  const int ngl = WS / 4 < kNTC ? WS / 4 : kNTC;
+  const int tj = threadIdx.x % ngl, tr = threadIdx.x / ngl, rstep = kNTC / ngl;
 
   // stage rows y0 - H .. y0 + B + H - 1 (periodic in y) with their halo columns
   for (int i = threadIdx.x; i < HT * nx4; i += kNTC) {
@@ -126,31 +130,31 @@ __global__ void __launch_bounds__(kNTC, 1)
         const int rlo = R * e + RS, rhi = HT - rlo;
         const int clo = (HP - H + R * e + RS) / 4;
         const int chi = (WS - (HP - H + R * e + RS) + 3) / 4;
-        const int nch = chi - clo;
-        for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNTC) {
-          const int rr = i / nch;
-          const int p = (rlo + rr) * WS + 4 * (clo + i - rr * nch);
-          site4_mu<MODEL, PF_ST_STD>(cur, p, WS, PL, m, mu);
-        }
+        if (tr < rstep)
+          for (int r = rlo + tr; r < rhi; r += rstep)
+            for (int j = tj; j < chi; j += ngl)
+              if (j >= clo) site4_mu<MODEL, PF_ST_STD>(cur, r * WS + 4 * j, WS, PL, m, mu);
         __syncthreads();
       }
       const int rlo = R * (e + 1), rhi = HT - rlo;
       const int clo = last ? HP / 4 : (HP - H + R * (e + 1)) / 4;
       const int chi = last ? (HP + NX) / 4 : (WS - (HP - H + R * (e + 1)) + 3) / 4;
-      const int nch = chi - clo;
-      for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNTC) {
-        const int rr = i / nch;
-        const int j = clo + i - rr * nch;
-        const int p = (rlo + rr) * WS + 4 * j;
-        float4 val[NF];
-        site4_update<MODEL, PF_ST_STD>(cur, mu, p, WS, PL, m, val);
-        if (last) {  // band interior: also the periodic copies, for the next super-step
+      if (tr < rstep) {
+        for (int r = rlo + tr; r < rhi; r += rstep) {
+          for (int j = tj; j < chi; j += ngl) {
+            if (j < clo) continue;
+            const int p = r * WS + 4 * j;
+            float4 val[NF];
+            site4_update<MODEL, PF_ST_STD>(cur, mu, p, WS, PL, m, val);
+            if (last) {  // band interior: also the periodic copies, for the next super-step
 #pragma unroll
-          for (int f = 0; f < NF; ++f)
-            put_row4<HP>(alt + f * PL + (rlo + rr) * WS, j - HP / 4, NX, val[f]);
-        } else {
+              for (int f = 0; f < NF; ++f)
+                put_row4<HP>(alt + f * PL + r * WS, j - HP / 4, NX, val[f]);
+            } else {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(alt + f * PL + p) = val[f];
+              for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(alt + f * PL + p) = val[f];
+            }
+          }
         }
       }
       __syncthreads();
