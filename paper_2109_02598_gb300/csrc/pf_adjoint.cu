@@ -55,20 +55,23 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// One reverse step on a 64 x 16 tile: stage u, v (the state x^n) and a, b (lambda^{n+1})
+// One reverse step on a 64 x TY tile: stage u, v (the state x^n) and a, b (lambda^{n+1})
 // with a periodic halo of 1 as aligned float4 groups (the forward tile body's staging), then
 // four sites per thread: update (a, b) and add the parameter-gradient terms to per-thread
 // sums, which go to this tile's FP64 slot in a fixed order.
-using AdjCfg = Cfg2<PF_MODEL_GS, 1, kATX, kATY>;
-
+// TY = 8 on grids too small to give every SM several 16-row tiles (more CTAs in flight hide
+// the L2 latency of the staging: 512^2 reverse step 8.4 -> 7.6 us), else 16 (2048^2: 49.5 us
+// with 16 rows, 58.8 with 8).
+template <int TY>
 __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs lam,
                                                         FieldOut lam_out, Geom g,
                                                         ModelParams m, double* gpart) {
+  using AdjCfg = Cfg2<PF_MODEL_GS, 1, kATX, TY>;
   constexpr int WS = AdjCfg::WS, PL = AdjCfg::PL, HP = AdjCfg::HP, H = AdjCfg::H;
   __shared__ __align__(16) float sm[4 * PL];  // u, v, a, b
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
-  const int y0 = blockIdx.y * kATY;
+  const int y0 = blockIdx.y * TY;
   load_region2d<AdjCfg>(x, g.nx, g.ny, g.pitch, x0, y0, sm);
   load_region2d<AdjCfg>(lam, g.nx, g.ny, g.pitch, x0, y0, sm + 2 * PL);
   __syncthreads();
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs l
   const float* sb = sm + 3 * PL;
   float pDu = 0.f, pDv = 0.f, pF = 0.f, pk = 0.f;
   constexpr int NG = kATX / 4;  // float4 groups per tile row
-  for (int i = threadIdx.x; i < kATY * NG; i += kNT2) {
+  for (int i = threadIdx.x; i < TY * NG; i += kNT2) {
     const int rr = i / NG, j = i - rr * NG;
     const int gy = y0 + rr;
     const int gx = x0 + 4 * j;
@@ -278,7 +281,29 @@ __global__ void __launch_bounds__(256) adj_final_kernel(const double* gpart, int
   }
 }
 
-dim3 adj_grid(const Geom& g) { return dim3((g.nx + kATX - 1) / kATX, (g.ny + kATY - 1) / kATY, 1); }
+// Tile height of the Gray-Scott reverse step on this grid (see adj_gs2d_kernel): 8 when
+// 16-row tiles would give fewer than four per SM, else 16.
+int gs_adj_ty(const Geom& q, int device) {
+  static int sms_by_dev[64] = {};
+  int sms = device >= 0 && device < 64 ? sms_by_dev[device] : 0;
+  if (sms == 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 1;
+    } else if (device >= 0 && device < 64) {
+      sms_by_dev[device] = sms;
+    }
+  }
+  const int64_t tiles16 = (int64_t)((q.nx + kATX - 1) / kATX) * ((q.ny + 15) / 16);
+  return tiles16 < 4 * (int64_t)sms ? 8 : 16;
+}
+
+// Reverse-step launch grid for the grid's model.
+dim3 adj_grid(const pf_grid_s* g) {
+  const Geom q = grid_geom(g);
+  const int ty = g->model == PF_MODEL_GS ? gs_adj_ty(q, g->device) : kATY;
+  return dim3((q.nx + kATX - 1) / kATX, (q.ny + ty - 1) / ty, 1);
+}
 
 float* ckpt_field(pf_grid_s* g, int64_t i, int f) {
   return g->adj.ckpt + (i * g->nf + f) * g->field_elems;
@@ -321,7 +346,8 @@ static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStrea
                                    int* lb_out) {
   AdjointState& a = g->adj;
   const Geom q = grid_geom(g);
-  const dim3 grid = adj_grid(q);
+  const dim3 grid = adj_grid(g);
+  const int gs_ty = gs_adj_ty(q, g->device);
   const int64_t nctas = (int64_t)grid.x * grid.y;
   cudaError_t e = cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, st);
   int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
@@ -351,7 +377,10 @@ static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStrea
         lo.f[f] = lam_field(g, 1 - lb, f);
       }
       if (g->model == PF_MODEL_GS)
-        adj_gs2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+        if (gs_ty == 8)
+          adj_gs2d_kernel<8><<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
+        else
+          adj_gs2d_kernel<16><<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
       else if (g->model == PF_MODEL_AC)
         adj_ac2d_kernel<<<grid, kNT2, 0, st>>>(xs, li, lo, q, m, a.gpart);
       else
@@ -399,7 +428,7 @@ int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval) {
     PF_CUDA_TRY(cudaMalloc(&a.lam, 2 * state));
     PF_CUDA_TRY(cudaMemsetAsync(a.lam, 0, 2 * state, g->stream));
   }
-  const dim3 grid = adj_grid(grid_geom(g));
+  const dim3 grid = adj_grid(g);
   const int64_t nctas = (int64_t)grid.x * grid.y;
   if (a.gpart_cap < nctas) {
     if (a.gpart) cudaFree(a.gpart);
