@@ -80,7 +80,7 @@ __device__ __forceinline__ float4 lap3d_x4(const float4& c, const float4& ym, co
 template <int MODEL, int W, int TY, int NS>
 __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
     fe3d_tb2_kernel(const __grid_constant__ Tb2Maps maps, FieldOut out, Geom g, ModelParams m,
-                    int nchunks, int chunk_len, int* err_flag) {
+                    int nchunks, int chunk_len, int balanced, int* err_flag) {
   using C = CfgB<MODEL, W, TY, NS>;
   constexpr int NF = C::NF;
   constexpr int LX = C::LX;
@@ -124,13 +124,34 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
 
   const int ncols = g.ny / TY;
   const int nitems = ncols * nchunks;
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int col = item % ncols;
-    const int chunk = item / ncols;
-    const int zlo = chunk * chunk_len;
-    const int zhi = min(g.nz, zlo + chunk_len);
-    if (zlo >= zhi) continue;  // uniform over the CTA
-    const int dir = (chunk & 1) ? -1 : 1;
+  // Work: (row tile, z-range) segments. Item mode: item = (tile, chunk of chunk_len planes),
+  // items dealt round-robin over the CTAs, chunks alternating up and down. Balanced mode:
+  // the (tile, plane) units in tile-major order cut into gridDim.x equal ranges, one per CTA
+  // (a range crossing a tile boundary makes two segments), direction alternating by CTA.
+  // units = ny nz / TY < 2^31 for every grid this kernel takes (nx = W, at most 2^36 sites)
+  const int units = ncols * g.nz;
+  int pos = (int)((int64_t)units * blockIdx.x / gridDim.x);
+  const int pos_end = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
+  int item = blockIdx.x;
+  for (;;) {
+    int col, zlo, zhi, dir;
+    if (balanced) {
+      if (pos >= pos_end) break;
+      col = pos / g.nz;
+      zlo = pos - col * g.nz;
+      zhi = min(g.nz, zlo + (pos_end - pos));
+      dir = (blockIdx.x & 1) ? -1 : 1;
+      pos += zhi - zlo;
+    } else {
+      if (item >= nitems) break;
+      col = item % ncols;
+      const int chunk = item / ncols;
+      zlo = chunk * chunk_len;
+      zhi = min(g.nz, zlo + chunk_len);
+      dir = (chunk & 1) ? -1 : 1;
+      item += gridDim.x;
+      if (zlo >= zhi) continue;  // uniform over the CTA
+    }
     const int n = zhi - zlo;                  // output planes
     const int zfirst = dir > 0 ? zlo : zhi - 1;
     const int y0 = col * TY;
@@ -258,9 +279,21 @@ cudaError_t launch_tb2(pf_grid_s* gr, const Tb2Maps& maps, FieldOut out, cudaStr
   const int chunk_len = (int)((g.nz + nchunks - 1) / nchunks);
   nchunks = (g.nz + chunk_len - 1) / chunk_len;
   const long long items = ncols * nchunks;
-  const long long grid = items < slots ? items : slots;
+  long long grid = items < slots ? items : slots;
+  // Balanced mode when it shortens the longest CTA's plane count (each segment also streams
+  // 4 halo planes): item mode runs ceil(items / grid) items of chunk_len + 4 planes, balanced
+  // mode about units / slots + 8 planes (two segments at most when a range is under nz).
+  const long long units = ncols * (long long)g.nz;
+  const long long item_span = (items + grid - 1) / grid * (chunk_len + 4);
+  const long long per = (units + slots - 1) / slots;
+  const long long bal_span = per + (per < g.nz ? 8 : 4 * ((per + g.nz - 1) / g.nz + 1));
+  int balanced = 0;
+  if (bal_span < item_span && slots > grid) {
+    balanced = 1;
+    grid = slots < units ? slots : units;
+  }
   kern<<<(unsigned)grid, C::NT, C::SMEM, st>>>(maps, out, g, gr->params, (int)nchunks, chunk_len,
-                                               gr->d_err);
+                                               balanced, gr->d_err);
   return cudaGetLastError();
 }
 

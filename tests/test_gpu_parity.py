@@ -162,6 +162,18 @@ def test_depth2_3d_kernel_is_bitwise_depth1(pf, model, shape, tile):
     assert rel_linf(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("model", ["ac", "gs"])
+def test_depth2_3d_balanced_split_is_bitwise_depth1(pf, model):
+    # 256 x 256 rows and 160 planes: 32 row tiles; the host hands the SMs equal ranges of
+    # the (tile, plane) sequence, ranges that cross tile boundaries (balanced mode)
+    shape = (160, 256, 256)
+    x0 = init_fields(model, shape, seed=13)
+    base = gpu_run(pf, model, x0, 4, tuning=(64, 16, 1))
+    got = gpu_run(pf, model, x0, 4, tuning=(256, 8, 2))
+    for a, b in zip(base, got):
+        assert np.array_equal(a, b)
+
+
 def test_depth2_3d_rejected_where_unsupported(pf):
     from paper_2109_02598_gb300 import PfError
     g = pf.Grid((8, 16, 64), 2).set_model("gs", COEFFS["gs"], DT["gs"])
