@@ -174,12 +174,19 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
       const int clo = (C::HP - C::H + C::R * s + C::RS) / 4;
       const int chi = (WS - (C::HP - C::H + C::R * s + C::RS) + 3) / 4;
       const int nch = chi - clo;
-      for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
-        const int rr = i / nch;
-        const int r = rlo + rr;
-        const int p = r * WS + 4 * (clo + i - rr * nch);
-        site4_mu<MODEL, ST>(src, p, WS, PL, m, mu);
-      }
+      auto mu_rows = [&](const int nrows, const int ncols) {
+        for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
+          const int rr = i / ncols;
+          const int p = (rlo + rr) * WS + 4 * (clo + i - rr * ncols);
+          site4_mu<MODEL, ST>(src, p, WS, PL, m, mu);
+        }
+      };
+      // mu is needed R (K-1-s) + RS past the grid's last row and column, no further
+      const int marg = C::R * (K - 1 - s) + C::RS;
+      const int rhi_e = min(rhi, C::H + (ny - y0) + marg);
+      const int chi_e = min(chi, (C::HP + (nx - x0) + marg + 3) / 4);
+      if (rhi_e == rhi && chi_e == chi) mu_rows(rhi - rlo, nch);  // compile-time bounds
+      else if (rhi_e > rlo && chi_e > clo) mu_rows(rhi_e - rlo, chi_e - clo);
       __syncthreads();
     }
     const bool last = (s == K - 1);
@@ -187,10 +194,17 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
     const int clo = last ? C::HP / 4 : (C::HP - C::H + C::R * (s + 1)) / 4;
     const int chi = last ? (C::HP + TX) / 4 : (WS - (C::HP - C::H + C::R * (s + 1)) + 3) / 4;
     const int nch = chi - clo;
-    for (int i = threadIdx.x; i < (rhi - rlo) * nch; i += kNT2) {
-      const int rr = i / nch;
+    // A tile that reaches past the grid's last row or column (small or ragged grids, batch
+    // instances) skips the sites more than R (K-1-s) past it: they never reach a stored
+    // value. Tiles inside the grid keep the compile-time bounds.
+    const int marg = C::R * (K - 1 - s);
+    const int rhi_e = min(rhi, C::H + (ny - y0) + marg);
+    const int chi_e = min(chi, (C::HP + (nx - x0) + marg + 3) / 4);
+    auto update_rows = [&](const int nrows, const int ncols) {
+    for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
+      const int rr = i / ncols;
       const int r = rlo + rr;
-      const int j = clo + i - rr * nch;
+      const int j = clo + i - rr * ncols;
       const int p = r * WS + 4 * j;
       float4 val[C::NF];
       site4_update<MODEL, ST>(src, mu, p, WS, PL, m, val);
@@ -216,6 +230,9 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
         for (int f = 0; f < C::NF; ++f) *reinterpret_cast<float4*>(dst + f * PL + p) = val[f];
       }
     }
+    };
+    if (rhi_e == rhi && chi_e == chi) update_rows(rhi - rlo, nch);  // compile-time bounds
+    else if (rhi_e > rlo && chi_e > clo) update_rows(rhi_e - rlo, chi_e - clo);
     if (!last) __syncthreads();
   }
 }
