@@ -324,20 +324,8 @@ def companions(stream, hbm):
     out = {}
     with torch.cuda.stream(stream):
         # ---- batched: 512 x 2D Gray-Scott, sides log-uniform in [64, 512], 2000 steps
-        specs = synthetic.batch_instances(512, seed=4)
-        b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5,
-                     stream=stream)
-        for i, q in enumerate(specs):
-            u, v = synthetic.batch_instance_init(q["n"], i)
-            b.write(i, 0, u).write(i, 1, v)
-        tuning = b.autotune(3)
-        b.run(2000)
-        ms = _time(stream, lambda: b.run(2000))
-        bglups = b.sites * 2000 / (ms * 1e-3) / 1e9
-        out["batched_gs2d_512x"] = {
-            "steps": 2000, "sites": b.sites, "ms": ms, "glups": bglups, "tuning": list(tuning),
-            "hbm_frac_k1_bytes": bglups * 16 / hbm, "launch": "one CUDA graph per 2000 steps"}
-        b.close()
+        out["batched_gs2d_512x"] = batch_timing(stream, 2000, hbm)
+        bglups = out["batched_gs2d_512x"]["glups"]
         # ---- plain 2D Gray-Scott of comparable state size (4096^2, 268 MB ping-pong)
         u, v = synthetic.gray_scott_init((4096, 4096), seed=9, n_seeds=1024, side=8)
         g = pf.Grid((4096, 4096), 2, stream=stream).set_model("gs", (0.2, 0.1, 0.04, 0.06), 0.5)
@@ -464,6 +452,38 @@ def run_spectral_case(spec: str):
                       "final_finite": bool(all(np.isfinite(x).all() for x in final))}))
 
 
+def batch_timing(stream, steps: int, hbm: float) -> dict:
+    """The batched workload: 512 independent 2D Gray-Scott grids, sides log-uniform in
+    [64, 512], seeded F and k; autotuned, then `steps` steps timed as one CUDA-graph run after
+    one untimed run of the same length."""
+    import paper_2109_02598_gb300 as pf
+    specs = synthetic.batch_instances(512, seed=4)
+    b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5,
+                 stream=stream)
+    for i, q in enumerate(specs):
+        u, v = synthetic.batch_instance_init(q["n"], i)
+        b.write(i, 0, u).write(i, 1, v)
+    tuning = b.autotune(3)
+    b.run(steps)
+    ms = _time(stream, lambda: b.run(steps))
+    glups = b.sites * steps / (ms * 1e-3) / 1e9
+    res = {"steps": steps, "sites": b.sites, "ms": ms, "glups": glups, "tuning": list(tuning),
+           "hbm_frac_k1_bytes": glups * 16 / hbm,
+           "launch": f"one CUDA graph per {steps} steps"}
+    b.close()
+    return res
+
+
+def run_batch_case(steps: int):
+    """The batched workload alone, printing its JSON line."""
+    import torch
+    hbm, _ = _peaks()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        res = batch_timing(stream, steps, hbm)
+    print(json.dumps({"batch": steps, **res}))
+
+
 def adjoint_timing(stream, n: int, steps: int) -> dict:
     """The Gray-Scott adjoint workload's recipe on an n x n grid for `steps` steps: the plain
     forward run, the checkpointed forward and the reverse pass, each timed with CUDA events
@@ -564,7 +584,12 @@ def main():
                     help="time the Gray-Scott adjoint alone on an N x N grid (forward with "
                          "checkpoints, reverse pass, and the plain forward run) and print its "
                          "JSON line")
+    ap.add_argument("--batch", metavar="STEPS", type=int,
+                    help="time the 512-instance batched Gray-Scott workload alone")
     args = ap.parse_args()
+    if args.batch:
+        run_batch_case(args.batch)
+        return
     if args.adjoint:
         run_adjoint_case(args.adjoint)
         return
