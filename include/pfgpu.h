@@ -126,6 +126,18 @@ int pf_write_field(pf_grid_t g, int field, const float* src, int src_on_device);
  * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
 int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device);
 
+/* Host copies that do not wait: the copy of a dense float32 host array into field `field`
+ * (write) or of field `field` out to one (read) is enqueued on the grid's stream after the
+ * work already there, and the call returns. A caller that pipelines jobs (uploading the next
+ * job's fields and downloading the last one's results while a step runs, e.g. on two grids
+ * with two streams) uses these; the host array must be page-locked (pinned) for the copy to
+ * overlap other work, and must stay valid and untouched until the stream has passed the
+ * copy (pf_synchronize). A read sees the field as the preceding pf_step calls leave it.
+ * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA; a timed-out kernel wait is reported by the next
+ * pf_synchronize. */
+int pf_write_field_host_async(pf_grid_t g, int field, const float* src);
+int pf_read_field_host_async(pf_grid_t g, int field, float* dst);
+
 /* Advance the state by n_steps forward-Euler steps (Sec. 2.4.1), asynchronously on the
  * grid's stream. Uses temporal blocking of depth k (pf_set_tuning) where the model and
  * dimension support it; the result is bitwise the same for every k and tile shape.

@@ -57,6 +57,8 @@ SIGNATURES = {
     "pf_write_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "pf_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pf_write_field_host_async": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "pf_read_field_host_async": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "pf_reduce": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _c_double_p]),
     "pf_set_stencil": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pf_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),

@@ -433,6 +433,26 @@ int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device) {
   return PF_OK;
 }
 
+int pf_write_field_host_async(pf_grid_t g, int field, const float* src) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  if (src == nullptr) return invalid("src is NULL");
+  const size_t w = sizeof(float) * g->nx;
+  PF_CUDA_TRY(cudaMemcpy2DAsync(g->buf[g->cur][field], sizeof(float) * g->pitch, src, w, w,
+                                (size_t)g->ny * g->nz, cudaMemcpyHostToDevice, g->stream));
+  return PF_OK;
+}
+
+int pf_read_field_host_async(pf_grid_t g, int field, float* dst) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  if (dst == nullptr) return invalid("dst is NULL");
+  const size_t w = sizeof(float) * g->nx;
+  PF_CUDA_TRY(cudaMemcpy2DAsync(dst, w, g->buf[g->cur][field], sizeof(float) * g->pitch, w,
+                                (size_t)g->ny * g->nz, cudaMemcpyDeviceToHost, g->stream));
+  return PF_OK;
+}
+
 int pf_step(pf_grid_t g, int64_t n_steps) {
   if (int rc = check_grid(g)) return rc;
   if (!g->model_set) {

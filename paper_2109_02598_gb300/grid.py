@@ -142,6 +142,28 @@ class Grid:
     def read_fields(self, device: bool = False):
         return tuple(self.read_field(i, device=device) for i in range(self.n_fields))
 
+    def write_field_async(self, field: int, pinned):
+        """Enqueue the copy of a pinned host torch tensor of ``shape`` into ``field`` and
+        return; ``pinned`` must stay untouched until ``synchronize``."""
+        torch = _torch()
+        if (tuple(pinned.shape) != self.shape or not pinned.is_contiguous() or pinned.is_cuda
+                or pinned.dtype != torch.float32):
+            raise ValueError("needs a contiguous float32 host tensor of the grid's shape")
+        check(self._lib.pf_write_field_host_async(self._h, field,
+                                                  ctypes.c_void_p(pinned.data_ptr())))
+        return self
+
+    def read_field_async(self, field: int, pinned):
+        """Enqueue the copy of ``field`` into a pinned host torch tensor and return; its
+        contents are valid after ``synchronize``."""
+        torch = _torch()
+        if (tuple(pinned.shape) != self.shape or not pinned.is_contiguous() or pinned.is_cuda
+                or pinned.dtype != torch.float32):
+            raise ValueError("needs a contiguous float32 host tensor of the grid's shape")
+        check(self._lib.pf_read_field_host_async(self._h, field,
+                                                 ctypes.c_void_p(pinned.data_ptr())))
+        return pinned
+
     # ---------------------------------------------------------------- stepping
     def step(self, n_steps: int = 1):
         check(self._lib.pf_step(self._h, int(n_steps)))

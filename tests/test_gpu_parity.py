@@ -510,3 +510,31 @@ def test_cluster_kernel_rules_and_autotune(pf):
 def set_cluster_tuning_strict(g):
     ny, nx = g.shape
     g.set_tuning(nx, ny // 16, 1)
+
+
+def test_async_host_copies_pipeline_jobs_on_two_grids(pf):
+    # the pattern of a caller that overlaps copies with steps: jobs alternate between two
+    # grids on two streams, each job uploading, stepping and downloading without waiting;
+    # every job's result equals the synchronous path's bit for bit
+    import torch
+    shape = (6, 32, 128)
+    x0 = init_fields("gs", shape, seed=50)
+    ref = gpu_run(pf, "gs", x0, 10)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    grids = [pf.Grid(shape, 2, stream=s).set_model("gs", COEFFS["gs"], DT["gs"]) for s in streams]
+    ins = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in x0]
+    outs = [[torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+            for _ in range(4)]
+    for j in range(4):
+        g = grids[j % 2]
+        for f in range(2):
+            g.write_field_async(f, ins[f])
+        g.step(10)
+        for f in range(2):
+            g.read_field_async(f, outs[j][f])
+    for g in grids:
+        g.synchronize()
+        g.close()
+    for o in outs:
+        for f in range(2):
+            assert np.array_equal(o[f].numpy(), ref[f])
