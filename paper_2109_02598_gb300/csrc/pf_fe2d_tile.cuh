@@ -152,6 +152,132 @@ __device__ __forceinline__ void site4_update(const float* src, const float* mu, 
   }
 }
 
+// ---- row strips (standard 5-point stencil) ----------------------------------------
+// A thread walks a vertical strip of one column group and keeps the rows above, at and below
+// the current site in registers: one float4 row load per site group and Laplacian instead of
+// three. The per-site arithmetic is that of lap2d_x4, site4_mu and site4_update, bit for bit.
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Strips are taken once each holds at least this many rows (ceil(nrows / S) >= 3, i.e.
+// nrows > 2 S): shorter ones lengthen a thread's dependent chain more than they save loads
+// (measured: 64x16 tiles at k = 4 with 2-row strips, 10 % slower; 128x16 tiles at k = 4 with
+// 3-4-row strips, 1-2 % faster).
+constexpr int kMinStripRows = 3;
+
+// Laplacians of a float4 group from its row (c), the rows above (u) and below (d) and its two
+// x-edge scalars: lap2d_x4<PF_ST_STD>'s arithmetic.
+__device__ __forceinline__ float4 lap4_rows(const float4& c, const float4& u, const float4& d,
+                                            float l, float r, float scale) {
+  float4 o;
+  o.x = lap2d(c.x, l, c.y, u.x, d.x, scale);
+  o.y = lap2d(c.y, c.x, c.z, u.y, d.y, scale);
+  o.z = lap2d(c.z, c.y, c.w, u.z, d.z, scale);
+  o.w = lap2d(c.w, c.z, r, u.w, d.w, scale);
+  return o;
+}
+
+// Thread t's strip of a region of nrows rows from rlo and ncols column groups from clo:
+// column group clo + t % ncols, rows [r0, r1) of strip t / ncols (S = kNT2 / ncols strips of
+// ceil(nrows / S) rows; threads beyond S ncols get none).
+struct Strip {
+  int j, r0, r1;
+};
+
+__device__ __forceinline__ Strip strip_of(int rlo, int nrows, int clo, int ncols) {
+  Strip st;
+  const int S = kNT2 / ncols;
+  const int q = threadIdx.x / ncols;
+  st.j = clo + (threadIdx.x - q * ncols);
+  if (q >= S) {
+    st.r0 = st.r1 = 0;
+    return st;
+  }
+  const int L = (nrows + S - 1) / S;
+  st.r0 = rlo + q * L;
+  st.r1 = min(rlo + nrows, st.r0 + L);
+  return st;
+}
+
+// site4_mu down a strip.
+template <int MODEL>
+__device__ __forceinline__ void mu_strip(const float* src, int ws, int pl, const Strip& st,
+                                         const ModelParams& m, float* mu) {
+  if (st.r0 >= st.r1) return;
+  const float* A = MODEL == PF_MODEL_CH ? src : src + pl;  // the field under the Laplacian
+  int p = st.r0 * ws + 4 * st.j;
+  float4 u = ld4(A + p - ws), c = ld4(A + p);
+  for (int r = st.r0; r < st.r1; ++r, p += ws) {
+    const float4 d = ld4(A + p + ws);
+    const float4 l = lap4_rows(c, u, d, A[p - 1], A[p + 4], m.lap_scale);
+    if constexpr (MODEL == PF_MODEL_CH) {
+      *reinterpret_cast<float4*>(mu + p) = make_float4(ch_mu(c.x, l.x, m), ch_mu(c.y, l.y, m),
+                                                       ch_mu(c.z, l.z, m), ch_mu(c.w, l.w, m));
+    } else {
+      const float4 ps = ld4(src + p);
+      *reinterpret_cast<float4*>(mu + p) =
+          make_float4(mc_mu(ps.x, c.x, l.x, m), mc_mu(ps.y, c.y, l.y, m),
+                      mc_mu(ps.z, c.z, l.z, m), mc_mu(ps.w, c.w, l.w, m));
+    }
+    u = c;
+    c = d;
+  }
+}
+
+// site4_update down a strip; emit(r, j, p, val) stores each group's new values.
+template <int MODEL, class Emit>
+__device__ __forceinline__ void update_strip(const float* src, const float* mu, int ws, int pl,
+                                             const Strip& st, const ModelParams& m, Emit&& emit) {
+  if (st.r0 >= st.r1) return;
+  constexpr int NF = ModelTraits<MODEL>::NF;
+  constexpr bool TWO = MODEL == PF_MODEL_GS || MODEL == PF_MODEL_C;  // two Laplacians
+  const float* A0 = MODEL == PF_MODEL_CH ? mu : src;        // AC, GS: phi / u; C: psi
+  const float* A1 = MODEL == PF_MODEL_GS ? src + pl : mu;   // GS: v; C: mu
+  int p = st.r0 * ws + 4 * st.j;
+  float4 u0 = ld4(A0 + p - ws), c0 = ld4(A0 + p);
+  float4 u1 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = u1;
+  if constexpr (TWO) {
+    u1 = ld4(A1 + p - ws);
+    c1 = ld4(A1 + p);
+  }
+  for (int r = st.r0; r < st.r1; ++r, p += ws) {
+    const float4 d0 = ld4(A0 + p + ws);
+    const float4 l0 = lap4_rows(c0, u0, d0, A0[p - 1], A0[p + 4], m.lap_scale);
+    float4 d1 = d0, l1 = l0;
+    if constexpr (TWO) {
+      d1 = ld4(A1 + p + ws);
+      l1 = lap4_rows(c1, u1, d1, A1[p - 1], A1[p + 4], m.lap_scale);
+    }
+    float4 val[NF];
+    if constexpr (MODEL == PF_MODEL_AC) {
+      val[0] = make_float4(ac_update(c0.x, l0.x, m), ac_update(c0.y, l0.y, m),
+                           ac_update(c0.z, l0.z, m), ac_update(c0.w, l0.w, m));
+    } else if constexpr (MODEL == PF_MODEL_CH) {
+      const float4 c = ld4(src + p);
+      val[0] = make_float4(ch_update(c.x, l0.x, m), ch_update(c.y, l0.y, m),
+                           ch_update(c.z, l0.z, m), ch_update(c.w, l0.w, m));
+    } else if constexpr (MODEL == PF_MODEL_C) {
+      const float4 cm = ld4(src + pl + p);
+      mc_update(c0.x, cm.x, l0.x, l1.x, m, val[0].x, val[1].x);
+      mc_update(c0.y, cm.y, l0.y, l1.y, m, val[0].y, val[1].y);
+      mc_update(c0.z, cm.z, l0.z, l1.z, m, val[0].z, val[1].z);
+      mc_update(c0.w, cm.w, l0.w, l1.w, m, val[0].w, val[1].w);
+    } else {
+      gs_update(c0.x, c1.x, l0.x, l1.x, m, val[0].x, val[1].x);
+      gs_update(c0.y, c1.y, l0.y, l1.y, m, val[0].y, val[1].y);
+      gs_update(c0.z, c1.z, l0.z, l1.z, m, val[0].z, val[1].z);
+      gs_update(c0.w, c1.w, l0.w, l1.w, m, val[0].w, val[1].w);
+    }
+    emit(r, st.j, p, val);
+    u0 = c0;
+    c0 = d0;
+    if constexpr (TWO) {
+      u1 = c1;
+      c1 = d1;
+    }
+  }
+}
+
 // k forward-Euler sub-steps of one tile; the last one is written to `out` (sites beyond
 // nx, ny are computed on periodic images and not stored).
 template <int MODEL, int K, int TX, int TY, int ST = PF_ST_STD>
@@ -161,6 +287,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
   using C = Cfg2<MODEL, K, TX, TY, ST>;
   constexpr int WS = C::WS;
   constexpr int PL = C::PL;
+  static_assert(WS / 4 <= kNT2, "a row's column groups must fit the CTA (row strips)");
   load_region2d<C>(in, nx, ny, pitch, x0, y0, sm);
   __syncthreads();
 #pragma unroll
@@ -175,10 +302,14 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
       const int chi = (WS - (C::HP - C::H + C::R * s + C::RS) + 3) / 4;
       const int nch = chi - clo;
       auto mu_rows = [&](const int nrows, const int ncols) {
-        for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
-          const int rr = i / ncols;
-          const int p = (rlo + rr) * WS + 4 * (clo + i - rr * ncols);
-          site4_mu<MODEL, ST>(src, p, WS, PL, m, mu);
+        if (ST == PF_ST_STD && nrows > (kMinStripRows - 1) * (kNT2 / ncols)) {
+          mu_strip<MODEL>(src, WS, PL, strip_of(rlo, nrows, clo, ncols), m, mu);
+        } else {
+          for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
+            const int rr = i / ncols;
+            const int p = (rlo + rr) * WS + 4 * (clo + i - rr * ncols);
+            site4_mu<MODEL, ST>(src, p, WS, PL, m, mu);
+          }
         }
       };
       // mu is needed R (K-1-s) + RS past the grid's last row and column, no further
@@ -200,14 +331,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
     const int marg = C::R * (K - 1 - s);
     const int rhi_e = min(rhi, C::H + (ny - y0) + marg);
     const int chi_e = min(chi, (C::HP + (nx - x0) + marg + 3) / 4);
-    auto update_rows = [&](const int nrows, const int ncols) {
-    for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
-      const int rr = i / ncols;
-      const int r = rlo + rr;
-      const int j = clo + i - rr * ncols;
-      const int p = r * WS + 4 * j;
-      float4 val[C::NF];
-      site4_update<MODEL, ST>(src, mu, p, WS, PL, m, val);
+    auto emit = [&](const int r, const int j, const int p, const float4* val) {
       if (last) {
         const int gx = x0 + 4 * j - C::HP;
         const int gy = y0 + r - C::H;
@@ -229,7 +353,20 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
 #pragma unroll
         for (int f = 0; f < C::NF; ++f) *reinterpret_cast<float4*>(dst + f * PL + p) = val[f];
       }
-    }
+    };
+    auto update_rows = [&](const int nrows, const int ncols) {
+      if (ST == PF_ST_STD && nrows > (kMinStripRows - 1) * (kNT2 / ncols)) {
+        update_strip<MODEL>(src, mu, WS, PL, strip_of(rlo, nrows, clo, ncols), m, emit);
+      } else {
+        for (int i = threadIdx.x; i < nrows * ncols; i += kNT2) {
+          const int rr = i / ncols;
+          const int j = clo + i - rr * ncols;
+          const int p = (rlo + rr) * WS + 4 * j;
+          float4 val[C::NF];
+          site4_update<MODEL, ST>(src, mu, p, WS, PL, m, val);
+          emit(rlo + rr, j, p, val);
+        }
+      }
     };
     if (rhi_e == rhi && chi_e == chi) update_rows(rhi - rlo, nch);  // compile-time bounds
     else if (rhi_e > rlo && chi_e > clo) update_rows(rhi_e - rlo, chi_e - clo);
