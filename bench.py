@@ -335,7 +335,7 @@ def _time(stream, fn, reps=1):
 def companions(stream, hbm):
     """The other workloads, each timed on the device: the 512-instance batched Gray-Scott
     run against a plain 2D grid, the adjoint against the plain forward run at the same
-    size, and the Cahn-Hilliard 2048^2 and Allen-Cahn 128^2 steps."""
+    size, and the Cahn-Hilliard 2048^2 and 8192^2 and Allen-Cahn 128^2 steps."""
     import torch
     import paper_2109_02598_gb300 as pf
     out = {}
@@ -356,18 +356,24 @@ def companions(stream, hbm):
         g.close()
         # ---- adjoint 512^2, 2000 steps, sqrt(N) checkpoints vs the plain forward run
         out["adjoint_gs2d_512"] = adjoint_timing(stream, 512, 2000)
-        # ---- Cahn-Hilliard 2048^2 (L2-resident) and Allen-Cahn 128^2
-        for name, steps in (("ch2d_2048", 2000), ("ac2d_128", 1000)):
-            w = synthetic.WORKLOADS[name]
-            x0 = synthetic.workload_init(name)
-            g = pf.Grid(w["shape"], 1, stream=stream).set_model(w["model"], w["coeffs"], w["dt"])
+        # ---- Cahn-Hilliard 2048^2 (L2-resident), the same recipe on 8192^2 (268 MB per
+        # field, out of L2) and Allen-Cahn 128^2
+        for name, wname, shape, steps in (("ch2d_2048", "ch2d_2048", None, 2000),
+                                          ("ch2d_8192", "ch2d_2048", (8192, 8192), 500),
+                                          ("ac2d_128", "ac2d_128", None, 1000)):
+            w = synthetic.WORKLOADS[wname]
+            shape = shape or w["shape"]
+            x0 = synthetic.workload_init(wname, shape)
+            g = pf.Grid(shape, 1, stream=stream).set_model(w["model"], w["coeffs"], w["dt"])
             g.write_fields(x0)
             t = g.autotune(5)
             g.step(steps)  # records the graph of this run length
             ms = _time(stream, lambda: g.step(steps))
-            sites = int(np.prod(w["shape"]))
-            out[name] = {"steps": steps, "glups": sites * steps / (ms * 1e-3) / 1e9,
-                         "tuning": list(t)}
+            sites = int(np.prod(shape))
+            glups = sites * steps / (ms * 1e-3) / 1e9
+            out[name] = {"steps": steps, "glups": glups, "tuning": list(t)}
+            if w["model"] == "ch":
+                out[name]["hbm_frac_k1_bytes"] = glups * 8.0 / hbm
             g.close()
         # ---- the paper's performance table (Sec. 3.1) with the forward-Euler solver:
         # 10^4 steps of Models A and C; device time and end to end (host in/out)

@@ -172,7 +172,18 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * of 16, else 8; k in {1, 2, 4, 8} for AC and GS, {1, 2} for CH and C, with k R <= ny / CS):
  * one thread-block cluster holds the whole grid, exchanges k-row halos between its CTAs
  * through distributed shared memory, and runs all steps of a pf_step call in one launch.
+ * 2D tile nx x PF_TILE_BANDS selects the band kernel (Allen-Cahn and Cahn-Hilliard, the
+ * standard stencil, k = 1, nx % 4 == 0 with 64 <= nx <= 4096, and a band of ceil(ny / P)
+ * full rows plus halos in each SM's shared memory, P = min(SMs, ny / (2R)) >= 2 CTAs, R = 1
+ * for Allen-Cahn and 2 for Cahn-Hilliard; Cahn-Hilliard 2048^2 takes 14 rows per SM): the
+ * grid stays in the shared memory of all SMs for a whole pf_step call (one cooperative
+ * launch), and neighbouring bands exchange their edge rows through global memory every step
+ * (as 64-bit words tagged with their step, so no flag or fence is needed).
+ * It needs all P CTAs resident at once: if the device cannot host them (other work, a
+ * restricted context), pf_step fails with PF_ERR_CUDA. Its exchange buffers (4 R nx 8-byte
+ * words per CTA) are allocated at its first launch.
  * Results are bitwise identical to the tiled kernels. */
+#define PF_TILE_BANDS (-1) /* tile_y of the band kernel (with tile_x = nx) */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
 
 /* The tuning in effect (after defaults are resolved). */
@@ -180,7 +191,8 @@ int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps);
 
 /* Time every supported (tile, k) for this grid and model (CUDA events), keep the fastest
  * and report it: tiled kernels as a replayed CUDA graph of max(probe_launches, 8) launches
- * (as pf_step runs them), the cluster kernel as one launch of 16 k probe_launches steps.
+ * (as pf_step runs them), the cluster and band kernels as one launch of 16 k probe_launches
+ * steps.
  * The state is not changed: probe launches read the current buffer and write the spare one.
  * Errors: PF_ERR_STATE (no model), PF_ERR_CUDA. */
 int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps);
@@ -372,10 +384,12 @@ int pf_porod_fit(int n_bins, const double* centres, const double* mean, const in
 
 /* ------------------------------------------------------------------- self-test */
 
-/* Self-test of the bounded waits inside the TMA kernels: launches one CTA that waits on an
- * mbarrier phase nothing completes, with a budget of budget_cycles SM clocks (in [1, 4e9]);
- * the wait gives up, the kernel records it and the call returns PF_ERR_TIMEOUT, which is the
- * expected result. Any other status means the path is broken. The GPU stays usable. */
+/* Self-test of the bounded waits inside the kernels: launches one CTA that waits on an
+ * mbarrier phase nothing completes (the TMA kernels' wait), then on tagged words nothing
+ * writes (the band kernel's wait for its neighbours' edge rows), each with a budget of
+ * budget_cycles SM clocks (in [1, 4e9]); both waits give up, the kernel records it and the
+ * call returns PF_ERR_TIMEOUT, which is the expected result. Any other status means a path
+ * is broken. The GPU stays usable. */
 int pf_selftest_wait_timeout(int64_t budget_cycles, void* stream);
 
 /* ------------------------------------------------------- reduction without allocation */

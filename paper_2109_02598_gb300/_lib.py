@@ -22,6 +22,8 @@ PF_ERR_NONFINITE = -5
 PF_ERR_STATE = -6
 PF_ERR_TIMEOUT = -7
 
+PF_TILE_BANDS = -1  # tile_y of the band kernel (with tile_x = nx)
+
 PF_MODEL_AC = 1
 PF_MODEL_CH = 2
 PF_MODEL_GS = 3

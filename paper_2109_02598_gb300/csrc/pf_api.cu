@@ -145,8 +145,9 @@ int resolve_tuning(pf_grid_s* g) {
     const int def = g->stencil == PF_ST_STD ? 1 : 0;  // 128 x 16; other stencils 64 x 16
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
     g->k = g->req_k > 0 ? g->req_k : 1;
-    if (g->tile != kTileCluster2D && g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
-    if (g->tile == kTileCluster2D) {
+    const bool on_chip = g->tile == kTileCluster2D || g->tile == kTileBands2D;
+    if (!on_chip && g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
+    if (on_chip) {
       if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
         g->tile = def;
         g->k = 1;
@@ -180,6 +181,8 @@ int resolve_tuning(pf_grid_s* g) {
 bool tile_supported(pf_grid_s* g, int tile, int k) {
   if (g->dim == 2 && tile == kTileCluster2D)
     return g->stencil == PF_ST_STD && fe2d_cluster_supported(g->model, k, grid_geom(g));
+  if (g->dim == 2 && tile == kTileBands2D)
+    return g->stencil == PF_ST_STD && k == 1 && fe2d_bands_supported(g->model, grid_geom(g));
   if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
   if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
   int tx, ty;
@@ -208,7 +211,8 @@ int check_device_error(pf_grid_s* g) {
   PF_CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (flag != 0) {
     PF_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
-    set_error("a kernel's bounded wait for a TMA copy ran out; the state is invalid");
+    set_error("a kernel's bounded wait (for a TMA copy or a neighbouring band) ran out; the "
+              "state is invalid");
     return PF_ERR_TIMEOUT;
   }
   return PF_OK;
@@ -227,6 +231,7 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
   const Geom q = grid_geom(g);
   if (g->dim == 2 && tile == kTileCluster2D)
     return launch_fe2d_cluster(g->model, k, q, in, out, g->params, k, st);
+  if (g->dim == 2 && tile == kTileBands2D) return launch_fe2d_bands(g, src, dst, k, st);
   if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
   if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
   if (k == 2) {
@@ -369,6 +374,7 @@ void pf_destroy(pf_grid_t g) {
   if (g == nullptr || g->magic != kGridMagic) return;
   cudaStreamSynchronize(g->stream);
   pf::adjoint_release(g);
+  pf::fe2d_bands_release(g);
   drop_graphs(g);
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->base) cudaFree(g->base);
@@ -474,6 +480,12 @@ int pf_step(pf_grid_t g, int64_t n_steps) {
     g->cur = 1 - g->cur;
     return PF_OK;
   }
+  if (g->dim == 2 && g->tile == kTileBands2D) {
+    // the whole run in one cooperative launch of the band kernel
+    PF_CUDA_TRY(launch_fe2d_bands(g, g->cur, 1 - g->cur, n_steps, g->stream));
+    g->cur = 1 - g->cur;
+    return PF_OK;
+  }
   if (count_launches(n_steps, g->k) >= kGraphMinLaunches) {
     // replay a recorded graph of the whole launch sequence (one host call)
     pf_grid_s::StepGraph* hit = nullptr;
@@ -576,7 +588,15 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     tile = -1;
   } else if (g->dim == 2) {
     const int cs = fe2d_cluster_size();
-    if (tile_x == g->nx && g->ny % cs == 0 && tile_y == g->ny / cs) {
+    if (tile_x == g->nx && tile_y == PF_TILE_BANDS) {
+      tile = kTileBands2D;  // the band kernel: one band of full rows per SM
+      if (g->stencil != PF_ST_STD || (k_steps != 0 && k_steps != 1) ||
+          !(g->model_set && fe2d_bands_supported(g->model, grid_geom(g))))
+        return invalid("the band kernel (tile %d x PF_TILE_BANDS) needs an Allen-Cahn or "
+                       "Cahn-Hilliard model, the standard stencil, k = 1, nx %% 4 == 0 with "
+                       "64 <= nx <= 4096, and a band of the grid in each SM's shared memory",
+                       tile_x);
+    } else if (tile_x == g->nx && g->ny % cs == 0 && tile_y == g->ny / cs) {
       tile = kTileCluster2D;  // the on-chip cluster kernel: full rows, ny / CS rows per CTA
       const int kk = k_steps > 0 ? k_steps : 1;
       if (g->stencil != PF_ST_STD ||
@@ -600,12 +620,12 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (!(g->model_set && fe3d_tb2_supported(g->model, tx, ty, grid_geom(g))))
       return invalid("3D k = 2 needs an AC/GS model, tile nx x 8 with nx = 128 or 256, ny %% 8 == 0");
   }
-  if (k_steps > 0 && g->dim == 2 && tile != kTileCluster2D) {
+  if (k_steps > 0 && g->dim == 2 && tile != kTileCluster2D && tile != kTileBands2D) {
     const int model = g->model_set ? g->model : PF_MODEL_AC;
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
   }
-  if (g->stencil != PF_ST_STD && tile != kTileCluster2D) {
+  if (g->stencil != PF_ST_STD && tile != kTileCluster2D && tile != kTileBands2D) {
     const int t = tile >= 0 ? tile : 0;
     const int kk = k_steps > 0 ? k_steps : 1;
     const bool ok = g->dim == 2 ? fe2d_stencil_supported(g->stencil, t, kk)
@@ -630,6 +650,9 @@ int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps) {
   if (g->dim == 2 && g->tile == kTileCluster2D) {
     tx = g->nx;
     ty = g->ny / fe2d_cluster_size();
+  } else if (g->dim == 2 && g->tile == kTileBands2D) {
+    tx = g->nx;
+    ty = PF_TILE_BANDS;
   } else if (g->dim == 2) {
     tile2d_shape(g->tile, &tx, &ty);
   } else {
@@ -653,15 +676,16 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   PF_CUDA_TRY(cudaEventCreate(&e1));
   float best = INFINITY;
   int best_tile = g->tile, best_k = g->k;
-  const int ntiles = g->dim == 2 ? kNumTiles2D + 1 : kNumTiles3D;  // 2D: + the cluster kernel
+  // 2D: + the cluster kernel and the band kernel
+  const int ntiles = g->dim == 2 ? kNumTiles2D + 2 : kNumTiles3D;
   static const int ks[4] = {1, 2, 4, 8};  // 8: the cluster kernel only
   int rc = PF_OK;
   for (int t = 0; t < ntiles && rc == PF_OK; ++t) {
     for (int ki = 0; ki < 4 && rc == PF_OK; ++ki) {
       const int k = ks[ki];
       if (!tile_supported(g, t, k)) continue;
-      // the cluster kernel runs a whole pf_step in one launch: probe it that way
-      const bool cluster = g->dim == 2 && t == kTileCluster2D;
+      // the cluster and band kernels run a whole pf_step in one launch: probe them that way
+      const bool cluster = g->dim == 2 && (t == kTileCluster2D || t == kTileBands2D);
       const int64_t probe_steps = cluster ? (int64_t)probe_launches * k * 16 : 0;
       // Every probe reads buffer cur and writes 1 - cur, so the state is left as it was.
       // Tiled candidates run as a replayed graph of n_l launches, as pf_step runs them.
@@ -685,7 +709,9 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
         if (e == cudaSuccess) e = cudaGraphLaunch(probe, g->stream);  // warm-up replay
       }
       if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
-      if (cluster && e == cudaSuccess) {
+      if (cluster && t == kTileBands2D && e == cudaSuccess) {
+        e = launch_fe2d_bands(g, g->cur, 1 - g->cur, probe_steps, g->stream);
+      } else if (cluster && e == cudaSuccess) {
         FieldPtrs in{};
         FieldOut out{};
         for (int f = 0; f < g->nf; ++f) {

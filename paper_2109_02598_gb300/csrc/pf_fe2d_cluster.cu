@@ -59,16 +59,6 @@ size_t cluster_smem_floats(const ClGeom& g) {
   return (size_t)2 * C::NF * g.pl + (C::MU ? g.pl : 0) + (size_t)4 * C::NF * C::H * g.nx;
 }
 
-// Store the float4 at staged column 4j + HP of a row, and its periodic copy when the column
-// lies within HP of either row end.
-template <int HP>
-__device__ __forceinline__ void put_row4(float* row, int j, int nx, float4 v) {
-  const int c = 4 * j;
-  *reinterpret_cast<float4*>(row + HP + c) = v;
-  if (c < HP) *reinterpret_cast<float4*>(row + HP + nx + c) = v;
-  if (c >= nx - HP) *reinterpret_cast<float4*>(row + c - (nx - HP)) = v;
-}
-
 template <int MODEL, int K>
 __global__ void __launch_bounds__(kNTC, 1)
     fe2d_cluster_kernel(FieldPtrs in, FieldOut out, ClGeom g, ModelParams m, int64_t n_steps) {

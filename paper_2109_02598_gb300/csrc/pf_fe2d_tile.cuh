@@ -278,6 +278,20 @@ __device__ __forceinline__ void update_strip(const float* src, const float* mu, 
   }
 }
 
+// ---- full rows with periodic halo columns (the on-chip kernels) ---------------------
+// A staged full row holds nx values from column HP on, with HP halo columns per side that
+// are periodic copies of the row's other end.
+
+// Store the float4 at staged column 4j + HP of a row, and its periodic copy when the column
+// lies within HP of either row end.
+template <int HP>
+__device__ __forceinline__ void put_row4(float* row, int j, int nx, float4 v) {
+  const int c = 4 * j;
+  *reinterpret_cast<float4*>(row + HP + c) = v;
+  if (c < HP) *reinterpret_cast<float4*>(row + HP + nx + c) = v;
+  if (c >= nx - HP) *reinterpret_cast<float4*>(row + c - (nx - HP)) = v;
+}
+
 // k forward-Euler sub-steps of one tile; the last one is written to `out` (sites beyond
 // nx, ny are computed on periodic images and not stored).
 template <int MODEL, int K, int TX, int TY, int ST = PF_ST_STD>

@@ -84,6 +84,11 @@ struct pf_grid_s {
   pf::TmaCache tma;
   pf::Tb2Cache tb2;
   int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
+  // band kernel (2D grid resident in the SMs' shared memory): exchange slots of the bands'
+  // edge rows as tagged 64-bit words, allocated at its first launch, and the last tag used
+  unsigned long long* band_x = nullptr;
+  size_t band_x_words = 0;
+  unsigned int band_tag = 0;
   // CUDA-graph cache of pf_step: a few recorded launch sequences, keyed by
   // (steps, tile, k, starting buffer), least recently used replaced first
   cudaStream_t capture = nullptr;  // private stream used only to record graphs
@@ -115,6 +120,11 @@ void tma3d_tile_shape(int tma_tile, int* tx, int* ty);
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g);
 cudaError_t tma3d_maps(pf_grid_s* g, int tma_tile, int buf);
 cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst, cudaStream_t st);
+
+// ---- 2D band kernel (AC, CH; k = 1): one band of full rows per SM, all steps in one
+// cooperative launch (pf_fe2d_bands.cu)
+cudaError_t launch_fe2d_bands(pf_grid_s* g, int src, int dst, int64_t n_steps, cudaStream_t st);
+void fe2d_bands_release(pf_grid_s* g);
 
 // ---- 3D depth-2 kernel (AC, GS; full x-rows of 128 or 256, 8-row tiles)
 bool fe3d_tb2_supported(int model, int tx, int ty, const Geom& g);

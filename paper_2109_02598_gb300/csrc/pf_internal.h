@@ -78,6 +78,12 @@ bool fe2d_cluster_supported(int model, int k, const Geom& q);
 cudaError_t launch_fe2d_cluster(int model, int k, const Geom& q, FieldPtrs in, FieldOut out,
                                 const ModelParams& m, int64_t n_steps, cudaStream_t st);
 
+// ---- 2D grids held in the shared memory of all SMs (pf_fe2d_bands.cu) ---------------
+// Tile id kTileBands2D (tile_y = PF_TILE_BANDS): one band of full rows per SM, neighbouring
+// bands exchange edge rows through global memory every step; AC and CH, k = 1.
+constexpr int kTileBands2D = kNumTiles2D + 1;
+bool fe2d_bands_supported(int model, const Geom& q);
+
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
 //           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);

@@ -185,6 +185,8 @@ class Grid:
 
     # ---------------------------------------------------------------- tuning
     def set_tuning(self, tile_x: int = 0, tile_y: int = 0, k: int = 0):
+        """Tile and temporal-blocking depth (0 = default). (nx, ny / CS) selects the on-chip
+        cluster kernel, (nx, PF_TILE_BANDS) the band kernel (one band of rows per SM)."""
         check(self._lib.pf_set_tuning(self._h, tile_x, tile_y, k))
         return self
 

@@ -512,6 +512,83 @@ def set_cluster_tuning_strict(g):
     g.set_tuning(nx, ny // 16, 1)
 
 
+@pytest.mark.parametrize("model,shape", [
+    ("ch", (256, 512)),   # 64 bands of exactly 2R = 4 rows: edge rows only
+    ("ch", (333, 388)),   # 83 bands of 4-5 rows; 97 threads (a partial warp)
+    ("ch", (1000, 1024)), # one band per SM, 6-7 rows
+    ("ac", (304, 128)),   # bands of 2 rows
+    ("ac", (77, 388)),    # 38 bands of 2-3 rows
+    ("ac", (1000, 512)),
+    ("ch", (608, 2560)),  # four columns per thread (nx > 2048), bands of 4 rows
+    ("ac", (304, 4096))])
+def test_band_kernel_bitwise_and_oracle(pf, model, shape):
+    # the grid held in the SMs' shared memory, bands exchanging edge rows every step:
+    # 1 and 37 steps give the tiled kernel's bits; 37 steps also meet the oracle
+    x0 = init_fields(model, shape, seed=60)
+    for n in (1, 37):
+        g = pf.Grid(shape, 1).set_model(model, COEFFS[model], DT[model], force=True)
+        g.set_tuning(shape[1], pf.PF_TILE_BANDS, 1)
+        assert g.tuning == (shape[1], pf.PF_TILE_BANDS, 1)
+        g.write_fields(x0)
+        g.step(n)
+        a = g.read_fields()
+        g.close()
+        b = gpu_run(pf, model, x0, n, tuning=(64, 16, 1))
+        for p, q in zip(a, b):
+            assert np.array_equal(p, q)
+    ref = oracle.run(model, x0, COEFFS[model], DT[model], 37)
+    assert rel_linf(a, ref) <= 1e-5
+
+
+def test_band_kernel_model_b_2048_and_repeated_calls(pf):
+    # the Model B configuration's grid: one step against the oracle; three calls of 5 steps
+    # equal one call of 15 (step counters restart with every launch) and the tiled kernel
+    shape = (2048, 2048)
+    x0 = (synthetic.cahn_hilliard_init(shape, seed=2),)
+    g = pf.Grid(shape, 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    g.set_tuning(2048, pf.PF_TILE_BANDS, 1)
+    g.write_fields(x0)
+    g.step(1)
+    one = g.read_fields()
+    ref = oracle.euler_step("ch", x0, COEFFS["ch"], DT["ch"])
+    assert rel_linf(one, ref) <= 1e-6
+    g.write_fields(x0)
+    for _ in range(3):
+        g.step(5)
+    a = g.read_fields()
+    g.write_fields(x0)
+    g.step(15)
+    b = g.read_fields()
+    g.close()
+    c = gpu_run(pf, "ch", x0, 15, tuning=(128, 16, 2))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[0], c[0])
+
+
+def test_band_kernel_rules_and_autotune(pf):
+    from paper_2109_02598_gb300 import PfError
+    g = pf.Grid((512, 512), 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    with pytest.raises(PfError, match="band kernel"):
+        g.set_tuning(512, pf.PF_TILE_BANDS, 2)  # k = 1 only
+    g.set_stencil("iso")
+    with pytest.raises(PfError, match="band kernel"):
+        g.set_tuning(512, pf.PF_TILE_BANDS, 1)
+    g.close()
+    for model, shape in (("gs", (512, 512)), ("ac", (512, 60)), ("ac", (3, 512))):
+        h = pf.Grid(shape, 2 if model == "gs" else 1).set_model(model, COEFFS[model], DT[model])
+        with pytest.raises(PfError, match="band kernel"):
+            h.set_tuning(shape[1], pf.PF_TILE_BANDS, 1)
+        h.close()
+    g = pf.Grid((1024, 1024), 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    x0 = (synthetic.cahn_hilliard_init((1024, 1024), seed=61),)
+    g.write_fields(x0)
+    t = g.autotune(3)  # the band kernel is a candidate; the state is left as it was
+    g.step(7)
+    a = g.read_fields()
+    g.close()
+    assert len(t) == 3
+    assert np.array_equal(a[0], gpu_run(pf, "ch", x0, 7)[0])
+
+
 def test_async_host_copies_pipeline_jobs_on_two_grids(pf):
     # the pattern of a caller that overlaps copies with steps: jobs alternate between two
     # grids on two streams, each job uploading, stepping and downloading without waiting;
