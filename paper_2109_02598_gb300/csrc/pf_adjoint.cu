@@ -510,7 +510,10 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
   if (dtheta != nullptr) {
     const double* S = a.ghost;
     if (g->model == PF_MODEL_GS) {
-      for (int i = 0; i < 4; ++i) dtheta[i] = a.dt * S[i];
+      // the kernel's Laplacians of u and v are unscaled (the parameters carry 1/h^2 in
+      // D_u and D_v), so the sums for D_u and D_v take the factor here
+      const double s = 1.0 / (g->h * g->h);
+      for (int i = 0; i < 4; ++i) dtheta[i] = a.dt * S[i] * (i < 2 ? s : 1.0);
     } else if (g->model == PF_MODEL_AC) {
       dtheta[0] = a.dt * S[0];
       dtheta[1] = -a.dt * S[1];

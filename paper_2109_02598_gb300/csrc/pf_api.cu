@@ -108,10 +108,13 @@ ModelParams make_params(int model, const double* c, double dt, double h, int ste
       m.a2 = (float)(dt * c[2]);
       break;
     case PF_MODEL_GS:
-      m.a0 = (float)c[0];
-      m.a1 = (float)c[1];
+      // the stencil factor goes into the diffusion coefficients (the only terms with a
+      // Laplacian), so Gray-Scott kernels may skip the multiply by lap_scale = 1
+      m.a0 = (float)(c[0] * (double)m.lap_scale);
+      m.a1 = (float)(c[1] * (double)m.lap_scale);
       m.a2 = (float)c[2];
       m.a3 = (float)(c[2] + c[3]);
+      m.lap_scale = 1.0f;
       break;
     case PF_MODEL_C:
       m.a0 = (float)c[0];

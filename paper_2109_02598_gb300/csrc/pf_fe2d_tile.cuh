@@ -64,8 +64,9 @@ __device__ __forceinline__ void load_region2d(const FieldPtrs& in, int nx, int n
 }
 
 // 2D Laplacians of four consecutive sites from a float4 row and its neighbours, with the
-// stencil ST (its neighbours beyond the float4 come from scalars of the same rows).
-template <int ST = PF_ST_STD>
+// stencil ST (its neighbours beyond the float4 come from scalars of the same rows). MODEL
+// only matters for Gray-Scott with the standard stencil, whose factor is 1 (lap_scaled).
+template <int ST = PF_ST_STD, int MODEL = PF_MODEL_AC>
 __device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float scale) {
   const float4 c = *reinterpret_cast<const float4*>(s + p);
   const float4 u = *reinterpret_cast<const float4*>(s + p - ws);
@@ -73,10 +74,10 @@ __device__ __forceinline__ float4 lap2d_x4(const float* s, int p, int ws, float 
   const float l = s[p - 1], r = s[p + 4];
   float4 o;
   if constexpr (ST == PF_ST_STD) {
-    o.x = lap2d(c.x, l, c.y, u.x, d.x, scale);
-    o.y = lap2d(c.y, c.x, c.z, u.y, d.y, scale);
-    o.z = lap2d(c.z, c.y, c.w, u.z, d.z, scale);
-    o.w = lap2d(c.w, c.z, r, u.w, d.w, scale);
+    o.x = lap_scaled<MODEL>(lap2d_sum(c.x, l, c.y, u.x, d.x), scale);
+    o.y = lap_scaled<MODEL>(lap2d_sum(c.y, c.x, c.z, u.y, d.y), scale);
+    o.z = lap_scaled<MODEL>(lap2d_sum(c.z, c.y, c.w, u.z, d.z), scale);
+    o.w = lap_scaled<MODEL>(lap2d_sum(c.w, c.z, r, u.w, d.w), scale);
   } else if constexpr (ST == PF_ST_ISO) {
     const float ul = s[p - ws - 1], ur = s[p - ws + 4], dl = s[p + ws - 1], dr = s[p + ws + 4];
     o.x = lap2d_iso(c.x, l, c.y, u.x, d.x, ul, u.y, dl, d.y, scale);
@@ -143,8 +144,8 @@ __device__ __forceinline__ void site4_update(const float* src, const float* mu, 
   } else {
     const float4 u = *reinterpret_cast<const float4*>(src + p);
     const float4 v = *reinterpret_cast<const float4*>(src + pl + p);
-    const float4 lu = lap2d_x4<ST>(src, p, ws, m.lap_scale);
-    const float4 lv = lap2d_x4<ST>(src + pl, p, ws, m.lap_scale);
+    const float4 lu = lap2d_x4<ST, MODEL>(src, p, ws, m.lap_scale);
+    const float4 lv = lap2d_x4<ST, MODEL>(src + pl, p, ws, m.lap_scale);
     gs_update(u.x, v.x, lu.x, lv.x, m, val[0].x, val[1].x);
     gs_update(u.y, v.y, lu.y, lv.y, m, val[0].y, val[1].y);
     gs_update(u.z, v.z, lu.z, lv.z, m, val[0].z, val[1].z);
@@ -166,14 +167,15 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 constexpr int kMinStripRows = 3;
 
 // Laplacians of a float4 group from its row (c), the rows above (u) and below (d) and its two
-// x-edge scalars: lap2d_x4<PF_ST_STD>'s arithmetic.
+// x-edge scalars: lap2d_x4<PF_ST_STD, MODEL>'s arithmetic.
+template <int MODEL = PF_MODEL_AC>
 __device__ __forceinline__ float4 lap4_rows(const float4& c, const float4& u, const float4& d,
                                             float l, float r, float scale) {
   float4 o;
-  o.x = lap2d(c.x, l, c.y, u.x, d.x, scale);
-  o.y = lap2d(c.y, c.x, c.z, u.y, d.y, scale);
-  o.z = lap2d(c.z, c.y, c.w, u.z, d.z, scale);
-  o.w = lap2d(c.w, c.z, r, u.w, d.w, scale);
+  o.x = lap_scaled<MODEL>(lap2d_sum(c.x, l, c.y, u.x, d.x), scale);
+  o.y = lap_scaled<MODEL>(lap2d_sum(c.y, c.x, c.z, u.y, d.y), scale);
+  o.z = lap_scaled<MODEL>(lap2d_sum(c.z, c.y, c.w, u.z, d.z), scale);
+  o.w = lap_scaled<MODEL>(lap2d_sum(c.w, c.z, r, u.w, d.w), scale);
   return o;
 }
 
@@ -242,11 +244,11 @@ __device__ __forceinline__ void update_strip(const float* src, const float* mu, 
   }
   for (int r = st.r0; r < st.r1; ++r, p += ws) {
     const float4 d0 = ld4(A0 + p + ws);
-    const float4 l0 = lap4_rows(c0, u0, d0, A0[p - 1], A0[p + 4], m.lap_scale);
+    const float4 l0 = lap4_rows<MODEL>(c0, u0, d0, A0[p - 1], A0[p + 4], m.lap_scale);
     float4 d1 = d0, l1 = l0;
     if constexpr (TWO) {
       d1 = ld4(A1 + p + ws);
-      l1 = lap4_rows(c1, u1, d1, A1[p - 1], A1[p + 4], m.lap_scale);
+      l1 = lap4_rows<MODEL>(c1, u1, d1, A1[p - 1], A1[p + 4], m.lap_scale);
     }
     float4 val[NF];
     if constexpr (MODEL == PF_MODEL_AC) {

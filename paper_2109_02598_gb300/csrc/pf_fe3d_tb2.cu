@@ -65,7 +65,9 @@ __device__ __forceinline__ void update4(const float4* c, const float4* lap, floa
 }
 
 // 7-point Laplacians of four sites: centre c, z-neighbours zm/zp, rows above/below and the
-// two x-edge scalars of the centre row.
+// two x-edge scalars of the centre row. The multiply by lap_scale stays even for Gray-Scott
+// (whose factor is 1, so the bits are those of lap_scaled): leaving it out measured 1.3 %
+// slower in this kernel (476 against 482 GLUPS on GS 256^3).
 __device__ __forceinline__ float4 lap3d_x4(const float4& c, const float4& ym, const float4& yp,
                                            const float4& zm, const float4& zp, float xm,
                                            float xp, float lap_scale) {

@@ -163,10 +163,14 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
         float xp = __shfl_down_sync(0xffffffffu, c[f].x, 1, LX);
         if (tx4 == 0) xm = M[C::MAIN + ty * 4 + 3];
         if (tx4 == LX - 1) xp = M[C::MAIN + C::SIDE + ty * 4 + 0];
-        lap[f].x = lap3d(c[f].x, xm, c[f].y, ym.x, yp.x, zm[f].x, zp[f].x, m.lap_scale);
-        lap[f].y = lap3d(c[f].y, c[f].x, c[f].z, ym.y, yp.y, zm[f].y, zp[f].y, m.lap_scale);
-        lap[f].z = lap3d(c[f].z, c[f].y, c[f].w, ym.z, yp.z, zm[f].z, zp[f].z, m.lap_scale);
-        lap[f].w = lap3d(c[f].w, c[f].z, xp, ym.w, yp.w, zm[f].w, zp[f].w, m.lap_scale);
+        lap[f].x = lap_scaled<MODEL>(
+            lap3d_sum(c[f].x, xm, c[f].y, ym.x, yp.x, zm[f].x, zp[f].x), m.lap_scale);
+        lap[f].y = lap_scaled<MODEL>(
+            lap3d_sum(c[f].y, c[f].x, c[f].z, ym.y, yp.y, zm[f].y, zp[f].y), m.lap_scale);
+        lap[f].z = lap_scaled<MODEL>(
+            lap3d_sum(c[f].z, c[f].y, c[f].w, ym.z, yp.z, zm[f].z, zp[f].z), m.lap_scale);
+        lap[f].w = lap_scaled<MODEL>(
+            lap3d_sum(c[f].w, c[f].z, xp, ym.w, yp.w, zm[f].w, zp[f].w), m.lap_scale);
       }
       if constexpr (MODEL == PF_MODEL_AC) {
         res[0].x = ac_update(c[0].x, lap[0].x, m);

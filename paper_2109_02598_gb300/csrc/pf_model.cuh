@@ -27,7 +27,7 @@ namespace pf {
 // Coefficients as the kernels use them (float32, rounded once on the host).
 //   AC: a0 = c1, a1 = c2
 //   CH: a0 = c1, a1 = c2, a2 = dt * M
-//   GS: a0 = Du, a1 = Dv, a2 = F, a3 = F + k
+//   GS: a0 = Du s, a1 = Dv s, a2 = F, a3 = F + k (s = the stencil factor; lap_scale = 1)
 //   C:  a0 = c1, a1 = c2, a2 = c3, a3 = c4, a4 = c5, a5 = 2 c5
 // lap_scale: the stencil's overall factor, 1/h^2 for the standard 5/7-point stencils,
 // 1/(6 h^2) for the isotropic 9/19-point ones, 1/(12 h^2) for the fourth-order 9-point one,
@@ -76,16 +76,37 @@ struct ModelTraits<PF_MODEL_C> {
   static constexpr int R = 2;  // m needs the Laplacian of its chemical potential
 };
 
+// 5-/7-point stencil sums before the factor 1/h^2.
+__device__ __forceinline__ float lap2d_sum(float c, float xm, float xp, float ym, float yp) {
+  const float s = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp));
+  return __fmaf_rn(-4.0f, c, s);
+}
+
+__device__ __forceinline__ float lap3d_sum(float c, float xm, float xp, float ym, float yp,
+                                           float zm, float zp) {
+  const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+  return __fmaf_rn(-6.0f, c, s);
+}
+
 __device__ __forceinline__ float lap2d(float c, float xm, float xp, float ym, float yp,
                                        float lap_scale) {
-  const float s = __fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp));
-  return __fmul_rn(__fmaf_rn(-4.0f, c, s), lap_scale);
+  return __fmul_rn(lap2d_sum(c, xm, xp, ym, yp), lap_scale);
 }
 
 __device__ __forceinline__ float lap3d(float c, float xm, float xp, float ym, float yp,
                                        float zm, float zp, float lap_scale) {
-  const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
-  return __fmul_rn(__fmaf_rn(-6.0f, c, s), lap_scale);
+  return __fmul_rn(lap3d_sum(c, xm, xp, ym, yp, zm, zp), lap_scale);
+}
+
+// Gray-Scott's parameters carry the stencil factor in D_u and D_v, and its lap_scale is 1
+// (make_params). x * 1 is exact, so a Gray-Scott kernel may leave the Laplacian's final
+// multiply out and still give the bits of one that does it.
+template <int MODEL>
+__device__ __forceinline__ float lap_scaled(float sum, float lap_scale) {
+  if constexpr (MODEL == PF_MODEL_GS)
+    return sum;
+  else
+    return __fmul_rn(sum, lap_scale);
 }
 
 // Isotropic 9-point: (4 (axial) + (diagonal) - 20 c) / (6 h^2)
