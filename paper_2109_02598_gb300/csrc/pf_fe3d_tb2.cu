@@ -184,7 +184,13 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         ic[f] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
     }
     // first-level index j = 0 .. n+1 is plane zfirst + (j-1) dir, from input planes j, j+1,
-    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2
+    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2. The stages of
+    // input planes j+1, j+2, the mbarrier phase of j+2 and the first-level ring planes
+    // j % 3, (j-1) % 3 advance incrementally instead of by division.
+    uint32_t s1 = (q_base + 1) % NS, s2 = (q_base + 2) % NS;
+    uint32_t ph2 = ((q_base + 2) / NS) & 1u;
+    float* l1w = l1;                       // first-level ring plane j % 3
+    float* l1r = l1 + 2 * C::L1_PLANE;     // and (j - 1) % 3
     for (int j = 0; j < n + 2; ++j) {
       if (__syncthreads_or(err)) break;
       if (tid == 0 && j + NS < nin) {
@@ -192,11 +198,16 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         issue(q_base + j + NS, y0, in_plane(j + NS));
         q_issued = q_base + j + NS + 1;
       }
-      err = !wait(q_base + j + 2);
+      err = !mbar_wait_bounded(&bars[s2], ph2, kWaitBudgetCycles);
       if (err) continue;
       // ---- first level on row r of plane j (input centre plane j+1)
-      const float* sc = stage_ptr(q_base + j + 1);
-      const float* sp = stage_ptr(q_base + j + 2);
+      const float* sc = ring + s1 * C::IN_STAGE;
+      const float* sp = ring + s2 * C::IN_STAGE;
+      s1 = s2;
+      if (++s2 == NS) {
+        s2 = 0;
+        ph2 ^= 1u;
+      }
       float4 izp[NF], lap[NF], l1v[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -209,17 +220,16 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         lap[f] = lap3d_x4(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.lap_scale);
       }
       update4<MODEL>(ic, lap, l1v, m);
-      float* l1p = l1 + (j % 3) * C::L1_PLANE;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        *reinterpret_cast<float4*>(l1p + f * C::L1_FIELD + r * W + 4 * x4) = l1v[f];
+        *reinterpret_cast<float4*>(l1w + f * C::L1_FIELD + r * W + 4 * x4) = l1v[f];
         izm[f] = ic[f];
         ic[f] = izp[f];
       }
       // ---- second level for output o = j - 2: centre is first-level plane j-1, whose
       // rows were completed before this iteration's barrier
       if (j >= 2 && second) {
-        const float* lp = l1 + ((j - 1) % 3) * C::L1_PLANE;
+        const float* lp = l1r;
         float4 lap2[NF], res[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -241,6 +251,8 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         lzm[f] = lc[f];
         lc[f] = l1v[f];
       }
+      l1r = l1w;
+      l1w = l1w == l1 + 2 * C::L1_PLANE ? l1 : l1w + C::L1_PLANE;
     }
     q_base += nin;
   }
