@@ -220,12 +220,15 @@ def test_ac2d_128_1000_steps(pf):
     assert rel_linf(one, oracle.euler_step("ac", x0, w["coeffs"], w["dt"])) <= 1e-6
 
 
-def test_ch2d_1000_steps_256(pf):
-    # the 2048^2 recipe at 256^2 so the oracle finishes 1000 steps in seconds
+@pytest.mark.parametrize("bands", [False, True])
+def test_ch2d_1000_steps_256(pf, bands):
+    # the 2048^2 recipe at 256^2 so the oracle finishes 1000 steps in seconds; also on the
+    # band kernel (64 bands of 4 rows)
     w = synthetic.WORKLOADS["ch2d_2048"]
     x0 = synthetic.workload_init("ch2d_2048", shape=(256, 256))
     ref = oracle.run("ch", x0, w["coeffs"], w["dt"], 1000, w["h"])
-    got = gpu_run(pf, "ch", x0, 1000, w["coeffs"], w["dt"], w["h"])
+    tuning = (256, pf.PF_TILE_BANDS, 1) if bands else None
+    got = gpu_run(pf, "ch", x0, 1000, w["coeffs"], w["dt"], w["h"], tuning=tuning)
     assert rel_l2(got, ref) <= 1e-3
 
 
@@ -247,18 +250,26 @@ def test_full_size_single_step(pf, name):
 
 
 def test_full_size_ch2d_mass_conserved(pf):
+    # 2000 steps of the 2048^2 configuration on the default tiled kernel and on the band
+    # kernel (the autotuner's choice for this grid): mass conserved, and the same bits
     w = synthetic.WORKLOADS["ch2d_2048"]
     (x0,) = synthetic.workload_init("ch2d_2048")
-    g = pf.Grid(x0.shape, 1, w["h"]).set_model("ch", w["coeffs"], w["dt"])
-    g.write_field(0, x0)
-    m0 = g.mass()
-    assert abs(m0 - oracle.mass(x0)) <= 1e-9 * np.abs(x0.astype(np.float64)).sum()
-    g.step(2000)
-    m1 = g.mass()
-    assert abs(m1 - m0) / x0.size <= 1e-6  # mean drift per site
-    phi = g.read_field(0)
-    assert np.isfinite(phi).all() and phi.std() > x0.std()  # spinodal growth happened
-    g.close()
+    phis = []
+    for tuning in (None, (2048, pf.PF_TILE_BANDS, 1)):
+        g = pf.Grid(x0.shape, 1, w["h"]).set_model("ch", w["coeffs"], w["dt"])
+        if tuning:
+            g.set_tuning(*tuning)
+        g.write_field(0, x0)
+        m0 = g.mass()
+        assert abs(m0 - oracle.mass(x0)) <= 1e-9 * np.abs(x0.astype(np.float64)).sum()
+        g.step(2000)
+        m1 = g.mass()
+        assert abs(m1 - m0) / x0.size <= 1e-6  # mean drift per site
+        phi = g.read_field(0)
+        assert np.isfinite(phi).all() and phi.std() > x0.std()  # spinodal growth happened
+        g.close()
+        phis.append(phi)
+    assert np.array_equal(phis[0], phis[1])
 
 
 def test_full_size_gs3d_stays_bounded(pf):
