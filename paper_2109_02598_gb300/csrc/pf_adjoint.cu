@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs l
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
   const int y0 = blockIdx.y * TY;
-  load_region2d<AdjCfg>(x, g.nx, g.ny, g.pitch, x0, y0, sm);
+  load_region2d<AdjCfg, false>(x, g.nx, g.ny, g.pitch, x0, y0, sm);  // waits with the next
   load_region2d<AdjCfg>(lam, g.nx, g.ny, g.pitch, x0, y0, sm + 2 * PL);
   __syncthreads();
   const float* su = sm;

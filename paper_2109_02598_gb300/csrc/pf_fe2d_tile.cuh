@@ -33,8 +33,26 @@ struct Cfg2 {
   static_assert(TX % 4 == 0, "tile width must be a multiple of 4");
 };
 
-// Stage rows [y0-H, y0+TY+H) x columns [x0-HP, x0+TX+HP) of every field into buffer 0.
-template <class C>
+// Asynchronous global -> shared copies (cp.async): a thread issues all of its copies before
+// waiting for any, so the staging costs one memory latency rather than one per group.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Stage rows [y0-H, y0+TY+H) x columns [x0-HP, x0+TX+HP) of every field into buffer 0:
+// 16-byte copies where the four columns lie inside the grid (x0, HP and the row pitch are
+// multiples of 4, so those are 16-byte aligned), four periodic 4-byte copies elsewhere. The
+// calling thread's copies are complete when this returns (WAIT; otherwise at the next
+// cp_async_wait_all); the caller's barrier then makes every thread's visible.
+template <class C, bool WAIT = true>
 __device__ __forceinline__ void load_region2d(const FieldPtrs& in, int nx, int ny,
                                               int64_t pitch, int x0, int y0, float* sm) {
   constexpr int CH4 = C::WS / 4;  // float4 groups per staged row
@@ -47,20 +65,22 @@ __device__ __forceinline__ void load_region2d(const FieldPtrs& in, int nx, int n
     float* dst = sm + r * C::WS + 4 * j;
     if (gx >= 0 && gx + 3 < nx) {
 #pragma unroll
-      for (int f = 0; f < C::NF; ++f)
-        *reinterpret_cast<float4*>(dst + f * C::PL) =
-            __ldg(reinterpret_cast<const float4*>(in.f[f] + row + gx));
+      for (int f = 0; f < C::NF; ++f) cp_async16(dst + f * C::PL, in.f[f] + row + gx);
     } else {
       const int64_t o0 = row + wrap_index(gx, nx), o1 = row + wrap_index(gx + 1, nx);
       const int64_t o2 = row + wrap_index(gx + 2, nx), o3 = row + wrap_index(gx + 3, nx);
 #pragma unroll
       for (int f = 0; f < C::NF; ++f) {
         const float* p = in.f[f];
-        *reinterpret_cast<float4*>(dst + f * C::PL) =
-            make_float4(__ldg(p + o0), __ldg(p + o1), __ldg(p + o2), __ldg(p + o3));
+        float* d = dst + f * C::PL;
+        cp_async4(d, p + o0);
+        cp_async4(d + 1, p + o1);
+        cp_async4(d + 2, p + o2);
+        cp_async4(d + 3, p + o3);
       }
     }
   }
+  if (WAIT) cp_async_wait_all();
 }
 
 // 2D Laplacians of four consecutive sites from a float4 row and its neighbours, with the
