@@ -179,9 +179,10 @@ __global__ void __launch_bounds__(kNT2) adj_ac2d_kernel(FieldPtrs x, FieldPtrs l
     const int c = i - r * kAW;
     const int64_t off =
         (int64_t)wrap_index(y0 - 1 + r, g.ny) * g.pitch + wrap_index(x0 - 1 + c, g.nx);
-    sp[i] = __ldg(x.f[0] + off);
-    sl[i] = __ldg(lam.f[0] + off);
+    cp_async4(&sp[i], x.f[0] + off);
+    cp_async4(&sl[i], lam.f[0] + off);
   }
+  cp_async_wait_all();
   __syncthreads();
   const float c2x3 = __fmul_rn(3.0f, m.a1);
   float s0 = 0.f, s1 = 0.f;
@@ -219,9 +220,10 @@ __global__ void __launch_bounds__(kNT2) adj_ch2d_kernel(FieldPtrs x, FieldPtrs l
     const int c = i - r * kBW;
     const int64_t off =
         (int64_t)wrap_index(y0 - 2 + r, g.ny) * g.pitch + wrap_index(x0 - 2 + c, g.nx);
-    sp[i] = __ldg(x.f[0] + off);
-    sl[i] = __ldg(lam.f[0] + off);
+    cp_async4(&sp[i], x.f[0] + off);
+    cp_async4(&sl[i], lam.f[0] + off);
   }
+  cp_async_wait_all();
   __syncthreads();
   // w on rows/cols 1 .. kBH-2 / kBW-2 (the tile and one ring)
   for (int i = threadIdx.x; i < (kATX + 2) * (kATY + 2); i += kNT2) {

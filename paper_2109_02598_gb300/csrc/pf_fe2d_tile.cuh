@@ -12,6 +12,7 @@
 #pragma once
 
 #include "pf_internal.h"
+#include "pf_tma.cuh"
 
 namespace pf {
 
@@ -32,20 +33,6 @@ struct Cfg2 {
   static constexpr int SMEM_FLOATS = NF * NBUF * PL + MU;
   static_assert(TX % 4 == 0, "tile width must be a multiple of 4");
 };
-
-// Asynchronous global -> shared copies (cp.async): a thread issues all of its copies before
-// waiting for any, so the staging costs one memory latency rather than one per group.
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 // Stage rows [y0-H, y0+TY+H) x columns [x0-HP, x0+TX+HP) of every field into buffer 0:
 // 16-byte copies where the four columns lie inside the grid (x0, HP and the row pitch are

@@ -6,6 +6,7 @@
 // and three mu planes (halo 1); mu is computed on chip and never stored.  Model C keeps
 // both of its fields in the phi planes and the chemical potential of m in the mu planes.
 #include "pf_internal.h"
+#include "pf_tma.cuh"
 
 namespace pf {
 
@@ -31,7 +32,9 @@ struct Cfg3 {
   static constexpr int SMEM_FLOATS = NPH * NF * PL + (R == 2 ? 3 * PL1 : 0);
 };
 
-// Stage plane z (periodic) of every field into ring slot `slot`.
+// Stage plane z (periodic) of every field into ring slot `slot`: 4-byte cp.async copies (the
+// rows start at x0 - R, so they are not 16-byte aligned), all of a thread's copies issued
+// before one wait; the caller's barrier then makes every thread's visible.
 template <class C>
 __device__ __forceinline__ void load_plane3d(const FieldPtrs& in, const Geom& g, int x0,
                                              int y0, int z, int slot, float* sm) {
@@ -43,8 +46,9 @@ __device__ __forceinline__ void load_plane3d(const FieldPtrs& in, const Geom& g,
     const int gx = wrap_index(x0 - C::R + c, g.nx);
     const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
 #pragma unroll
-    for (int f = 0; f < C::NF; ++f) sm[(slot * C::NF + f) * C::PL + i] = __ldg(in.f[f] + off);
+    for (int f = 0; f < C::NF; ++f) cp_async4(sm + (slot * C::NF + f) * C::PL + i, in.f[f] + off);
   }
+  cp_async_wait_all();
 }
 
 // 3D Laplacian at position p of a staged plane c (row width W) with the planes b below and
