@@ -11,6 +11,9 @@ import re
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libpfgpu.so")
+# PFGPU_CHECKED=1 loads the checked variant (built with -DPF_CHECK: shared memory filled with
+# NaN before every staging) instead; a process uses one or the other.
+CHECKED_LIB_PATH = os.path.join(PKG, "_build", "checked", "libpfgpu_checked.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "pfgpu.h")
 
 PF_OK = 0
@@ -116,11 +119,13 @@ class PfError(RuntimeError):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
+def load(path: str = None):
     """Load the library (once) and declare its signatures. Raises if it is not built."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = CHECKED_LIB_PATH if os.environ.get("PFGPU_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(
             f"libpfgpu.so not found at {path}: build it with __graft_entry__.build() "

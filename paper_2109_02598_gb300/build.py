@@ -20,6 +20,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpfgpu.so")
+# The checked variant (-DPF_CHECK): every kernel fills its shared memory with NaN before
+# staging, so a read of a slot that staging or an earlier sub-step did not write poisons the
+# result and the parity tests see it (compute-sanitizer is not available).
+CHECKED_BUILD = os.path.join(BUILD, "checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libpfgpu_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -65,20 +70,23 @@ def _stamp(extra_flags) -> str:
     return h.hexdigest()
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
-    """Compile and link the library; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_file = os.path.join(BUILD, "stamp.txt")
+def build(verbose: bool = False, force: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile and link the library (checked: the PF_CHECK variant); returns its path."""
+    bdir, lib = (CHECKED_BUILD, CHECKED_LIB) if checked else (BUILD, LIB)
+    if checked:
+        extra_flags = list(extra_flags) + ["-DPF_CHECK"]
+    os.makedirs(bdir, exist_ok=True)
+    stamp_file = os.path.join(bdir, "stamp.txt")
     stamp = _stamp(list(extra_flags) + [_cuda_libdir(_nvcc())])
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         if open(stamp_file).read().strip() == stamp:
-            return LIB
+            return lib
     nvcc = _nvcc()
     srcs = _sources()
     extra_flags = list(extra_flags) + [f'-DPF_CUDA_LIBDIR="{_cuda_libdir(nvcc)}"']
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode != 0:
@@ -89,16 +97,16 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
-        raise RuntimeError("link of libpfgpu.so failed")
-    os.replace(tmp, LIB)
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed")
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as f:
         f.write(stamp + "\n")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

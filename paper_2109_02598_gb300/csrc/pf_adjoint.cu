@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kNT2) adj_gs2d_kernel(FieldPtrs x, FieldPtrs l
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
   const int y0 = blockIdx.y * TY;
+  canary_fill(sm, 4 * PL);
   load_region2d<AdjCfg, false>(x, g.nx, g.ny, g.pitch, x0, y0, sm);  // waits with the next
   load_region2d<AdjCfg>(lam, g.nx, g.ny, g.pitch, x0, y0, sm + 2 * PL);
   __syncthreads();
@@ -174,6 +175,8 @@ __global__ void __launch_bounds__(kNT2) adj_ac2d_kernel(FieldPtrs x, FieldPtrs l
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
   const int y0 = blockIdx.y * kATY;
+  canary_fill(sp, kAPL);
+  canary_fill(sl, kAPL);
   for (int i = threadIdx.x; i < kAPL; i += kNT2) {
     const int r = i / kAW;
     const int c = i - r * kAW;
@@ -215,6 +218,9 @@ __global__ void __launch_bounds__(kNT2) adj_ch2d_kernel(FieldPtrs x, FieldPtrs l
   __shared__ double red[4][kNT2 / 32];
   const int x0 = blockIdx.x * kATX;
   const int y0 = blockIdx.y * kATY;
+  canary_fill(sp, kBPL);
+  canary_fill(sl, kBPL);
+  canary_fill(sw, kBPL);
   for (int i = threadIdx.x; i < kBPL; i += kNT2) {
     const int r = i / kBW;
     const int c = i - r * kBW;

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(NT, 1)
   auto put_aside = [&](int r, const VT& v) { stv<V>(aside + r * nx + V * j, v); };
   auto get_aside = [&](int r) { return ldv<V>(aside + r * nx + V * j); };
 
+  canary_fill(phi, (size_t)(g.bmax + 2 * R + C::RING) * ws + (size_t)2 * R * nx);
   for (int y = -R; y < B + R; ++y) {
     const int gy = wrap_index(y0 + y, g.ny);
     VT v;

@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(kNTC, 1)
   const int ngl = WS / 4 < kNTC ? WS / 4 : kNTC;
   const int tj = threadIdx.x % ngl, tr = threadIdx.x / ngl, rstep = kNTC / ngl;
 
+#ifdef PF_CHECK
+  canary_fill(sm, (size_t)2 * NF * PL + (C::MU ? PL : 0) + (size_t)4 * NF * H * NX);
+  cluster.sync();  // no neighbour stores into this CTA's receive buffers before the fill
+#endif
   // stage rows y0 - H .. y0 + B + H - 1 (periodic in y) with their halo columns
   for (int i = threadIdx.x; i < HT * nx4; i += kNTC) {
     const int r = i / nx4, j = i - r * nx4;

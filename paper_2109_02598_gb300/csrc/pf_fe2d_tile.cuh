@@ -311,6 +311,7 @@ __device__ __forceinline__ void fe2d_tile(const FieldPtrs& in, const FieldOut& o
   constexpr int WS = C::WS;
   constexpr int PL = C::PL;
   static_assert(WS / 4 <= kNT2, "a row's column groups must fit the CTA (row strips)");
+  canary_fill(sm, C::SMEM_FLOATS);
   load_region2d<C>(in, nx, ny, pitch, x0, y0, sm);
   __syncthreads();
 #pragma unroll

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut ou
   const int y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * tz;
   const int z1 = min(z0 + tz, g.nz);
+  canary_fill(sm, C::SMEM_FLOATS);
   load_plane3d<C>(in, g, x0, y0, z0 - 1, 0, sm);
   load_plane3d<C>(in, g, x0, y0, z0, 1, sm);
   int sb = 0, sc = 1, sa = 2;
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(kNT3) fe3d_r2_kernel(FieldPtrs in, FieldOut ou
   auto pslot = [&](int p) { return (p - z0 + 8) % NPH; };
   auto plane = [&](int p) { return ph + pslot(p) * NF * PL; };
   // prologue: mu(z0-1) from phi(z0-2..z0), then mu(z0) from phi(z0-1..z0+1)
+  canary_fill(sm, C::SMEM_FLOATS);
   load_plane3d<C>(in, g, x0, y0, z0 - 2, pslot(z0 - 2), ph);
   load_plane3d<C>(in, g, x0, y0, z0 - 1, pslot(z0 - 1), ph);
   load_plane3d<C>(in, g, x0, y0, z0, pslot(z0), ph);

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
   const int x4 = tid % LX;
   const int r = tid / LX;  // first-level row y0 - 1 + r; input row r + 1
   const bool second = (r >= 1 && r <= TY);
+  canary_fill(ring, (size_t)NS * C::IN_STAGE + 3 * C::L1_PLANE);  // TMA issues follow a proxy fence
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();

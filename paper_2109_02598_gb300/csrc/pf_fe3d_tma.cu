@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(CfgT<MODEL, TX, TY, NS>::NT)
   const int tid = threadIdx.x;
   const int tx4 = tid % LX;
   const int ty = tid / LX;
+  canary_fill(ring, (size_t)NS * C::STAGE);  // TMA issues follow a proxy fence
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();

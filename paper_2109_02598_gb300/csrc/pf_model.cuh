@@ -189,6 +189,20 @@ __device__ __forceinline__ void mc_update(float psi, float m, float lap_psi, flo
   m_n = __fmaf_rn(p.dt, lap_mu, m);
 }
 
+// Checked builds (PF_CHECK): fill n floats of shared memory with NaN before they are staged,
+// so a read of a slot that staging or an earlier sub-step did not write turns results into
+// NaN, which the parity tests see. Every thread of the CTA calls it; it ends with a CTA
+// barrier. A no-op in normal builds.
+__device__ __forceinline__ void canary_fill(float* p, size_t n) {
+#ifdef PF_CHECK
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = __int_as_float(0x7fc00000);
+  __syncthreads();
+#else
+  (void)p;
+  (void)n;
+#endif
+}
+
 // Periodic index: i in [-n, 2n) maps into [0, n); anything else takes the slow modulo
 // (only tiles larger than the grid reach it).
 __device__ __forceinline__ int wrap_index(int i, int n) {
