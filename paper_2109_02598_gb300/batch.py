@@ -11,8 +11,9 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import GS2DSpec, check
-from .grid import _stream_handle, _torch
+from . import tunecache
+from ._lib import GS2DSpec, PfError, check
+from .grid import _device_tag, _stream_handle, _torch
 
 
 class Batch:
@@ -100,10 +101,25 @@ class Batch:
                                             ctypes.byref(c)))
         return a.value, b.value, c.value
 
-    def autotune(self, probe_launches: int = 3):
+    def autotune(self, probe_launches: int = 3, cache: str | None = None):
+        """Time every (tile, k) on the whole batch and keep the fastest. With a cache file
+        (`cache` or $PFGPU_TUNE_CACHE) a stored choice for this device, library version and
+        list of instance sizes is applied without probing, and a new one is stored."""
+        path = tunecache.cache_path(cache)
+        key = None
+        if path:
+            key = tunecache.batch_key(_device_tag(), self._lib.pf_version(), self.shapes)
+            hit = tunecache.get(path, key)
+            if hit is not None:
+                try:
+                    return self.set_tuning(*hit).tuning
+                except PfError:
+                    pass  # not valid for this build or device: tune again
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self._lib.pf_batch_autotune(self._h, probe_launches, ctypes.byref(a),
                                           ctypes.byref(b), ctypes.byref(c)))
+        if path:
+            tunecache.put(path, key, (a.value, b.value, c.value))
         return a.value, b.value, c.value
 
 

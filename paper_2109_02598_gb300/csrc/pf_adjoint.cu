@@ -412,6 +412,7 @@ using namespace pf;
 extern "C" {
 
 int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval) {
+  NvtxRange nvtx_("pf_adj_forward");
   if (int rc = check_grid(g)) return rc;
   if (int rc = check_gs2d(g)) return rc;
   if (n_steps < 1) return invalid("n_steps must be >= 1");
@@ -463,6 +464,7 @@ int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval) {
 
 int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int on_device,
                     float* dLdu0, float* dLdv0, double* dtheta) {
+  NvtxRange nvtx_("pf_adj_backward");
   if (int rc = check_grid(g)) return rc;
   if (int rc = check_gs2d(g)) return rc;
   AdjointState& a = g->adj;

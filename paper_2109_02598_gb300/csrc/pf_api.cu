@@ -463,6 +463,7 @@ int pf_read_field_host_async(pf_grid_t g, int field, float* dst) {
 }
 
 int pf_step(pf_grid_t g, int64_t n_steps) {
+  NvtxRange nvtx_("pf_step");
   if (int rc = check_grid(g)) return rc;
   if (!g->model_set) {
     set_error("pf_step: no model set (call pf_set_model first)");
@@ -526,6 +527,7 @@ int pf_step(pf_grid_t g, int64_t n_steps) {
 }
 
 int pf_reduce(pf_grid_t g, int what, int field, double* out) {
+  NvtxRange nvtx_("pf_reduce");
   if (int rc = check_grid(g)) return rc;
   if (out == nullptr) return invalid("out is NULL");
   if (what != PF_REDUCE_MASS && what != PF_REDUCE_ENERGY) return invalid("unknown reduction %d", what);
@@ -668,6 +670,7 @@ int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps) {
 }
 
 int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps) {
+  NvtxRange nvtx_("pf_autotune");
   if (int rc = check_grid(g)) return rc;
   if (!g->model_set) {
     set_error("pf_autotune: no model set");

@@ -234,6 +234,7 @@ int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps) {
 
 int pf_batch_autotune(pf_batch_t b, int probe_launches, int* tile_x, int* tile_y,
                       int* k_steps) {
+  NvtxRange nvtx_("pf_batch_autotune");
   if (int rc = check_batch(b)) return rc;
   if (probe_launches < 1) probe_launches = 3;
   cudaEvent_t e0, e1;
@@ -270,6 +271,7 @@ int pf_batch_autotune(pf_batch_t b, int probe_launches, int* tile_x, int* tile_y
 }
 
 int pf_batch_run(pf_batch_t b, int64_t n_steps) {
+  NvtxRange nvtx_("pf_batch_run");
   if (int rc = check_batch(b)) return rc;
   if (n_steps < 0) return invalid("n_steps must be >= 0");
   if (n_steps == 0) return PF_OK;

@@ -1,6 +1,7 @@
 // Host-side declarations shared by the translation units of libpfgpu (not installed).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -42,6 +43,15 @@ cudaError_t ensure_smem_attr(KernelT kernel, size_t bytes, unsigned long long* m
   if (e == cudaSuccess) *mask |= bit;
   return e;
 }
+
+// A named range on the host timeline of a profiler that reads NVTX (header-only NVTX3; without
+// such a tool attached a push or pop is a call through a null-checked pointer).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Thread-local error reporting (pf_last_error).
 void set_error(const char* fmt, ...);

@@ -486,6 +486,7 @@ int pf_spectral_read_field(pf_spectral_t s, int field, float* dst, int dst_on_de
 }
 
 int pf_spectral_step(pf_spectral_t s, int64_t n_steps) {
+  NvtxRange nvtx_("pf_spectral_step");
   if (int rc = check_spectral(s)) return rc;
   if (n_steps < 0) return invalid("n_steps must be >= 0");
   if (use_fused(s)) return spectral_fused_run(s, n_steps);

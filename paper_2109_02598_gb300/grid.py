@@ -13,7 +13,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import MODEL_FIELDS, MODEL_IDS, check
+from . import tunecache
+from ._lib import MODEL_FIELDS, MODEL_IDS, PfError, check
 
 
 def _torch():
@@ -29,6 +30,14 @@ def _stream_handle(stream):
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+def _device_tag() -> str:
+    """Name and compute capability of the current CUDA device (the tune cache's key)."""
+    torch = _torch()
+    d = torch.cuda.current_device()
+    major, minor = torch.cuda.get_device_capability(d)
+    return f"{torch.cuda.get_device_name(d)}|sm{major}{minor}"
 
 
 class Grid:
@@ -196,11 +205,51 @@ class Grid:
         check(self._lib.pf_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
 
-    def autotune(self, probe_launches: int = 5):
+    def autotune(self, probe_launches: int = 5, cache: str | None = None):
+        """Time every supported (tile, k) and keep the fastest (pf_autotune). With a cache
+        file (`cache` or $PFGPU_TUNE_CACHE) a stored choice for this device, library version,
+        shape, field count, model and stencil is applied without probing, and a new one is
+        stored."""
+        path = tunecache.cache_path(cache)
+        key = None
+        if path:
+            key = tunecache.grid_key(_device_tag(), self._lib.pf_version(), self.shape,
+                                     self.n_fields, str(self.model),
+                                     getattr(self, "stencil", "std"))
+            hit = tunecache.get(path, key)
+            if hit is not None:
+                try:
+                    return self.set_tuning(*hit).tuning
+                except PfError:
+                    pass  # not valid for this build or device: tune again
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self._lib.pf_autotune(self._h, probe_launches, ctypes.byref(a), ctypes.byref(b),
                                     ctypes.byref(c)))
+        if path:
+            tunecache.put(path, key, (a.value, b.value, c.value))
         return a.value, b.value, c.value
+
+    def run_series(self, n_steps: int, every: int, energy: bool = False):
+        """Advance n_steps in chunks of `every` and record the mass of every field (and the
+        discrete free energy, for Models A, B and C) after each chunk: a list of dicts
+        {"step", "mass": [...], "energy"}; the first entry is the state before stepping."""
+        if every < 1:
+            raise ValueError("every must be >= 1")
+
+        def sample(step):
+            rec = {"step": step, "mass": [self.mass(f) for f in range(self.n_fields)]}
+            if energy:
+                rec["energy"] = self.energy()
+            return rec
+
+        series = [sample(0)]
+        done = 0
+        while done < n_steps:
+            k = min(every, n_steps - done)
+            self.step(k)
+            done += k
+            series.append(sample(done))
+        return series
 
     # ---------------------------------------------------------------- analysis
     def structure_factor(self, field: int = 0, n_bins: int = 32):

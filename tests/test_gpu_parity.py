@@ -600,6 +600,45 @@ def test_band_kernel_rules_and_autotune(pf):
     assert np.array_equal(a[0], gpu_run(pf, "ch", x0, 7)[0])
 
 
+def test_autotune_cache_file(pf, tmp_path):
+    # the first autotune stores its choice; a second grid of the same kind takes it from the
+    # file; an entry the library rejects is tuned again and overwritten
+    from paper_2109_02598_gb300 import tunecache
+    path = str(tmp_path / "tune.json")
+    x0 = init_fields("ch", (256, 256), seed=62)
+    g = pf.Grid((256, 256), 1).set_model("ch", COEFFS["ch"], DT["ch"]).write_fields(x0)
+    t1 = g.autotune(3, cache=path)
+    g.close()
+    data = tunecache.read(path)
+    assert list(data.values()) == [list(t1)]
+    key = next(iter(data))
+    h = pf.Grid((256, 256), 1).set_model("ch", COEFFS["ch"], DT["ch"]).write_fields(x0)
+    assert h.autotune(3, cache=path) == t1
+    h.close()
+    tunecache.put(path, key, (7, 7, 1))  # no such tile
+    h = pf.Grid((256, 256), 1).set_model("ch", COEFFS["ch"], DT["ch"]).write_fields(x0)
+    t3 = h.autotune(3, cache=path)
+    h.close()
+    assert tunecache.get(path, key) == tuple(t3) != (7, 7, 1)
+
+
+def test_run_series_mass_and_energy(pf):
+    # Model B conserves mass; Model A's discrete energy does not increase at a stable dt
+    x0 = init_fields("ch", (128, 128), seed=63)
+    g = pf.Grid((128, 128), 1).set_model("ch", COEFFS["ch"], DT["ch"]).write_fields(x0)
+    s = g.run_series(200, 25)
+    g.close()
+    assert [r["step"] for r in s] == list(range(0, 201, 25))
+    assert max(abs(r["mass"][0] - s[0]["mass"][0]) for r in s) / x0[0].size <= 1e-6
+    x0 = init_fields("ac", (128, 128), seed=64)
+    g = pf.Grid((128, 128), 1).set_model("ac", COEFFS["ac"], DT["ac"]).write_fields(x0)
+    s = g.run_series(100, 10, energy=True)
+    g.close()
+    e = [r["energy"] for r in s]
+    assert all(b <= a * (1 + 1e-6) + 1e-6 for a, b in zip(e, e[1:]))
+    assert e[-1] < e[0]
+
+
 def test_async_host_copies_pipeline_jobs_on_two_grids(pf):
     # the pattern of a caller that overlaps copies with steps: jobs alternate between two
     # grids on two streams, each job uploading, stepping and downloading without waiting;
