@@ -192,7 +192,8 @@ int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps);
 /* Time every supported (tile, k) for this grid and model (CUDA events), keep the fastest
  * and report it: tiled kernels as a replayed CUDA graph of max(probe_launches, 8) launches
  * (as pf_step runs them), the cluster and band kernels as one launch of 16 k probe_launches
- * steps.
+ * steps. A cluster or band candidate whose CTAs the device cannot host at once (the launch
+ * reports it) is skipped.
  * The state is not changed: probe launches read the current buffer and write the spare one.
  * Errors: PF_ERR_STATE (no model), PF_ERR_CUDA. */
 int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* k_steps);

@@ -698,6 +698,12 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
       const int n_l = probe_launches > 8 ? probe_launches : 8;
       cudaGraphExec_t probe = nullptr;
       cudaError_t e = launch_step(g, t, k, g->cur, 1 - g->cur, g->stream);  // warm-up
+      if (cluster && (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorLaunchOutOfResources)) {
+        // the on-chip kernels need all their CTAs resident at once; where the device cannot
+        // host them now (other work, a restricted context), they are not candidates
+        cudaGetLastError();
+        continue;
+      }
       if (!cluster && e == cudaSuccess) {
         if (g->capture == nullptr)
           e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
