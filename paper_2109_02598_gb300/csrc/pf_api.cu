@@ -22,6 +22,10 @@ void set_error(const char* fmt, ...) {
 int cuda_fail(cudaError_t e, const char* what) {
   set_error("CUDA error %d (%s) in %s: %s", (int)e, cudaGetErrorName(e), what,
             cudaGetErrorString(e));
+  // reset the runtime's last error, so a failed launch that left the context usable (a
+  // grid too large to co-schedule, a bad configuration) is not reported again by the next
+  // launch's check; an error that poisons the context keeps failing every later call anyway
+  (void)cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
 }
 
