@@ -551,6 +551,19 @@ def test_band_kernel_bitwise_and_oracle(pf, model, shape):
     assert rel_linf(a, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("model,coeffs,dt", [("ch", (0.8, 1.2, 0.6), 0.0012),
+                                              ("ac", (0.7, 1.3), 0.02)])
+def test_band_kernel_spacing_and_coefficients(pf, model, coeffs, dt):
+    # h = 0.5 (Laplacian factor 4) and non-unit coefficients: the tiled kernel's bits
+    shape = (300, 256)
+    x0 = init_fields(model, shape, seed=65)
+    a = gpu_run(pf, model, x0, 23, coeffs, dt, h=0.5, tuning=(256, pf.PF_TILE_BANDS, 1))
+    b = gpu_run(pf, model, x0, 23, coeffs, dt, h=0.5, tuning=(64, 16, 1))
+    assert np.array_equal(a[0], b[0])
+    ref = oracle.run(model, x0, coeffs, dt, 23, 0.5)
+    assert rel_linf(a, ref) <= 1e-5
+
+
 def test_band_kernel_model_b_2048_and_repeated_calls(pf):
     # the Model B configuration's grid: one step against the oracle; three calls of 5 steps
     # equal one call of 15 (step counters restart with every launch) and the tiled kernel
