@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from . import tunecache
+from . import checkpoint, tunecache
 from ._lib import MODEL_FIELDS, MODEL_IDS, PfError, check
 
 
@@ -62,6 +62,10 @@ class Grid:
                                        ctypes.byref(handle)))
         self._h = handle
         self.model = None
+        self.coeffs = None
+        self.dt = None
+        self.stencil = "std"
+        self.steps_done = 0  # steps taken through this object (or restored by load)
 
     # ---------------------------------------------------------------- lifecycle
     def close(self):
@@ -176,7 +180,40 @@ class Grid:
     # ---------------------------------------------------------------- stepping
     def step(self, n_steps: int = 1):
         check(self._lib.pf_step(self._h, int(n_steps)))
+        self.steps_done += int(n_steps)
         return self
+
+    # ---------------------------------------------------------------- checkpoints
+    def save(self, path: str, extra: dict | None = None):
+        """Write a checkpoint: the fields and what is needed to continue the run (model,
+        coefficients, dt, h, stencil, tuning, steps taken). `extra`: JSON-serialisable
+        values stored alongside."""
+        meta = {"shape": list(self.shape), "h": self.h, "model": self.model,
+                "coeffs": list(self.coeffs) if self.coeffs is not None else None,
+                "dt": self.dt, "stencil": self.stencil, "tuning": list(self.tuning),
+                "steps": self.steps_done, "extra": extra or {}}
+        checkpoint.save_state(path, meta, self.read_fields())
+        return self
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        """A grid restored from a checkpoint written by save(): same fields, model,
+        coefficients, dt, h, stencil and step count, and the saved tuning where this build
+        and device accept it. Stepping it on gives the bits of the run that did not stop."""
+        meta, fields = checkpoint.load_state(path)
+        g = cls(meta["shape"], len(fields), meta["h"], stream=stream)
+        if meta["model"] is not None:
+            g.set_model(meta["model"], meta["coeffs"], meta["dt"], force=True)
+        if meta["stencil"] != "std":
+            g.set_stencil(meta["stencil"])
+        try:
+            g.set_tuning(*meta["tuning"])
+        except PfError:
+            pass  # not available here: the default tuning gives the same bits
+        g.write_fields(fields)
+        g.steps_done = int(meta["steps"])
+        g.checkpoint_extra = meta.get("extra", {})
+        return g
 
     def synchronize(self):
         check(self._lib.pf_synchronize(self._h))

@@ -652,6 +652,30 @@ def test_run_series_mass_and_energy(pf):
     assert e[-1] < e[0]
 
 
+@pytest.mark.parametrize("model,shape,tuning", [("gs", (6, 32, 128), None),
+                                                 ("ch", (256, 256), (256, -1, 1)),
+                                                 ("c", (40, 36), (64, 16, 2))])
+def test_checkpoint_resume_is_bitwise(pf, tmp_path, model, shape, tuning):
+    # 12 steps, save, load into a new grid, 18 more: the bits of 30 steps without a stop
+    x0 = init_fields(model, shape, seed=66)
+    g = pf.Grid(shape, len(x0)).set_model(model, COEFFS[model], DT[model], force=True)
+    if tuning:
+        g.set_tuning(*tuning)
+    g.write_fields(x0).step(12)
+    g.save(str(tmp_path / "c.npz"), extra={"note": "half way"})
+    g.close()
+    h = pf.Grid.load(str(tmp_path / "c.npz"))
+    assert h.steps_done == 12 and h.model == model and h.checkpoint_extra == {"note": "half way"}
+    if tuning:
+        assert h.tuning == tuning
+    h.step(18)
+    a = h.read_fields()
+    h.close()
+    b = gpu_run(pf, model, x0, 30, tuning=tuning)
+    for p, q in zip(a, b):
+        assert np.array_equal(p, q)
+
+
 def test_async_host_copies_pipeline_jobs_on_two_grids(pf):
     # the pattern of a caller that overlaps copies with steps: jobs alternate between two
     # grids on two streams, each job uploading, stepping and downloading without waiting;
