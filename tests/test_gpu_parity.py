@@ -676,6 +676,31 @@ def test_checkpoint_resume_is_bitwise(pf, tmp_path, model, shape, tuning):
         assert np.array_equal(p, q)
 
 
+def test_config_runner_series_checkpoints_and_resume(pf, tmp_path):
+    # a run from a configuration: series every 20 steps, checkpoints every 30; resuming from
+    # the step-30 checkpoint for 30 more steps writes the step-60 checkpoint's bits
+    from paper_2109_02598_gb300 import checkpoint, run
+    cfg = {"grid": {"shape": [128, 128]},
+           "model": {"name": "ch", "coeffs": [1.0, 1.0, 1.0], "dt": 0.01},
+           "init": {"synthetic": "cahn_hilliard_init", "args": {"seed": 67, "amp": 0.3}},
+           "run": {"steps": 60, "tuning": [64, 16, 2], "series_every": 20,
+                   "checkpoint_every": 30, "series_path": str(tmp_path / "a" / "series.json"),
+                   "checkpoint_path": str(tmp_path / "a" / "ckpt_{step}.npz")}}
+    s = run.run(cfg)
+    assert s["steps_done"] == 60 and s["series"] == 4 and len(s["checkpoints"]) == 2
+    series = __import__("json").load(open(tmp_path / "a" / "series.json"))
+    assert [r["step"] for r in series] == [0, 20, 40, 60]
+    assert max(abs(r["mass"][0] - series[0]["mass"][0]) for r in series) <= 1e-6 * 128 * 128
+    cfg2 = dict(cfg, init={"checkpoint": str(tmp_path / "a" / "ckpt_30.npz")},
+                run=dict(cfg["run"], steps=30, series_path=None,
+                         checkpoint_path=str(tmp_path / "b" / "ckpt_{step}.npz")))
+    s2 = run.run(cfg2)
+    assert s2["steps_done"] == 60 and s2["checkpoints"] == [str(tmp_path / "b" / "ckpt_60.npz")]
+    _, a = checkpoint.load_state(str(tmp_path / "a" / "ckpt_60.npz"))
+    _, b = checkpoint.load_state(str(tmp_path / "b" / "ckpt_60.npz"))
+    assert np.array_equal(a[0], b[0])
+
+
 def test_async_host_copies_pipeline_jobs_on_two_grids(pf):
     # the pattern of a caller that overlaps copies with steps: jobs alternate between two
     # grids on two streams, each job uploading, stepping and downloading without waiting;
