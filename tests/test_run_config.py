@@ -39,3 +39,16 @@ def test_rejections(edit, msg):
         msg = "must list"
     with pytest.raises(ConfigError, match=msg):
         validate(c)
+
+
+def test_command_line_reports_configuration_errors(tmp_path, capsys):
+    import json
+
+    from paper_2109_02598_gb300.run import main
+    assert main([]) == 2  # usage
+    bad = base()
+    bad["model"]["name"] = "nope"
+    p = tmp_path / "bad.json"
+    p.write_text(json.dumps(bad))
+    assert main([str(p)]) == 2
+    assert "configuration error" in capsys.readouterr().err
