@@ -272,6 +272,26 @@ def test_full_size_ch2d_mass_conserved(pf):
     assert np.array_equal(phis[0], phis[1])
 
 
+def test_full_length_ch2d_on_the_band_kernel(pf):
+    # the whole Model B configuration (2048^2, 20000 steps) on the kernel the autotuner
+    # picks for it: mass conserved to float32 round-off, the field finite, the free energy
+    # lower than at the start (the scheme is the energy's H^-1 gradient flow)
+    w = synthetic.WORKLOADS["ch2d_2048"]
+    (x0,) = synthetic.workload_init("ch2d_2048")
+    g = pf.Grid(x0.shape, 1, w["h"]).set_model("ch", w["coeffs"], w["dt"])
+    g.set_tuning(2048, pf.PF_TILE_BANDS, 1)
+    g.write_field(0, x0)
+    m0, e0 = g.mass(), g.energy()
+    g.step(w["steps"])
+    m1, e1 = g.mass(), g.energy()
+    phi = g.read_field(0)
+    g.close()
+    assert w["steps"] == 20000
+    assert abs(m1 - m0) / x0.size <= 1e-6
+    assert np.isfinite(phi).all() and np.abs(phi).max() < 1.5
+    assert e1 < e0
+
+
 def test_full_size_gs3d_stays_bounded(pf):
     w = synthetic.WORKLOADS["gs3d_256"]
     x0 = synthetic.workload_init("gs3d_256")
