@@ -293,16 +293,25 @@ def test_full_length_ch2d_on_the_band_kernel(pf):
 
 
 def test_full_size_gs3d_stays_bounded(pf):
+    # the whole 3D Gray-Scott configuration (256^3, 5000 steps) on the default depth-1 TMA
+    # kernel and on the depth-2 kernel the autotuner picks: finite, within [-0.01, 1.01],
+    # and the same bits
     w = synthetic.WORKLOADS["gs3d_256"]
     x0 = synthetic.workload_init("gs3d_256")
-    g = pf.Grid(x0[0].shape, 2, w["h"]).set_model("gs", w["coeffs"], w["dt"])
-    g.write_fields(x0)
-    g.step(500)
-    u, v = g.read_fields()
-    assert np.isfinite(u).all() and np.isfinite(v).all()
-    assert u.min() >= -0.01 and u.max() <= 1.01 and v.min() >= -0.01 and v.max() <= 1.01
-    # far from the seeds the state is still the exact fixed point neighbourhood
-    g.close()
+    out = []
+    for tuning in (None, (256, 8, 2)):
+        g = pf.Grid(x0[0].shape, 2, w["h"]).set_model("gs", w["coeffs"], w["dt"])
+        if tuning:
+            g.set_tuning(*tuning)
+        g.write_fields(x0)
+        g.step(w["steps"])
+        u, v = g.read_fields()
+        g.close()
+        assert np.isfinite(u).all() and np.isfinite(v).all()
+        assert u.min() >= -0.01 and u.max() <= 1.01 and v.min() >= -0.01 and v.max() <= 1.01
+        out.append((u, v))
+    assert w["steps"] == 5000
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 # ---------------------------------------------------------------- invariants on the GPU
