@@ -105,3 +105,32 @@ def test_batch_rejects_unstable_dt(pf):
     from paper_2109_02598_gb300 import PfError
     with pytest.raises(PfError, match="stability"):
         pf.Batch(make_specs([(16, 16)]), 5.0)
+
+
+def test_full_batch_configuration(pf):
+    # the batched configuration itself: 512 instances, sides log-uniform in [64, 512], seeded
+    # F and k. After 1000 steps, four instances (the smallest, the largest and two more) are
+    # within the 1000-step tolerance of the oracle; after 2000 every instance is finite and
+    # within [-0.01, 1.01]
+    specs = synthetic.batch_instances(512, seed=4)
+    b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5)
+    x0 = [synthetic.batch_instance_init(q["n"], i) for i, q in enumerate(specs)]
+    for i, (u, v) in enumerate(x0):
+        b.write(i, 0, u).write(i, 1, v)
+    b.autotune(3)
+    b.run(1000)
+    sides = [q["n"] for q in specs]
+    picks = {int(np.argmin(sides)), int(np.argmax(sides)), 100, 300}
+    for i in picks:
+        coeffs = (0.2, 0.1, specs[i]["F"], specs[i]["k"])
+        ref = oracle.run("gs", x0[i], coeffs, 0.5, 1000)
+        got = (b.read(i, 0), b.read(i, 1))
+        num = np.sqrt(sum(((g.astype(np.float64) - r) ** 2).sum() for g, r in zip(got, ref)))
+        den = np.sqrt(sum((r ** 2).sum() for r in ref))
+        assert num / den <= 1e-3, (i, sides[i], num / den)
+    b.run(1000)
+    for i in range(len(specs)):
+        u, v = b.read(i, 0), b.read(i, 1)
+        assert np.isfinite(u).all() and np.isfinite(v).all(), i
+        assert u.min() >= -0.01 and u.max() <= 1.01 and v.min() >= -0.01 and v.max() <= 1.01, i
+    b.close()
