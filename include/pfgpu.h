@@ -410,11 +410,17 @@ int pf_selftest_wait_timeout(int64_t budget_cycles, void* stream);
  * Scratch: a fixed 4 KiB device array (512 FP64 partial sums) inside the library, which every
  * GPU that loads the library holds until the process exits; the partial count does not grow
  * with the grid, so every grid within the size limits below fits. The first call on a device
- * looks up the array's device address (make that call before any stream capture). All calls
- * share the array and each overwrites all of it before reading it; calls that overlap on the
- * GPU race and may return wrong sums.
+ * looks up the array's device address (make that call before any stream capture). Under
+ * CUDA's lazy module loading (the default) that first call also loads the library's modules
+ * on the device, which allocates device memory for their code and the array and may
+ * synchronise: make one warm-up call before handing the device to an allocator that must
+ * own all of it. The address is cached per device for the process; after cudaDeviceReset
+ * it is stale, so do not call this entry point again after a reset. All calls share the
+ * array and each overwrites all of it before reading it; calls that overlap on the GPU race
+ * and may return wrong sums.
  * Errors: PF_ERR_INVALID_ARG (NULL pointers, sides outside [1, 2^30], pitch < nx, more than
- * 2^36 floats), PF_ERR_CUDA. Calls no cudaMalloc, cudaFree or other allocating routine. */
+ * 2^36 floats, h not finite or <= 0), PF_ERR_CUDA. After the first call on a device it calls
+ * no cudaMalloc, cudaFree or other allocating routine. */
 int pf_reduce_noalloc(int what, int dim, const int64_t* n, int64_t pitch, const float* field,
                       double h, double c1, double c2, double* out_dev, void* stream);
 

@@ -338,9 +338,12 @@ int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stre
     return invalid("n_fields must be 1 or 2 (got %d)", n_fields);
   if (!(h > 0.0) || !std::isfinite(h)) return invalid("h must be finite and > 0");
   const int64_t pitch = (n[0] + 3) / 4 * 4;
-  const int64_t plane = pitch * n[1];
+  const int64_t plane = pitch * n[1];  // <= (2^30 + 3) 2^30: no overflow
+  const int64_t max_elems = (int64_t)1 << 36;
+  if (plane > max_elems || nz > max_elems / plane)  // by division: plane * nz may overflow
+    return invalid("grid too large: %lld x %lld x %lld floats exceed 2^36", (long long)pitch,
+                   (long long)n[1], (long long)nz);
   const int64_t elems = plane * nz;
-  if (elems > ((int64_t)1 << 36)) return invalid("grid too large");
   pf_grid_s* g = new (std::nothrow) pf_grid_s();
   if (g == nullptr) return PF_ERR_OOM;
   g->magic = kGridMagic;

@@ -13,12 +13,18 @@
 // The scratch is a file-scope __device__ array.  In host code its name only stands in
 // for the symbol; its device address is fetched once per device with
 // cudaGetSymbolAddress (with that device current) on the first call made on that device,
-// and cached.  Make that first call before any stream capture.
+// and cached.  Make that first call before any stream capture.  Under CUDA's lazy module
+// loading (the default) that first call is also where the library's modules are loaded on
+// the device, which allocates device memory for their code and for this array and may
+// synchronise; a warm-up call before the caller's allocator takes the device avoids that.
+// The cached address belongs to the device's primary context: after cudaDeviceReset it no
+// longer exists, so this entry point must not be called again in that process.
 //
 // Every call on a device shares the one array.  Each call writes all 512 partials before
 // reading any of them, so no stale contents from the previous call are used and nothing
 // needs clearing; but two calls whose kernels overlap on the GPU (e.g. on two streams
 // without ordering) race on the array and may return wrong sums.
+#include <cmath>
 #include <mutex>
 
 #include "pf_internal.h"
@@ -69,10 +75,13 @@ extern "C" int pf_reduce_noalloc(int what, int dim, const int64_t* n, int64_t pi
                    (long long)n[0], (long long)n[1], (long long)nz);
   if (pitch < n[0]) return invalid("pf_reduce_noalloc: pitch %lld < nx %lld", (long long)pitch,
                                    (long long)n[0]);
-  if (pitch > lim || pitch * n[1] * nz > ((int64_t)1 << 36))
-    return invalid("pf_reduce_noalloc: field of %lld floats exceeds the 2^36 maximum",
-                   (long long)(pitch * n[1] * nz));
-  if (!(h > 0.0)) return invalid("pf_reduce_noalloc: h must be > 0");
+  // pitch, ny, nz <= 2^30 each: pitch * ny fits in int64, and the plane count is compared
+  // by division, so no product can overflow
+  const int64_t max_elems = (int64_t)1 << 36;
+  if (pitch > lim || pitch * n[1] > max_elems || nz > max_elems / (pitch * n[1]))
+    return invalid("pf_reduce_noalloc: field of %lld x %lld x %lld floats exceeds the 2^36 "
+                   "maximum", (long long)pitch, (long long)n[1], (long long)nz);
+  if (!(h > 0.0) || !std::isfinite(h)) return invalid("pf_reduce_noalloc: h must be finite and > 0");
   double* scratch = nullptr;
   if (int rc = scratch_for_current_device(&scratch)) return rc;
   Geom g{};

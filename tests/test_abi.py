@@ -41,6 +41,24 @@ def test_create_grid_rejects_bad_arguments(lib):
     bad = (ctypes.c_int64 * 3)(0, 16, 16)
     assert lib.pf_create_grid(2, bad, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
     assert lib.pf_create_grid(2, n, 1, 1.0, None, None) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_create_grid(2, n, 1, float("inf"), None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+
+
+def test_size_checks_do_not_overflow(lib):
+    """2^30 x 2^30 x 16 floats is 2^64: a check that multiplies the sides wraps to 0 and passes.
+    Both entry points must reject it (before any device work, so this runs without a GPU)."""
+    h = ctypes.c_void_p()
+    big = (ctypes.c_int64 * 3)(1 << 30, 1 << 30, 16)
+    assert lib.pf_create_grid(3, big, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    assert "2^36" in _err(lib)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the call fails validation first
+    out = ctypes.c_void_p(512)
+    rc = lib.pf_reduce_noalloc(_lib.PF_REDUCE_MASS, 3, big, 1 << 30, fake, 1.0, 0.0, 0.0, out, None)
+    assert rc == _lib.PF_ERR_INVALID_ARG and "2^36" in _err(lib)
+    ok = (ctypes.c_int64 * 3)(8, 8, 8)
+    for bad_h in (float("inf"), float("nan"), 0.0, -1.0):
+        rc = lib.pf_reduce_noalloc(_lib.PF_REDUCE_MASS, 3, ok, 8, fake, bad_h, 0.0, 0.0, out, None)
+        assert rc == _lib.PF_ERR_INVALID_ARG and "h must be" in _err(lib)
 
 
 def test_calls_on_null_handle_fail_cleanly(lib):

@@ -69,6 +69,15 @@ def test_noalloc_matches_pf_reduce_on_consecutive_calls(pf):
     ma, eb = ga.mass(), gb.energy()
     assert abs(got[0] - ma) <= 1e-12 * max(1.0, np.abs(a.astype(np.float64)).sum())
     assert abs(got[1] - eb) <= 1e-12 * abs(eb)
+    # the property the entry point exists for: once the first call on the device has run,
+    # further calls take no device memory
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        assert _noalloc(lib, _lib.PF_REDUCE_ENERGY, ga, 0.9, 1.1, out[0:1], stream) == _lib.PF_OK
+        assert _noalloc(lib, _lib.PF_REDUCE_MASS, gb, 0.0, 0.0, out[1:2], stream) == _lib.PF_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
     ga.close()
     gb.close()
 
@@ -87,3 +96,6 @@ def test_noalloc_rejects_bad_sizes(pf):
     rc = lib.pf_reduce_noalloc(_lib.PF_REDUCE_MASS, 2, n, 4, ctypes.c_void_p(field.data_ptr()),
                                1.0, 0.0, 0.0, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == _lib.PF_ERR_INVALID_ARG and b"pitch" in lib.pf_last_error()
+    rc = lib.pf_reduce_noalloc(_lib.PF_REDUCE_MASS, 2, n, 8, ctypes.c_void_p(field.data_ptr()),
+                               float("inf"), 0.0, 0.0, ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == _lib.PF_ERR_INVALID_ARG and b"finite" in lib.pf_last_error()
