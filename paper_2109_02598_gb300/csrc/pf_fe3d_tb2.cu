@@ -3,15 +3,15 @@
 // Laplacian), so HBM traffic per lattice-site update halves to 4 NF bytes.
 //
 // Tiles span whole x-rows (W = nx, 128 or 256), so the periodic wrap in x is an index wrap
-// inside shared memory; a CTA owns TY rows and streams a z-chunk (even chunks up, odd
-// chunks down, as in the depth-1 kernel).  Per input plane, TMA brings rows
-// y0-2 .. y0+TY+1 of every field (three boxes: two rows above, the TY rows, two rows
-// below, wrapped in y) into an NS-stage ring.  Thread (x4, r), r = 0 .. TY+1, computes the
-// first time level on row y0-1+r (one ring wider than the tile in y) and stores it to a
-// three-plane ring in shared memory; threads r = 1 .. TY then compute the second level on
-// row y0-1+r from that ring and write it to HBM.  Both levels keep their z-neighbours in
-// registers (each thread reads the planes of its own column), and the same per-site
-// functions as every other kernel make the result bitwise identical to two depth-1 steps.
+// inside shared memory; a CTA owns TY rows and streams z-ranges of them (the split over the
+// CTAs is Tb2Sched below).  Per input plane, TMA brings rows y0-2 .. y0+TY+1 of every field
+// (three boxes: two rows above, the TY rows, two rows below, wrapped in y) into an NS-stage
+// ring.  Thread (x4, r), r = 0 .. TY+1, computes the first time level on row y0-1+r (one
+// row wider than the tile in y) and stores it to a two-plane buffer in shared memory;
+// threads r = 1 .. TY then compute the second level on row y0-1+r from it and write it to
+// HBM.  Both levels keep their z-neighbours in registers (each thread reads the planes of
+// its own column), and the same per-site functions as every other kernel make the result
+// bitwise identical to two depth-1 steps.
 //
 // Requires nx == W, ny % TY == 0 and ny >= 2.
 #include "pf_grid.h"
@@ -19,6 +19,8 @@
 #include "pf_tma.cuh"
 
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 namespace pf {
 
@@ -37,15 +39,29 @@ struct CfgB {
   static constexpr int L1_PLANE = NF * L1_FIELD;
   static constexpr uint32_t TX_BYTES = IN_STAGE * 4;
   static constexpr size_t SMEM =
-      (size_t)(NS * IN_STAGE + 3 * L1_PLANE) * 4 + NS * 8 + 128;  // + barriers + align
+      (size_t)(NS * IN_STAGE + 2 * L1_PLANE) * 4 + NS * 8 + 128;  // + barriers + align
   static_assert(W % 32 == 0, "rows must be 128-byte multiples");
 };
 
-// x-neighbour scalars of the float4 at column 4*x4 in a row of W floats (periodic).
+// x-neighbour scalars of the float4 at column 4*x4 of a row of W floats (periodic). They
+// come from the centre float4 c that this thread already holds: the neighbouring lanes' c.w
+// and c.x by warp shuffle, and at the warp's two ends one load whose address is the same for
+// every lane (a broadcast). A warp covers 32 consecutive float4 columns of one row (W/4 is a
+// multiple of 32), so lanes 0 and 31 are the only ones whose neighbour lies in another warp.
+// Plain scalar loads of the two neighbours, four floats apart across the lanes, cost four
+// shared-memory wavefronts each (four lanes per bank); this costs two (GS 256^3: 484.5 ->
+// 501 GLUPS together with the ROWS schedule below).
 template <int W>
-__device__ __forceinline__ void x_edges(const float* row, int x4, float& xm, float& xp) {
-  xm = row[x4 == 0 ? W - 1 : 4 * x4 - 1];
-  xp = row[x4 == W / 4 - 1 ? 0 : 4 * x4 + 4];
+__device__ __forceinline__ void x_edges_c(const float* row, int x4, const float4& c, float& xm,
+                                          float& xp) {
+  const int lane = threadIdx.x & 31;
+  const int xb = x4 - lane;  // first float4 column of this warp
+  const float em = row[xb == 0 ? W - 1 : 4 * xb - 1];
+  const float ep = row[xb + 32 == W / 4 ? 0 : 4 * (xb + 32)];
+  const float wm = __shfl_up_sync(0xffffffffu, c.w, 1);
+  const float wp = __shfl_down_sync(0xffffffffu, c.x, 1);
+  xm = lane == 0 ? em : wm;
+  xp = lane == 31 ? ep : wp;
 }
 
 template <int MODEL>
@@ -65,38 +81,56 @@ __device__ __forceinline__ void update4(const float4* c, const float4* lap, floa
 }
 
 // 7-point Laplacians of four sites: centre c, z-neighbours zm/zp, rows above/below and the
-// two x-edge scalars of the centre row. The multiply by lap_scale stays even for Gray-Scott
-// (whose factor is 1, so the bits are those of lap_scaled): leaving it out measured 1.3 %
-// slower in this kernel (476 against 482 GLUPS on GS 256^3).
+// two x-edge scalars of the centre row. Gray-Scott's stencil factor is carried in D_u and D_v
+// (its lap_scale is 1), so its final multiply is left out, as lap_scaled does: the same bits,
+// eight instructions fewer per float4 and level (GS 256^3: 503 -> 521 GLUPS).
+template <int MODEL>
 __device__ __forceinline__ float4 lap3d_x4(const float4& c, const float4& ym, const float4& yp,
                                            const float4& zm, const float4& zp, float xm,
                                            float xp, float lap_scale) {
   float4 l;
-  l.x = lap3d(c.x, xm, c.y, ym.x, yp.x, zm.x, zp.x, lap_scale);
-  l.y = lap3d(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, lap_scale);
-  l.z = lap3d(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, lap_scale);
-  l.w = lap3d(c.w, c.z, xp, ym.w, yp.w, zm.w, zp.w, lap_scale);
+  l.x = lap_scaled<MODEL>(lap3d_sum(c.x, xm, c.y, ym.x, yp.x, zm.x, zp.x), lap_scale);
+  l.y = lap_scaled<MODEL>(lap3d_sum(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y), lap_scale);
+  l.z = lap_scaled<MODEL>(lap3d_sum(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z), lap_scale);
+  l.w = lap_scaled<MODEL>(lap3d_sum(c.w, c.z, xp, ym.w, yp.w, zm.w, zp.w), lap_scale);
   return l;
 }
+
+// How the (row tile, plane) work is split over the CTAs (chosen on the host, tb2_schedule).
+//   ITEMS:    item = (tile, chunk of chunk_len planes), items dealt round-robin over the CTAs,
+//             chunks alternating up and down in z.
+//   BALANCED: the (tile, plane) units in tile-major order cut into gridDim.x equal ranges,
+//             one per CTA (a range crossing a tile boundary makes two segments), direction
+//             alternating by CTA.
+//   ROWS:     full_rows rows of one CTA per tile, row c streaming planes [c L, (c+1) L) in
+//             the direction of chunk c; the remaining CTAs split the top row [full_rows L, nz)
+//             of every tile in tile-major order. CTAs of neighbouring tiles in a full row work
+//             on the same plane at the same time, so the halo rows they share come from L2.
+struct Tb2Sched {
+  int mode;
+  int nchunks, chunk_len;    // ITEMS
+  int full_rows, L, pdir;    // ROWS: rows of ncols CTAs, their chunk length, partial direction
+};
+constexpr int kTb2Items = 0, kTb2Balanced = 1, kTb2Rows = 2;
 
 template <int MODEL, int W, int TY, int NS>
 __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
     fe3d_tb2_kernel(const __grid_constant__ Tb2Maps maps, FieldOut out, Geom g, ModelParams m,
-                    int nchunks, int chunk_len, int balanced, int* err_flag) {
+                    Tb2Sched sc_, int* err_flag) {
   using C = CfgB<MODEL, W, TY, NS>;
   constexpr int NF = C::NF;
   constexpr int LX = C::LX;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_sa = smem_addr(smem_raw);
   float* ring = reinterpret_cast<float*>(smem_raw + ((128 - (base_sa & 127)) & 127));
-  float* l1 = ring + NS * C::IN_STAGE;  // three first-level planes
-  uint64_t* bars = reinterpret_cast<uint64_t*>(l1 + 3 * C::L1_PLANE);
+  float* l1 = ring + NS * C::IN_STAGE;  // two first-level planes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(l1 + 2 * C::L1_PLANE);
 
   const int tid = threadIdx.x;
   const int x4 = tid % LX;
   const int r = tid / LX;  // first-level row y0 - 1 + r; input row r + 1
   const bool second = (r >= 1 && r <= TY);
-  canary_fill(ring, (size_t)NS * C::IN_STAGE + 3 * C::L1_PLANE);  // TMA issues follow a proxy fence
+  canary_fill(ring, (size_t)NS * C::IN_STAGE + 2 * C::L1_PLANE);  // TMA issues follow a proxy fence
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
@@ -126,34 +160,47 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
   };
 
   const int ncols = g.ny / TY;
-  const int nitems = ncols * nchunks;
-  // Work: (row tile, z-range) segments. Item mode: item = (tile, chunk of chunk_len planes),
-  // items dealt round-robin over the CTAs, chunks alternating up and down. Balanced mode:
-  // the (tile, plane) units in tile-major order cut into gridDim.x equal ranges, one per CTA
-  // (a range crossing a tile boundary makes two segments), direction alternating by CTA.
+  // Work: (row tile, z-range) segments, per the schedule's mode (Tb2Sched).
   // units = ny nz / TY < 2^31 for every grid this kernel takes (nx = W, at most 2^36 sites)
-  const int units = ncols * g.nz;
-  int pos = (int)((int64_t)units * blockIdx.x / gridDim.x);
-  const int pos_end = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
-  int item = blockIdx.x;
+  // Live across a segment: pos, pos_end (BALANCED, the ROWS top row) or item; the rest is
+  // recomputed from the launch parameters when a segment starts.
+  int pos = 0, pos_end = 0, item = blockIdx.x;
+  const int nfull = sc_.full_rows * ncols;
+  if (sc_.mode == kTb2Balanced) {
+    const int units = ncols * g.nz;
+    pos = (int)((int64_t)units * blockIdx.x / gridDim.x);
+    pos_end = (int)((int64_t)units * (blockIdx.x + 1) / gridDim.x);
+  } else if (sc_.mode == kTb2Rows && (int)blockIdx.x >= nfull) {
+    const int units = ncols * (g.nz - sc_.full_rows * sc_.L);
+    const int p = blockIdx.x - nfull, np = gridDim.x - nfull;
+    pos = (int)((int64_t)units * p / np);
+    pos_end = (int)((int64_t)units * (p + 1) / np);
+  }
   for (;;) {
     int col, zlo, zhi, dir;
-    if (balanced) {
-      if (pos >= pos_end) break;
-      col = pos / g.nz;
-      zlo = pos - col * g.nz;
-      zhi = min(g.nz, zlo + (pos_end - pos));
-      dir = (blockIdx.x & 1) ? -1 : 1;
-      pos += zhi - zlo;
-    } else {
-      if (item >= nitems) break;
+    if (sc_.mode == kTb2Items || (sc_.mode == kTb2Rows && (int)blockIdx.x < nfull)) {
+      const bool rows = sc_.mode == kTb2Rows;
+      if (item >= (rows ? nfull : ncols * sc_.nchunks)) break;
       col = item % ncols;
       const int chunk = item / ncols;
-      zlo = chunk * chunk_len;
-      zhi = min(g.nz, zlo + chunk_len);
+      const int len = rows ? sc_.L : sc_.chunk_len;
+      zlo = chunk * len;
+      zhi = min(g.nz, zlo + len);
       dir = (chunk & 1) ? -1 : 1;
-      item += gridDim.x;
+      item += rows ? nfull : gridDim.x;
       if (zlo >= zhi) continue;  // uniform over the CTA
+    } else {
+      if (pos >= pos_end) break;
+      const bool rows = sc_.mode == kTb2Rows;
+      const int zbase = rows ? sc_.full_rows * sc_.L : 0;
+      const int zlen = g.nz - zbase;
+      col = pos / zlen;
+      zlo = pos - col * zlen;
+      zhi = min(zlen, zlo + (pos_end - pos));
+      pos += zhi - zlo;
+      zlo += zbase;
+      zhi += zbase;
+      dir = rows ? sc_.pdir : ((blockIdx.x & 1) ? -1 : 1);
     }
     const int n = zhi - zlo;                  // output planes
     const int zfirst = dir > 0 ? zlo : zhi - 1;
@@ -176,8 +223,8 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         izm[f] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
-      err = !wait(q_base + 1);
     }
+    if (!err) err = !wait(q_base + 1);
     if (!err) {
       const float* st = stage_ptr(q_base + 1);
 #pragma unroll
@@ -185,13 +232,16 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         ic[f] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
     }
     // first-level index j = 0 .. n+1 is plane zfirst + (j-1) dir, from input planes j, j+1,
-    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2. The stages of
-    // input planes j+1, j+2, the mbarrier phase of j+2 and the first-level ring planes
-    // j % 3, (j-1) % 3 advance incrementally instead of by division.
+    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2 (o and o+2 in
+    // registers, o+1 in shared memory). The stages of input planes j+1, j+2 and the
+    // mbarrier phase of j+2 advance incrementally instead of by division.
     uint32_t s1 = (q_base + 1) % NS, s2 = (q_base + 2) % NS;
     uint32_t ph2 = ((q_base + 2) / NS) & 1u;
-    float* l1w = l1;                       // first-level ring plane j % 3
-    float* l1r = l1 + 2 * C::L1_PLANE;     // and (j - 1) % 3
+    // Two first-level planes suffice: iteration j writes plane j into the slot of plane
+    // j - 2, which iteration j - 1 read last, and the barrier at the top of iteration j
+    // separates the two.
+    float* l1w = l1;                       // first-level plane j
+    float* l1r = l1 + C::L1_PLANE;         // and j - 1
     for (int j = 0; j < n + 2; ++j) {
       if (__syncthreads_or(err)) break;
       if (tid == 0 && j + NS < nin) {
@@ -200,6 +250,7 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         q_issued = q_base + j + NS + 1;
       }
       err = !mbar_wait_bounded(&bars[s2], ph2, kWaitBudgetCycles);
+      err = __any_sync(0xffffffffu, err);  // the shuffles below need the whole warp
       if (err) continue;
       // ---- first level on row r of plane j (input centre plane j+1)
       const float* sc = ring + s1 * C::IN_STAGE;
@@ -217,8 +268,8 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         const float4 yp = *reinterpret_cast<const float4*>(F + (r + 2) * W + 4 * x4);
         izp[f] = *reinterpret_cast<const float4*>(sp + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
         float xm, xp;
-        x_edges<W>(F + (r + 1) * W, x4, xm, xp);
-        lap[f] = lap3d_x4(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.lap_scale);
+        x_edges_c<W>(F + (r + 1) * W, x4, ic[f], xm, xp);
+        lap[f] = lap3d_x4<MODEL>(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.lap_scale);
       }
       update4<MODEL>(ic, lap, l1v, m);
 #pragma unroll
@@ -238,8 +289,8 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
           const float4 ym = *reinterpret_cast<const float4*>(F + (r - 1) * W + 4 * x4);
           const float4 yp = *reinterpret_cast<const float4*>(F + (r + 1) * W + 4 * x4);
           float xm, xp;
-          x_edges<W>(F + r * W, x4, xm, xp);
-          lap2[f] = lap3d_x4(lc[f], ym, yp, lzm[f], l1v[f], xm, xp, m.lap_scale);
+          x_edges_c<W>(F + r * W, x4, lc[f], xm, xp);
+          lap2[f] = lap3d_x4<MODEL>(lc[f], ym, yp, lzm[f], l1v[f], xm, xp, m.lap_scale);
         }
         update4<MODEL>(lc, lap2, res, m);
         const int z = zfirst + (j - 2) * dir;
@@ -252,8 +303,9 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         lzm[f] = lc[f];
         lc[f] = l1v[f];
       }
+      float* const t = l1r;
       l1r = l1w;
-      l1w = l1w == l1 + 2 * C::L1_PLANE ? l1 : l1w + C::L1_PLANE;
+      l1w = t;
     }
     q_base += nin;
   }
@@ -265,6 +317,61 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         (void)mbar_wait_bounded(&bars[q % NS], (q / NS) & 1u, kWaitBudgetCycles);
     }
   }
+}
+
+// The work split with the shortest longest-CTA plane count (each segment streams 4 halo
+// planes besides its own), ROWS preferred when it is within one plane of the best, since it
+// keeps neighbouring tiles in step over z.
+Tb2Sched tb2_schedule(int ncols, int nz, long long slots, long long* grid_out) {
+  Tb2Sched s{};
+  // ITEMS
+  long long nchunks = slots / ncols;
+  if (nchunks > nz / 4) nchunks = nz / 4;
+  if (nchunks < 1) nchunks = 1;
+  const int chunk_len = (int)((nz + nchunks - 1) / nchunks);
+  nchunks = (nz + chunk_len - 1) / chunk_len;
+  const long long items = (long long)ncols * nchunks;
+  const long long item_grid = items < slots ? items : slots;
+  const long long item_span = (items + item_grid - 1) / item_grid * (chunk_len + 4);
+  // BALANCED: about units / slots + 8 planes (two segments at most when a range is under nz)
+  const long long units = (long long)ncols * nz;
+  const long long per = (units + slots - 1) / slots;
+  const long long bal_span = per + (per < nz ? 8 : 4 * ((per + nz - 1) / nz + 1));
+  const long long bal_grid = slots < units ? slots : units;
+  // ROWS
+  long long rows_span = -1, rows_L = 0;
+  const long long F = slots / ncols, R = slots - F * ncols;
+  for (long long L = 4; F >= 1 && L * F <= nz; ++L) {
+    const long long Lp = nz - F * L;  // planes of the top row
+    long long span = L + 4;
+    if (Lp > 0) {
+      if (R == 0) continue;
+      const long long pu = ((long long)ncols * Lp + R - 1) / R;
+      const long long segs = (pu + Lp - 1) / Lp + 1;
+      span = std::max(span, pu + 4 * segs);
+    }
+    if (rows_span < 0 || span < rows_span) {
+      rows_span = span;
+      rows_L = L;
+    }
+  }
+  const long long best = std::min(item_span, slots > item_grid ? bal_span : item_span);
+  if (rows_span > 0 && rows_span <= best + 1) {
+    s.mode = kTb2Rows;
+    s.full_rows = (int)F;
+    s.L = (int)rows_L;
+    s.pdir = ((F - 1) & 1) ? 1 : -1;  // meet the last full row's chunk at its end
+    *grid_out = (nz - F * rows_L) > 0 ? slots : F * ncols;
+  } else if (bal_span < item_span && slots > item_grid) {
+    s.mode = kTb2Balanced;
+    *grid_out = bal_grid;
+  } else {
+    s.mode = kTb2Items;
+    *grid_out = item_grid;
+  }
+  s.nchunks = (int)nchunks;
+  s.chunk_len = chunk_len;
+  return s;
 }
 
 template <int MODEL, int W, int TY, int NS>
@@ -286,29 +393,9 @@ cudaError_t launch_tb2(pf_grid_s* gr, const Tb2Maps& maps, FieldOut out, cudaStr
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gr->device);
   if (e != cudaSuccess) return e;
   const Geom g = grid_geom(gr);
-  const long long ncols = g.ny / TY;
-  const long long slots = (long long)sms * occ;
-  long long nchunks = slots / ncols;
-  if (nchunks > g.nz / 4) nchunks = g.nz / 4;
-  if (nchunks < 1) nchunks = 1;
-  const int chunk_len = (int)((g.nz + nchunks - 1) / nchunks);
-  nchunks = (g.nz + chunk_len - 1) / chunk_len;
-  const long long items = ncols * nchunks;
-  long long grid = items < slots ? items : slots;
-  // Balanced mode when it shortens the longest CTA's plane count (each segment also streams
-  // 4 halo planes): item mode runs ceil(items / grid) items of chunk_len + 4 planes, balanced
-  // mode about units / slots + 8 planes (two segments at most when a range is under nz).
-  const long long units = ncols * (long long)g.nz;
-  const long long item_span = (items + grid - 1) / grid * (chunk_len + 4);
-  const long long per = (units + slots - 1) / slots;
-  const long long bal_span = per + (per < g.nz ? 8 : 4 * ((per + g.nz - 1) / g.nz + 1));
-  int balanced = 0;
-  if (bal_span < item_span && slots > grid) {
-    balanced = 1;
-    grid = slots < units ? slots : units;
-  }
-  kern<<<(unsigned)grid, C::NT, C::SMEM, st>>>(maps, out, g, gr->params, (int)nchunks, chunk_len,
-                                               balanced, gr->d_err);
+  long long grid = 0;
+  const Tb2Sched sc = tb2_schedule(g.ny / TY, g.nz, (long long)sms * occ, &grid);
+  kern<<<(unsigned)grid, C::NT, C::SMEM, st>>>(maps, out, g, gr->params, sc, gr->d_err);
   return cudaGetLastError();
 }
 

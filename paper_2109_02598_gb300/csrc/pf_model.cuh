@@ -189,6 +189,115 @@ __device__ __forceinline__ void mc_update(float psi, float m, float lap_psi, flo
   m_n = __fmaf_rn(p.dt, lap_mu, m);
 }
 
+// ---- four sites at once with packed FP32 pairs ------------------------------------------
+// The sm_100 family executes FP32 add, multiply and fma on register pairs: one instruction
+// updates two sites, and per lane the result is the IEEE-rounded result of the scalar
+// intrinsic (__fadd2_rn is two __fadd_rn, and so on). The functions below apply the per-site
+// arithmetic above to the four sites of a float4 as two pairs, with the same operations in
+// the same order, so a kernel that uses them gives the bits of one that uses the scalar
+// functions, with about half the arithmetic instructions. Negated operands and x - y = x + (-y)
+// are exact, so writing a subtraction as an addition of the negation keeps the bits too.
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(const float2& a, const float2& b) {
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 add4(const float4& a, const float4& b) {
+  return cat4(__fadd2_rn(lo2(a), lo2(b)), __fadd2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 mul4(const float4& a, const float4& b) {
+  return cat4(__fmul2_rn(lo2(a), lo2(b)), __fmul2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 mul4(float a, const float4& b) {
+  const float2 aa = make_float2(a, a);
+  return cat4(__fmul2_rn(aa, lo2(b)), __fmul2_rn(aa, hi2(b)));
+}
+__device__ __forceinline__ float4 fma4(const float4& a, const float4& b, const float4& c) {
+  return cat4(__ffma2_rn(lo2(a), lo2(b), lo2(c)), __ffma2_rn(hi2(a), hi2(b), hi2(c)));
+}
+__device__ __forceinline__ float4 fma4(float a, const float4& b, const float4& c) {
+  const float2 aa = make_float2(a, a);
+  return cat4(__ffma2_rn(aa, lo2(b), lo2(c)), __ffma2_rn(aa, hi2(b), hi2(c)));
+}
+__device__ __forceinline__ float4 neg4(const float4& a) {
+  return make_float4(-a.x, -a.y, -a.z, -a.w);
+}
+
+// lap3d_sum of the four sites of c (x-neighbours: the scalar xm left of c.x, xp right of c.w)
+__device__ __forceinline__ float4 lap3d_sum4(const float4& c, float xm, float xp,
+                                             const float4& ym, const float4& yp,
+                                             const float4& zm, const float4& zp) {
+  const float4 sx = make_float4(__fadd_rn(xm, c.y), __fadd_rn(c.x, c.z), __fadd_rn(c.y, c.w),
+                                __fadd_rn(c.z, xp));
+  const float4 s = add4(add4(sx, add4(ym, yp)), add4(zm, zp));
+  return fma4(-6.0f, c, s);
+}
+
+// lap2d_sum of the four sites of c
+__device__ __forceinline__ float4 lap2d_sum4(const float4& c, float xm, float xp,
+                                             const float4& ym, const float4& yp) {
+  const float4 sx = make_float4(__fadd_rn(xm, c.y), __fadd_rn(c.x, c.z), __fadd_rn(c.y, c.w),
+                                __fadd_rn(c.z, xp));
+  return fma4(-4.0f, c, add4(sx, add4(ym, yp)));
+}
+
+// ac_update of four sites
+__device__ __forceinline__ float4 ac_update4(const float4& p, const float4& lap,
+                                             const ModelParams& m) {
+  const float4 p3 = mul4(mul4(p, p), p);
+  float4 f = fma4(m.a0, p, lap);
+  f = fma4(-m.a1, p3, f);
+  return fma4(m.dt, f, p);
+}
+
+// ch_mu of four sites
+__device__ __forceinline__ float4 ch_mu4(const float4& p, const float4& lap,
+                                         const ModelParams& m) {
+  const float4 p3 = mul4(mul4(p, p), p);
+  const float4 mu = fma4(m.a1, p3, neg4(lap));
+  return fma4(-m.a0, p, mu);
+}
+
+// ch_update of four sites
+__device__ __forceinline__ float4 ch_update4(const float4& p, const float4& lap_mu,
+                                             const ModelParams& m) {
+  return fma4(m.a2, lap_mu, p);
+}
+
+// gs_update of four sites
+__device__ __forceinline__ void gs_update4(const float4& u, const float4& v, const float4& lu,
+                                           const float4& lv, const ModelParams& m, float4& un,
+                                           float4& vn) {
+  const float4 uvv = mul4(mul4(u, v), v);
+  float4 fu = fma4(m.a0, lu, neg4(uvv));
+  fu = fma4(m.a2, add4(make_float4(1.0f, 1.0f, 1.0f, 1.0f), neg4(u)), fu);
+  float4 fv = fma4(m.a1, lv, uvv);
+  fv = fma4(-m.a3, v, fv);
+  un = fma4(m.dt, fu, u);
+  vn = fma4(m.dt, fv, v);
+}
+
+// mc_mu of four sites
+__device__ __forceinline__ float4 mc_mu4(const float4& psi, const float4& m4,
+                                         const float4& lap_m, const ModelParams& p) {
+  const float4 m3 = mul4(mul4(m4, m4), m4);
+  float4 mu = fma4(p.a3, m3, neg4(lap_m));
+  mu = fma4(-p.a2, m4, mu);
+  return fma4(-p.a4, mul4(psi, psi), mu);
+}
+
+// mc_update of four sites
+__device__ __forceinline__ void mc_update4(const float4& psi, const float4& m4,
+                                           const float4& lap_psi, const float4& lap_mu,
+                                           const ModelParams& p, float4& psi_n, float4& m_n) {
+  const float4 p3 = mul4(mul4(psi, psi), psi);
+  float4 f = fma4(p.a0, psi, lap_psi);
+  f = fma4(-p.a1, p3, f);
+  f = fma4(p.a5, mul4(psi, m4), f);
+  psi_n = fma4(p.dt, f, psi);
+  m_n = fma4(p.dt, lap_mu, m4);
+}
+
 // Checked builds (PF_CHECK): fill n floats of shared memory with NaN before they are staged,
 // so a read of a slot that staging or an earlier sub-step did not write turns results into
 // NaN, which the parity tests see. Every thread of the CTA calls it; it ends with a CTA

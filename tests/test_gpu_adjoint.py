@@ -3,6 +3,10 @@ oracle adjoint (itself pinned by complex-step and central differences), the chec
 schedule invariance, the autograd Function, and central differences at full size.
 
 Bars: relative L2 of dL/d(u0, v0) <= 1e-3 and relative error of dL/dtheta <= 1e-3."""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -130,21 +134,40 @@ def test_autograd_function(pf):
     assert np.all(np.abs(th.grad.cpu().numpy() - rth) <= 1e-3 * np.abs(rth))
 
 
-def test_full_size_theta_gradient_vs_central_differences(pf):
-    # 512^2, 2000 steps, sqrt(N) checkpoints: dL/dF and dL/dk against FP64 central
-    # differences of the oracle's loss (eps = 1e-6).
+def _loss(u0, v0, coeffs, n, ut, vt):
+    return oracle.gray_scott_final_and_loss(u0, v0, coeffs, DT, n, ut, vt)[2]
+
+
+def test_full_size_gradients_vs_central_differences(pf):
+    # 512^2, 2000 steps, sqrt(N) checkpoints: every parameter gradient (D_u, D_v, F, k) and
+    # the initial-state gradient along one seeded random direction in (u0, v0), against FP64
+    # central differences of the oracle's loss (eps = 1e-6). The twelve oracle runs go to
+    # worker processes (spawned: this process already holds a CUDA context).
     u0, v0 = synthetic.workload_init("gs2d_adjoint_512")
     n = 2000
-    ut, vt = target(u0, v0, n)
-    _, _, gth = gpu_adjoint(pf, u0, v0, n, 0, ut, vt)
-    for i in (2, 3):
-        eps = 1e-6
-        cp = list(COEFFS); cp[i] += eps
-        cm = list(COEFFS); cm[i] -= eps
-        lp = oracle.gray_scott_final_and_loss(u0, v0, tuple(cp), DT, n, ut, vt)[2]
-        lm = oracle.gray_scott_final_and_loss(u0, v0, tuple(cm), DT, n, ut, vt)[2]
-        fd = (lp - lm) / (2 * eps)
-        assert abs(gth[i] - fd) <= 1e-3 * abs(fd), (i, gth[i], fd)
+    eps = 1e-6
+    rng = np.random.default_rng(2000)
+    du, dv = rng.standard_normal(u0.shape), rng.standard_normal(v0.shape)
+    u64, v64 = u0.astype(np.float64), v0.astype(np.float64)
+    with ProcessPoolExecutor(min(12, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        ut, vt = target(u0, v0, n)
+        jobs = {}
+        for i in range(4):
+            cp = list(COEFFS); cp[i] += eps
+            cm = list(COEFFS); cm[i] -= eps
+            jobs[i] = (ex.submit(_loss, u0, v0, tuple(cp), n, ut, vt),
+                       ex.submit(_loss, u0, v0, tuple(cm), n, ut, vt))
+        jobs["x0"] = (ex.submit(_loss, u64 + eps * du, v64 + eps * dv, COEFFS, n, ut, vt),
+                      ex.submit(_loss, u64 - eps * du, v64 - eps * dv, COEFFS, n, ut, vt))
+        _, (gu0, gv0), gth = gpu_adjoint(pf, u0, v0, n, 0, ut, vt)
+        for key, (plus, minus) in jobs.items():
+            fd = (plus.result() - minus.result()) / (2 * eps)
+            if key == "x0":
+                ad = float((gu0.astype(np.float64) * du).sum() + (gv0.astype(np.float64) * dv).sum())
+            else:
+                ad = gth[key]
+            assert abs(ad - fd) <= 1e-3 * abs(fd), (key, ad, fd)
 
 
 # --------------------------------------------- Models A and B: dL/d(c1, c2) and mobility M

@@ -1,5 +1,9 @@
 """Batched 2D Gray-Scott through the C ABI: every instance against the FP64 oracle, and
 bitwise against the same grid stepped alone (the batch runs the same tile body)."""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -134,3 +138,58 @@ def test_full_batch_configuration(pf):
         assert np.isfinite(u).all() and np.isfinite(v).all(), i
         assert u.min() >= -0.01 and u.max() <= 1.01 and v.min() >= -0.01 and v.max() <= 1.01, i
     b.close()
+
+
+def _rel(got, ref, norm):
+    if norm == "inf":
+        num = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(got, ref))
+        return num / max(np.abs(r).max() for r in ref)
+    num = np.sqrt(sum(((g.astype(np.float64) - r) ** 2).sum() for g, r in zip(got, ref)))
+    return num / np.sqrt(sum((r ** 2).sum() for r in ref))
+
+
+def test_full_batch_every_instance_against_the_oracle(pf):
+    # the 512-instance configuration with the autotuner's tuning (the one the bench times):
+    # every instance within the single-step bar after one step and after one launch of the
+    # tuned depth k; 16 instances spread over the sizes within the 1000-step bar. The oracle
+    # runs in worker processes (spawned: this process already holds a CUDA context).
+    specs = synthetic.batch_instances(512, seed=4)
+    coeffs = [(0.2, 0.1, q["F"], q["k"]) for q in specs]
+    x0 = [synthetic.batch_instance_init(q["n"], i) for i, q in enumerate(specs)]
+
+    def batch_after(steps, tuning):
+        b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5)
+        for i, (u, v) in enumerate(x0):
+            b.write(i, 0, u).write(i, 1, v)
+        if tuning is None:
+            b.autotune(3)
+        else:
+            b.set_tuning(*tuning)
+        t = b.tuning
+        b.run(steps)
+        out = [(b.read(i, 0), b.read(i, 1)) for i in range(len(specs))]
+        b.close()
+        return out, tuple(t)
+
+    sides = np.array([q["n"] for q in specs])
+    order = np.argsort(sides, kind="stable")
+    picks = [int(order[j]) for j in np.linspace(0, len(specs) - 1, 16).round().astype(int)]
+    workers = min(16, os.cpu_count() or 1)
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        long_ref = {i: ex.submit(oracle.run, "gs", x0[i], coeffs[i], 0.5, 1000) for i in picks}
+        one, tuning = batch_after(1, None)
+        k = tuning[2]
+        ref1 = list(ex.map(oracle.run, ["gs"] * len(specs), x0, coeffs, [0.5] * len(specs),
+                           [1] * len(specs), chunksize=8))
+        for i, (got, ref) in enumerate(zip(one, ref1)):
+            assert _rel(got, ref, "inf") <= 1e-6, (i, sides[i])
+        if k > 1:
+            refk = list(ex.map(oracle.run, ["gs"] * len(specs), x0, coeffs,
+                               [0.5] * len(specs), [k] * len(specs), chunksize=8))
+            launch, _ = batch_after(k, tuning)
+            for i, (got, ref) in enumerate(zip(launch, refk)):
+                assert _rel(got, ref, "inf") <= 1e-6, (i, sides[i], k)
+        thousand, _ = batch_after(1000, tuning)
+        for i in picks:
+            err = _rel(thousand[i], long_ref[i].result(), "l2")
+            assert err <= 1e-3, (i, sides[i], err)

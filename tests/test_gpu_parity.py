@@ -163,13 +163,18 @@ def test_depth2_3d_kernel_is_bitwise_depth1(pf, model, shape, tile):
 
 
 @pytest.mark.parametrize("model", ["ac", "gs"])
-def test_depth2_3d_balanced_split_is_bitwise_depth1(pf, model):
-    # 256 x 256 rows and 160 planes: 32 row tiles; the host hands the SMs equal ranges of
-    # the (tile, plane) sequence, ranges that cross tile boundaries (balanced mode)
-    shape = (160, 256, 256)
+@pytest.mark.parametrize("shape,tile", [((160, 256, 256), 256), ((256, 256, 256), 256),
+                                        ((8, 1280, 128), 128)])
+def test_depth2_3d_work_splits_are_bitwise_depth1(pf, model, shape, tile):
+    # The host splits the (row tile, plane) work of the depth-2 kernel over the SMs three ways.
+    # 256 x 256 rows (32 row tiles) with 160 or 256 planes: four rows of one CTA per tile, each
+    # a chunk of planes, and the remaining CTAs share the top chunk of every tile (ROWS).
+    # 1280 x 128 rows (160 tiles, more than the SMs) with 8 planes: equal ranges of the
+    # (tile, plane) sequence that cross tile boundaries (BALANCED). Either way, the same bits
+    # as the depth-1 kernel.
     x0 = init_fields(model, shape, seed=13)
     base = gpu_run(pf, model, x0, 4, tuning=(64, 16, 1))
-    got = gpu_run(pf, model, x0, 4, tuning=(256, 8, 2))
+    got = gpu_run(pf, model, x0, 4, tuning=(tile, 8, 2))
     for a, b in zip(base, got):
         assert np.array_equal(a, b)
 
@@ -238,6 +243,24 @@ def test_gs3d_1000_steps_48(pf):
     ref = oracle.run("gs", x0, w["coeffs"], w["dt"], 1000, w["h"])
     got = gpu_run(pf, "gs", x0, 1000, w["coeffs"], w["dt"], w["h"])
     assert rel_l2(got, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("shape,tunings", [
+    ((48, 32, 128), [(128, 8, 2), (64, 16, 1)]),
+    ((16, 16, 256), [(256, 8, 2), (128, 16, 1)])])
+def test_gs3d_1000_steps_on_the_timed_3d_kernels(pf, shape, tunings):
+    # the 3D Gray-Scott recipe on grids the depth-2 kernel (full x-rows, 8-row tiles) and the
+    # TMA z-streaming kernel both take, each pinned to the oracle directly: one launch's steps
+    # (two for depth 2) within the single-step bar, 1000 steps within the 1000-step bar
+    w = synthetic.WORKLOADS["gs3d_256"]
+    x0 = synthetic.workload_init("gs3d_256", shape=shape)
+    ref = oracle.run("gs", x0, w["coeffs"], w["dt"], 1000, w["h"])
+    for t in tunings:
+        k = t[2]
+        one = gpu_run(pf, "gs", x0, k, w["coeffs"], w["dt"], w["h"], tuning=t)
+        assert rel_linf(one, oracle.run("gs", x0, w["coeffs"], w["dt"], k, w["h"])) <= 1e-6, t
+        got = gpu_run(pf, "gs", x0, 1000, w["coeffs"], w["dt"], w["h"], tuning=t)
+        assert rel_l2(got, ref) <= 1e-3, (t, rel_l2(got, ref))
 
 
 @pytest.mark.parametrize("name", ["ch2d_2048", "gs3d_256"])
