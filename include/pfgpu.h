@@ -331,13 +331,16 @@ int pf_spectral_synchronize(pf_spectral_t s);
 
 /* Engines of pf_spectral_step; both compute the same scheme (float32, to rounding):
  *   PF_SPECTRAL_ENGINE_CUFFT  cuFFT transforms with this library's kernels between them;
- *   PF_SPECTRAL_ENGINE_FUSED  2D grids with power-of-two sides in [4, 1024]: the whole run
- *                             in one cooperative launch, two phases per step (rows: inverse
- *                             x transform, nonlinear terms, forward x transform; columns:
- *                             forward y transform, update, inverse y transform) with this
- *                             library's shared-memory FFTs and a bounded grid barrier;
- *   PF_SPECTRAL_ENGINE_AUTO   (default) fused where it was measured faster: sides up to 256,
- *                             and one-field models up to 512; else cuFFT. */
+ *   PF_SPECTRAL_ENGINE_FUSED  power-of-two sides, nx in [4, 1024], in 2D ny <= 1024 and in 3D
+ *                             a (y, z) slab that fits one CTA's shared memory (64 x 64 and
+ *                             the like): the whole run in one cooperative launch, two phases
+ *                             per step (x-rows: inverse x transform, nonlinear terms, forward
+ *                             x transform; per kx, the (y, z) slab: forward transform, update,
+ *                             inverse transform) with this library's shared-memory FFTs and a
+ *                             bounded grid barrier;
+ *   PF_SPECTRAL_ENGINE_AUTO   (default) fused wherever it takes the grid, except two-field
+ *                             (Model C) 2D grids with a 1024 side, where cuFFT was measured
+ *                             faster; else cuFFT. */
 #define PF_SPECTRAL_ENGINE_AUTO 0
 #define PF_SPECTRAL_ENGINE_CUFFT 1
 #define PF_SPECTRAL_ENGINE_FUSED 2

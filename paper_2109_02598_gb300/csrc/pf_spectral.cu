@@ -218,14 +218,16 @@ cudaError_t launch_nonlinear(const pf_spectral_s* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// AUTO takes the fused engine where it was measured faster than cuFFT on GB300: sides up
-// to 256, and one-field models at 512 (per step, fused vs cuFFT: 64^2 9.7 vs 10.6 us, 128^2
-// 12.0 vs 13.8, 256^2 13.1 vs 13.7, Model A 512^2 15.9 vs 16.7; but Model C 512^2 23.0 vs
-// 18.9 and 1024^2 40.6 vs 32.9).
+// AUTO takes the fused engine where it was measured faster than cuFFT on GB300: every grid
+// it takes except two-field (Model C) 2D grids with a 1024 side (per step, fused vs cuFFT:
+// 64^2 Model A 9.2 vs 10.1 us, 128^2 A 10.9 vs 13.3 and C 11.1 vs 13.7, 256^2 A 12.8 vs 13.2,
+// 512^2 A 13.5 vs 16.3 and C 17.3 vs 18.4, 1024^2 A 28.2 vs 32.4 but C 67.7 vs 37.9, 64^3 A
+// 17.4 vs 18.2 and C 18.3 vs 21.7).
 bool auto_prefers_fused(const pf_spectral_s* s) {
   if (!s->fused_ok) return false;
+  if (s->dim == 3) return true;
   const int64_t nmax = s->d[0] > s->d[1] ? s->d[0] : s->d[1];
-  return nmax <= 256 || (nmax <= 512 && s->nf == 1);
+  return s->nf == 1 || nmax < 1024;
 }
 
 bool use_fused(const pf_spectral_s* s) {
@@ -513,7 +515,8 @@ int pf_spectral_set_engine(pf_spectral_t s, int engine) {
       engine != PF_SPECTRAL_ENGINE_FUSED)
     return invalid("unknown spectral engine %d", engine);
   if (engine == PF_SPECTRAL_ENGINE_FUSED && !s->fused_ok)
-    return invalid("the fused engine takes 2D grids with power-of-two sides in [4, 1024]");
+    return invalid("the fused engine takes power-of-two sides (nx in [4, 1024]) whose (y, z) "
+                   "slab fits in a CTA's shared memory");
   s->engine = engine;
   return PF_OK;
 }

@@ -1,5 +1,5 @@
 // Internal state of a spectral solver, shared by its two engines: cuFFT plus this library's
-// pointwise kernels (pf_spectral.cu) and the fused 2D engine (pf_spectral_fused.cu).
+// pointwise kernels (pf_spectral.cu) and the fused engine (pf_spectral_fused.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,13 +31,14 @@ struct pf_spectral_s {
   // fused engine
   int engine = 0;                   // PF_SPECTRAL_ENGINE_*
   bool fused_ok = false;            // the fused engine takes this grid (set at creation)
-  float2* twiddle = nullptr;        // W_nx^j (j < nx) then W_ny^j (j < ny), forward sign
+  float2* twiddle = nullptr;        // W_nx^j (j < nx), W_ny^j (j < ny), W_nz^j (j < nz)
   unsigned int* d_bar = nullptr;    // grid barrier: count, generation; then the error flag
   int fused_blocks = 0;             // CTAs of the cooperative launch (0: not prepared)
   int fused_threads = 0;            // threads per CTA
   int fused_row_team = 0;           // threads per row task
-  int fused_col_team = 0;           // threads per column task
-  int fused_cpt = 0;                // columns each column team owns
+  int fused_col_team = 0;           // threads per slab task
+  int fused_cpt = 0;                // slabs each slab team owns
+  int fused_rbuf = 0, fused_cbuf = 0;  // float2s of a row / slab team's FFT buffers
   size_t fused_smem = 0;            // dynamic shared memory per CTA
 };
 

@@ -117,7 +117,7 @@ class Spectral:
     ENGINES = {"auto": 0, "cufft": 1, "fused": 2}
 
     def set_engine(self, engine: str = "auto"):
-        """"cufft", "fused" (2D, power-of-two sides in [4, 1024]) or "auto"."""
+        """"cufft", "fused" (power-of-two sides; in 3D a (y, z) slab that fits a CTA) or "auto"."""
         check(self._lib.pf_spectral_set_engine(self._h, self.ENGINES[engine]))
         return self
 

@@ -71,8 +71,10 @@ def test_single_step(pf, model, shape):
     assert rel_linf(gpu_spectral(pf, model, x0, 1, engine="cufft"), ref) <= 2e-6
 
 
-# the fused engine: power-of-two sides, from the smallest it takes (4 x 2) to 1024
-FUSED_SHAPES = [(2, 4), (16, 16), (32, 64), (64, 8), (128, 128), (256, 1024)]
+# the fused engine: power-of-two sides, from the smallest it takes (4 x 2) to 1024; in 3D,
+# (y, z) slabs from 2 x 2 to the paper's 64 x 64, and rows up to 256
+FUSED_SHAPES = [(2, 4), (16, 16), (32, 64), (64, 8), (128, 128), (256, 1024),
+                (2, 2, 4), (4, 8, 16), (16, 2, 32), (8, 32, 256), (64, 64, 64)]
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -85,13 +87,14 @@ def test_fused_engine_single_and_twenty_steps(pf, model, shape):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_fused_and_cufft_engines_agree_and_interleave(pf, model):
-    x0 = init(model, (64, 128), seed=10)
+@pytest.mark.parametrize("shape", [(64, 128), (16, 32, 8)])
+def test_fused_and_cufft_engines_agree_and_interleave(pf, model, shape):
+    x0 = init(model, shape, seed=10)
     a = gpu_spectral(pf, model, x0, 60, engine="fused")
     b = gpu_spectral(pf, model, x0, 60, engine="cufft")
     assert rel_linf(a, b) <= 2e-5
     # engines can alternate on one solver: the state is shared
-    s = pf.Spectral((64, 128), model, COEFFS[model], DT[model]).write_fields(x0)
+    s = pf.Spectral(shape, model, COEFFS[model], DT[model]).write_fields(x0)
     for i in range(6):
         s.set_engine("fused" if i % 2 else "cufft").step(10)
     c = s.read_fields()
@@ -104,9 +107,13 @@ def test_engine_selection(pf):
     assert s.engine == "fused"
     assert s.set_engine("cufft").engine == "cufft"
     s.close()
-    # auto: fused up to 256 per side, and up to 512 for one-field models
+    # auto: fused wherever it takes the grid, except Model C with a 1024 side in 2D; in 3D
+    # only slabs that fit a CTA's shared memory
     for shape, model, want in [((256, 256), "c", "fused"), ((512, 512), "ac", "fused"),
-                               ((512, 512), "c", "cufft"), ((1024, 1024), "ac", "cufft")]:
+                               ((512, 512), "c", "fused"), ((1024, 1024), "ac", "fused"),
+                               ((1024, 1024), "c", "cufft"),
+                               ((64, 64, 64), "c", "fused"), ((8, 16, 32), "ac", "fused"),
+                               ((256, 256, 256), "ac", "cufft")]:
         s = pf.Spectral(shape, model, COEFFS[model], DT[model])
         assert s.engine == want, (shape, model)
         s.close()
@@ -136,7 +143,8 @@ def test_two_hundred_steps(pf, model, shape, dt, engine):
 
 
 @pytest.mark.parametrize("model", MODELS)
-@pytest.mark.parametrize("shape,engine", [((24, 40), "cufft"), ((32, 64), "fused")])
+@pytest.mark.parametrize("shape,engine", [((24, 40), "cufft"), ((32, 64), "fused"),
+                                          ((8, 16, 32), "fused")])
 def test_one_call_equals_single_steps(pf, model, shape, engine):
     # cuFFT: two recorded 32-step graphs and 6 direct steps against 70 single calls; fused:
     # one 70-step launch against 70 one-step launches
