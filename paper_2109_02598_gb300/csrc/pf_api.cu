@@ -648,8 +648,8 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
   }
   if (g->dim == 3 && k_steps != 2 && tile >= kFirstTmaTile3D &&
       !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g))))
-    return invalid("3D tile %dx%d needs an AC/GS model and nx %% %d == 0, ny %% %d == 0",
-                   tile_x, tile_y, tile_x, tile_y);
+    return invalid("3D tile %dx%d needs nx %% %d == 0 and ny %% %d == 0", tile_x, tile_y,
+                   tile_x, tile_y);
   g->req_tile = tile;
   g->req_k = k_steps;
   drop_graphs(g);

@@ -244,7 +244,9 @@ cudaError_t launch_tma(pf_grid_s* gr, const Tma3dMaps& maps, FieldOut out, cudaS
 }  // namespace
 
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g) {
-  if (model != PF_MODEL_AC && model != PF_MODEL_GS) return false;
+  if (model != PF_MODEL_AC && model != PF_MODEL_GS && model != PF_MODEL_CH &&
+      model != PF_MODEL_C)
+    return false;
   if (tma_tile < 0 || tma_tile >= kNumTmaTiles3D) return false;
   int tx, ty;
   tma3d_tile_shape(tma_tile, &tx, &ty);
@@ -258,6 +260,8 @@ void tma3d_tile_shape(int tma_tile, int* tx, int* ty) {
 }
 
 cudaError_t launch_fe3d_tma(pf_grid_s* gr, int tma_tile, int src, int dst, cudaStream_t st) {
+  if (gr->model == PF_MODEL_CH || gr->model == PF_MODEL_C)
+    return launch_fe3d_tma_r2(gr, tma_tile, src, dst, st);
   cudaError_t e = tma3d_maps(gr, tma_tile, src);
   if (e != cudaSuccess) return e;
   FieldOut out{};

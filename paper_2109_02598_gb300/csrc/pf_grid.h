@@ -23,6 +23,21 @@ struct TmaCache {
   Tma3dMaps maps[2];
 };
 
+// TMA descriptors of the radius-2 3D kernel (Models B and C): the tile interior box, a
+// two-row halo box, the 4-wide column box and a 4 x 1 corner box, per field.
+struct Tma2Maps {
+  CUtensorMap inner[PF_MAX_FIELDS];
+  CUtensorMap row2[PF_MAX_FIELDS];
+  CUtensorMap side[PF_MAX_FIELDS];
+  CUtensorMap corner[PF_MAX_FIELDS];
+};
+
+struct Tma2Cache {
+  int tile = -1;
+  bool valid[2] = {false, false};
+  Tma2Maps maps[2];
+};
+
 // TMA descriptors of the depth-2 3D kernel: a two-row halo box and the 8-row interior box,
 // both spanning the whole x-row, per field.
 struct Tb2Maps {
@@ -82,6 +97,7 @@ struct pf_grid_s {
   double* red_host = nullptr;      // pinned
   pf::AdjointState adj;
   pf::TmaCache tma;
+  pf::Tma2Cache tma2;
   pf::Tb2Cache tb2;
   int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
   // band kernel (2D grid resident in the SMs' shared memory): exchange slots of the bands'
@@ -114,12 +130,15 @@ Geom grid_geom(const pf_grid_s* g);
 ModelParams make_params(int model, const double* c, double dt, double h, int stencil = 0);
 cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStream_t st);
 
-// ---- 3D TMA kernel (AC, GS): TMA tile ids 0 = 64x16, 1 = 128x8, 2 = 128x16
+// ---- 3D TMA kernels (AC, GS; Models B and C in pf_fe3d_tma2.cu): TMA tile ids 0 = 64x16,
+// 1 = 128x8, 2 = 128x16
 constexpr int kNumTmaTiles3D = 3;
 void tma3d_tile_shape(int tma_tile, int* tx, int* ty);
 bool fe3d_tma_supported(int model, int tma_tile, const Geom& g);
 cudaError_t tma3d_maps(pf_grid_s* g, int tma_tile, int buf);
 cudaError_t launch_fe3d_tma(pf_grid_s* g, int tma_tile, int src, int dst, cudaStream_t st);
+// Models B and C on the same tiles (pf_fe3d_tma2.cu)
+cudaError_t launch_fe3d_tma_r2(pf_grid_s* g, int tma_tile, int src, int dst, cudaStream_t st);
 
 // ---- 2D band kernel (AC, CH; k = 1): one band of full rows per SM, all steps in one
 // cooperative launch (pf_fe2d_bands.cu)

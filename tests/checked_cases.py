@@ -86,7 +86,7 @@ def run_cases(pf):
     for model, shape in (("ch", (256, 512)), ("ac", (77, 388)), ("ch", (333, 388))):
         res[f"bands_{model}_{shape[0]}x{shape[1]}"] = run_grid(
             pf, model, shape, 11, (shape[1], pf.PF_TILE_BANDS, 1))
-    # 3D: the general kernel (all models), the TMA kernel and the depth-2 kernel
+    # 3D: the general kernel (all models), the TMA kernels and the depth-2 kernel
     for model in ("ac", "ch", "gs", "c"):
         for tile in ((32, 16), (64, 8)):
             res[f"3d_general_{model}_{tile[0]}x{tile[1]}"] = run_grid(pf, model, (10, 20, 36), 5,
@@ -94,6 +94,10 @@ def run_cases(pf):
     for model in ("ac", "gs"):
         res[f"3d_tma_{model}"] = run_grid(pf, model, (12, 32, 128), 5, (64, 16, 1))
         res[f"3d_depth2_{model}"] = run_grid(pf, model, (12, 16, 128), 6, (128, 8, 2))
+    for model in ("ch", "c"):  # the radius-2 TMA kernel
+        for tile in ((64, 16), (128, 8)):
+            res[f"3d_tma_r2_{model}_{tile[0]}x{tile[1]}"] = run_grid(
+                pf, model, (9, 32, 128), 5, (tile[0], tile[1], 1))
     # the batch
     shapes = [(64, 64), (97, 130), (5, 7), (33, 300)]
     specs = [dict(ny=s[0], nx=s[1], Du=0.2, Dv=0.1, F=0.03 + 0.005 * i, k=0.05 + 0.003 * i)

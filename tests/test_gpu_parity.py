@@ -198,10 +198,31 @@ def test_tma_tile_rejected_when_grid_does_not_divide(pf):
         g.set_tuning(64, 16, 1)  # ny = 20 is not a multiple of 16
     g.set_tuning(64, 8, 1)  # the general kernel takes any size
     g.close()
-    h = pf.Grid((8, 32, 64), 1).set_model("ch", COEFFS["ch"], DT["ch"])
-    with pytest.raises(PfError):
-        h.set_tuning(64, 16, 1)  # no TMA kernel for Model B
+    h = pf.Grid((8, 40, 64), 1).set_model("ch", COEFFS["ch"], DT["ch"])
+    with pytest.raises(PfError, match="ny"):
+        h.set_tuning(64, 16, 1)  # Model B on the TMA tiles too, but ny = 40 % 16 != 0
     h.close()
+
+
+@pytest.mark.parametrize("model", ["ch", "c"])
+@pytest.mark.parametrize("shape,tiles", [((12, 32, 128), [(64, 16), (128, 8), (128, 16)]),
+                                         ((5, 16, 64), [(64, 16)]),
+                                         ((3, 8, 128), [(128, 8)]),
+                                         ((64, 64, 64), [(64, 16)])])
+def test_radius2_tma_kernel_is_bitwise_general(pf, model, shape, tiles):
+    # Models B and C on the TMA z-streaming tiles (the chemical potential on chip, one ring
+    # wider than the tile): the general kernel's bits for every tile and step count, and the
+    # oracle within the single-step bar
+    x0 = init_fields(model, shape, seed=14)
+    for n in (1, 2, 7):
+        base = gpu_run(pf, model, x0, n, tuning=(32, 16, 1))
+        for t in tiles:
+            got = gpu_run(pf, model, x0, n, tuning=(t[0], t[1], 1))
+            for a, b in zip(base, got):
+                assert np.array_equal(a, b), (n, t)
+    t = tiles[0]
+    one = gpu_run(pf, model, x0, 1, tuning=(t[0], t[1], 1))
+    assert rel_linf(one, oracle.euler_step(model, x0, COEFFS[model], DT[model])) <= 1e-6
 
 
 def test_default_tuning_picks_tma_for_the_3d_workload(pf):
