@@ -23,6 +23,8 @@ Every function is plain numpy in float64 and follows the paper's definitions dir
 * Gray-Scott, which the paper names as a reaction-diffusion example (Sec. 1) but does not
   write out, in its standard two-species form
   du/dt = Du lap u - u v^2 + F (1 - u),  dv/dt = Dv lap v + u v^2 - (F + k) v;
+* N coupled species (any number of fields, Sec. 2.3) of reaction-diffusion type,
+  du_i/dt = D_i lap u_i + sum_m K[i][m] prod_j u_j^E[m][j], polynomial rates;
 * the forward-Euler solver (Sec. 2.4.1): x^{n+1} = x^n + dt f(x^n), every field updated
   from the same x^n, i.e. the paper's ``equation()`` then ``step()`` split (Sec. 2.2.4);
 * the discrete free energy whose gradient flow Model A is, and the discrete adjoint of
@@ -37,7 +39,7 @@ import itertools
 
 import numpy as np
 
-MODELS = ("ac", "ch", "gs", "c")
+MODELS = ("ac", "ch", "gs", "c", "rd")
 
 
 def _f64(x):
@@ -161,8 +163,68 @@ def rhs_model_c(psi, m, c1=1.0, c2=1.0, c3=1.0, c4=1.0, c5=1.0, h: float = 1.0,
     return f_psi, lap(mu_m)
 
 
+# ---------------------------------------- N coupled species (reaction-diffusion, generic)
+#
+# The paper writes a model as a set of coupled equations of motion over any number of fields
+# (Sec. 2.3); Gray-Scott (Sec. 1) is the two-species reaction-diffusion case. The generic
+# family here couples N fields through polynomial reaction terms:
+#   du_i/dt = D_i lap u_i + sum_m K[i][m] prod_j u_j ** E[m][j]
+# with M monomials whose integer exponents E[m][j] are in 0..3, and rates K. Coefficient
+# layout (the C interface's): D_0 .. D_{N-1}, M, then E row by row (M rows of N), then K row by
+# row (N rows of M).
+
+RD_MAX_FIELDS = 4
+RD_MAX_MONOMIALS = 8
+
+
+def rd_unpack(coeffs, n_fields: int):
+    """(D, E, K) from the flat coefficient list of an N-species system."""
+    c = [float(x) for x in coeffs]
+    N = int(n_fields)
+    if not 1 <= N <= RD_MAX_FIELDS or len(c) < N + 1:
+        raise ValueError("bad field count or coefficient list")
+    D = np.array(c[:N])
+    M = int(round(c[N]))
+    if c[N] != M or not 0 <= M <= RD_MAX_MONOMIALS or len(c) != N + 1 + 2 * N * M:
+        raise ValueError("bad monomial count or coefficient list length")
+    E = np.array(c[N + 1:N + 1 + M * N]).reshape(M, N)
+    if not np.all((E == np.round(E)) & (E >= 0) & (E <= 3)):
+        raise ValueError("exponents must be integers in 0..3")
+    K = np.array(c[N + 1 + M * N:]).reshape(N, M)
+    return D, E.astype(int), K
+
+
+def rd_pack(D, E, K):
+    """The flat coefficient list of (D, E, K)."""
+    D = [float(x) for x in D]
+    E = np.asarray(E, dtype=float).reshape(-1, len(D))
+    K = np.asarray(K, dtype=float).reshape(len(D), E.shape[0])
+    return tuple(D) + (float(E.shape[0]),) + tuple(E.ravel()) + tuple(K.ravel())
+
+
+def rhs_rd(fields, coeffs, h: float = 1.0, stencil: str = "std"):
+    """N-species reaction-diffusion right-hand side (one array per field)."""
+    u = [_f64(f) for f in fields]
+    D, E, K = rd_unpack(coeffs, len(u))
+    mono = []
+    for row in E:
+        p = np.ones_like(u[0])
+        for j, e in enumerate(row):
+            p = p * u[j] ** int(e)
+        mono.append(p)
+    out = []
+    for i in range(len(u)):
+        f = D[i] * laplacian_stencil(u[i], h, stencil)
+        for mm, p in enumerate(mono):
+            f = f + K[i, mm] * p
+        out.append(f)
+    return tuple(out)
+
+
 def rhs(model: str, fields, coeffs, h: float = 1.0, stencil: str = "std"):
     """Right-hand side f(x) of ``model`` for the tuple of fields ``x``."""
+    if model == "rd":
+        return rhs_rd(fields, coeffs, h, stencil)
     if model == "ac":
         return (rhs_allen_cahn(fields[0], *coeffs, h=h, stencil=stencil),)
     if model == "ch":
