@@ -60,6 +60,15 @@ extern "C" {
 #define PF_MODEL_C 4  /* Model C (eutectic), 2 fields (psi, m), coeffs {c1, c2, c3, c4, c5}:
                          dpsi/dt = lap psi + c1 psi - c2 psi^3 + 2 c5 psi m,
                          dm/dt = -lap^2 m - lap(c3 m - c4 m^3 + c5 psi^2)   (Sec. 3) */
+#define PF_MODEL_RD 5 /* N coupled species of reaction-diffusion type, N = the grid's field
+                         count (1..4; the coupled equations of motion of Sec. 2.3, of which
+                         Gray-Scott, Sec. 1, is the two-species case):
+                           du_i/dt = D_i lap u_i + sum_m K[i][m] prod_j u_j^E[m][j]
+                         coeffs {D_0 .. D_{N-1}, M, E[0][0..N-1] .. E[M-1][..],
+                                 K[0][0..M-1] .. K[N-1][..]}: M <= 8 monomials, exponents
+                         integers in [0, 3], D_i >= 0; N + 1 + 2 N M values. 5-/7-point
+                         stencil, one kernel, k = 1; the stability check covers the
+                         diffusion terms (dt max D 4d/h^2 <= 2) */
 
 /* ---------------------------------------------------------------- Laplacian stencils */
 #define PF_STENCIL_STD 0 /* second order: 5-point (2D), 7-point (3D); the default      */
@@ -92,7 +101,7 @@ const char* pf_last_error(void);
 /* Create a periodic grid (the paper's Grid/System, Sec. 2.2.1 and 2.2.5).
  *   dim      2 or 3;
  *   n        n[0] = nx, n[1] = ny, n[2] = nz (ignored for dim 2); each in [1, 2^30];
- *   n_fields 1 or 2 (Gray-Scott needs 2);
+ *   n_fields 1 .. 4 (Models A and B take 1, Gray-Scott and Model C 2, PF_MODEL_RD any);
  *   h        grid spacing, > 0;
  *   stream   cudaStream_t to enqueue all work on (NULL = legacy default stream);
  *   out      receives the handle.
@@ -106,7 +115,7 @@ void pf_destroy(pf_grid_t g);
 
 /* Choose the equation of motion and its coefficients (Sec. 3; see PF_MODEL_*).
  *   coeffs/n_coeffs  AC {c1, c2}, CH {c1, c2, M}, GS {Du, Dv, F, k},
- *                    C {c1, c2, c3, c4, c5} (exact count);
+ *                    C {c1, c2, c3, c4, c5}, RD as at PF_MODEL_RD (exact count);
  *   dt               time step, > 0;
  *   force            0: reject dt beyond the linear stability bound of forward Euler
  *                    (PF_ERR_UNSTABLE_DT, nothing changed); 1: accept it.

@@ -1,12 +1,13 @@
 """GB300-native explicit forward-Euler step for phase-field (Allen-Cahn, Cahn-Hilliard,
-Model C) and reaction-diffusion (Gray-Scott) models on periodic 2D/3D grids, plus the
+Model C) and reaction-diffusion (Gray-Scott, N coupled species) models on periodic 2D/3D
+grids, plus the
 semi-implicit Fourier spectral solver and the structure factor (arxiv 2109.02598).
 
 The compute path is libpfgpu.so (hand-written CUDA for sm_103a behind the C ABI of
 ``include/pfgpu.h``); this package only marshals arguments to it.
 """
 from ._lib import PF_TILE_BANDS, PfError, load  # noqa: F401
-from .grid import Grid  # noqa: F401
+from .grid import Grid, rd_coeffs  # noqa: F401
 from .adjoint import (GrayScottAdjoint, PhaseFieldAdjoint, adjoint_backward,  # noqa: F401
                       adjoint_forward)
 from .batch import Batch, shard_instances  # noqa: F401
@@ -14,4 +15,4 @@ from .spectral import Spectral, porod_fit, structure_factor  # noqa: F401
 
 __all__ = ["PF_TILE_BANDS", "Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PhaseFieldAdjoint", "PfError",
            "Spectral", "adjoint_backward", "adjoint_forward", "load", "porod_fit",
-           "structure_factor"]
+           "rd_coeffs", "structure_factor"]

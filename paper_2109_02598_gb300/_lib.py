@@ -31,7 +31,9 @@ PF_MODEL_AC = 1
 PF_MODEL_CH = 2
 PF_MODEL_GS = 3
 PF_MODEL_C = 4
-MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS, "c": PF_MODEL_C}
+PF_MODEL_RD = 5
+MODEL_IDS = {"ac": PF_MODEL_AC, "ch": PF_MODEL_CH, "gs": PF_MODEL_GS, "c": PF_MODEL_C,
+             "rd": PF_MODEL_RD}
 MODEL_FIELDS = {"ac": 1, "ch": 1, "gs": 2, "c": 2}
 
 STENCIL_IDS = {"std": 0, "iso": 1, "4th": 2, "iso27": 3}

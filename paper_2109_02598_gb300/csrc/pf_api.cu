@@ -43,6 +43,7 @@ int model_fields(int model) {
     case PF_MODEL_CH: return 1;
     case PF_MODEL_GS: return 2;
     case PF_MODEL_C: return 2;
+    case PF_MODEL_RD: return -1;  // the grid's field count, 1 .. PF_MAX_FIELDS
   }
   return 0;
 }
@@ -148,6 +149,11 @@ bool tile_supported(pf_grid_s* g, int tile, int k);
 // Turn the requested tuning (or the defaults) into the tuning in effect for the current
 // model and grid.
 int resolve_tuning(pf_grid_s* g) {
+  if (g->model_set && g->model == PF_MODEL_RD) {  // one kernel per dimension (pf_rdn.cu)
+    g->tile = 0;
+    g->k = 1;
+    return PF_OK;
+  }
   if (g->dim == 2) {
     const int def = g->stencil == PF_ST_STD ? 1 : 0;  // 128 x 16; other stencils 64 x 16
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
@@ -186,6 +192,7 @@ int resolve_tuning(pf_grid_s* g) {
 }
 
 bool tile_supported(pf_grid_s* g, int tile, int k) {
+  if (g->model == PF_MODEL_RD) return tile == 0 && k == 1;
   if (g->dim == 2 && tile == kTileCluster2D)
     return g->stencil == PF_ST_STD && fe2d_cluster_supported(g->model, k, grid_geom(g));
   if (g->dim == 2 && tile == kTileBands2D)
@@ -236,6 +243,7 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
     out.f[f] = g->buf[dst][f];
   }
   const Geom q = grid_geom(g);
+  if (g->model == PF_MODEL_RD) return launch_rd(q, g->nf, in, out, g->rd, st);
   if (g->dim == 2 && tile == kTileCluster2D)
     return launch_fe2d_cluster(g->model, k, q, in, out, g->params, k, st);
   if (g->dim == 2 && tile == kTileBands2D) return launch_fe2d_bands(g, src, dst, k, st);
@@ -335,7 +343,7 @@ int pf_create_grid(int dim, const int64_t* n, int n_fields, double h, void* stre
     return invalid("grid sizes must be in [1, 2^30] (got %lld x %lld x %lld)",
                    (long long)n[0], (long long)n[1], (long long)nz);
   if (n_fields < 1 || n_fields > PF_MAX_FIELDS)
-    return invalid("n_fields must be 1 or 2 (got %d)", n_fields);
+    return invalid("n_fields must be in [1, %d] (got %d)", PF_MAX_FIELDS, n_fields);
   if (!(h > 0.0) || !std::isfinite(h)) return invalid("h must be finite and > 0");
   const int64_t pitch = (n[0] + 3) / 4 * 4;
   const int64_t plane = pitch * n[1];  // <= (2^30 + 3) 2^30: no overflow
@@ -395,9 +403,67 @@ void pf_destroy(pf_grid_t g) {
   delete g;
 }
 
+// N coupled species: coefficients D_0 .. D_{N-1}, M, the M x N exponents (row by row), the
+// N x M rates (row by row), N = the grid's field count.
+int set_model_rd(pf_grid_s* g, const double* c, int n_coeffs, double dt, int force) {
+  const int N = g->nf;
+  if (c == nullptr || n_coeffs < N + 1) return invalid("N-species model: coefficient list too short");
+  for (int i = 0; i < n_coeffs; ++i)
+    if (!std::isfinite(c[i])) return invalid("coefficient %d is not finite", i);
+  const double mm = c[N];
+  if (!(mm >= 0 && mm <= kRdMonomials && mm == std::floor(mm)))
+    return invalid("N-species model: the monomial count (coefficient %d) must be an integer "
+                   "in [0, %d]", N, kRdMonomials);
+  const int M = (int)mm;
+  if (n_coeffs != N + 1 + 2 * N * M)
+    return invalid("N-species model with %d fields and %d monomials takes %d coefficients "
+                   "(got %d)", N, M, N + 1 + 2 * N * M, n_coeffs);
+  for (int i = 0; i < N; ++i)
+    if (c[i] < 0) return invalid("diffusion coefficient D_%d must be >= 0", i);
+  const double* E = c + N + 1;
+  const double* K = E + M * N;
+  for (int i = 0; i < M * N; ++i)
+    if (!(E[i] >= 0 && E[i] <= 3 && E[i] == std::floor(E[i])))
+      return invalid("exponents must be integers in [0, 3] (coefficient %d)", N + 1 + i);
+  if (g->stencil != PF_ST_STD) return invalid("the N-species model runs with the 5-/7-point stencil");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("dt must be finite and > 0");
+  // stability of the diffusion part (the reaction terms depend on the state): dt max D
+  // (4 d / h^2) <= 2
+  double dmax = 0;
+  for (int i = 0; i < N; ++i) dmax = std::fmax(dmax, c[i]);
+  const double lim = dmax > 0 ? 2.0 * g->h * g->h / (dmax * 4.0 * g->dim) : INFINITY;
+  if (dt > lim && !force) {
+    set_error("dt = %g exceeds the forward-Euler stability limit %g of the diffusion terms "
+              "(pass force=1 to accept)", dt, lim);
+    return PF_ERR_UNSTABLE_DT;
+  }
+  RdParams p{};
+  p.nmono = M;
+  for (int m = 0; m < M; ++m) {
+    int packed = 0;
+    for (int j = 0; j < N; ++j) packed |= ((int)E[m * N + j]) << (2 * j);
+    p.E[m] = packed;
+  }
+  for (int i = 0; i < N; ++i) {
+    p.D[i] = (float)(c[i] / (g->h * g->h));
+    for (int m = 0; m < M; ++m) p.K[i][m] = (float)K[i * M + m];
+  }
+  p.dt = (float)dt;
+  g->model = PF_MODEL_RD;
+  g->rd = p;
+  g->rd_ncoeffs = n_coeffs;
+  for (int i = 0; i < n_coeffs; ++i) g->rd_coeffs[i] = c[i];
+  g->dt = dt;
+  g->model_set = 1;
+  drop_graphs(g);
+  resolve_tuning(g);
+  return PF_OK;
+}
+
 int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, double dt,
                  int force) {
   if (int rc = check_grid(g)) return rc;
+  if (model == PF_MODEL_RD) return set_model_rd(g, coeffs, n_coeffs, dt, force);
   if (model_fields(model) == 0) return invalid("unknown model %d", model);
   if (model_fields(model) != g->nf)
     return invalid("model %d needs %d field(s); grid has %d", model, model_fields(model), g->nf);
@@ -577,7 +643,9 @@ int pf_set_stencil(pf_grid_t g, int stencil) {
     return invalid("the 27-point stencil is defined for 3D grids only");
   if (stencil == PF_STENCIL_4TH && g->dim != 2)
     return invalid("the fourth-order stencil is defined for 2D grids only");
-  if (g->model_set && stencil != g->stencil) {
+  if (g->model_set && g->model == PF_MODEL_RD && stencil != PF_STENCIL_STD)
+    return invalid("the N-species model runs with the 5-/7-point stencil");
+  if (g->model_set && g->model != PF_MODEL_RD && stencil != g->stencil) {
     const double lim = stable_dt_limit(g->model, g->dim, g->h, g->coeffs, stencil);
     if (g->dt > lim) {
       set_error("dt = %g exceeds the forward-Euler stability limit %g with this stencil "
@@ -586,7 +654,8 @@ int pf_set_stencil(pf_grid_t g, int stencil) {
     }
   }
   g->stencil = stencil;
-  if (g->model_set) g->params = make_params(g->model, g->coeffs, g->dt, g->h, stencil);
+  if (g->model_set && g->model != PF_MODEL_RD)
+    g->params = make_params(g->model, g->coeffs, g->dt, g->h, stencil);
   g->req_tile = -1;
   g->req_k = 0;
   drop_graphs(g);
@@ -595,6 +664,13 @@ int pf_set_stencil(pf_grid_t g, int stencil) {
 
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
   if (int rc = check_grid(g)) return rc;
+  if (g->model_set && g->model == PF_MODEL_RD) {  // one kernel: the tile request is not used
+    if (k_steps < 0 || k_steps > 1)
+      return invalid("the N-species model runs one step per launch (k_steps 0 or 1)");
+    (void)tile_x;
+    (void)tile_y;
+    return resolve_tuning(g);
+  }
   int tile = -1;
   if (tile_x == 0 && tile_y == 0) {
     tile = -1;

@@ -81,7 +81,7 @@ struct pf_grid_s {
   int device = 0;
   int64_t pitch = 0, plane = 0, field_elems = 0;
   float* base = nullptr;
-  float* buf[2][PF_MAX_FIELDS] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  float* buf[2][PF_MAX_FIELDS] = {};
   int cur = 0;
   int model = 0;
   double coeffs[5] = {0, 0, 0, 0, 0};
@@ -89,6 +89,11 @@ struct pf_grid_s {
   int model_set = 0;
   int stencil = 0;  // PF_STENCIL_* (Laplacian stencil of the step)
   pf::ModelParams params{};
+  // N coupled species (PF_MODEL_RD): the coefficient list as given and the kernel's form
+  static constexpr int kMaxRdCoeffs = PF_MAX_FIELDS + 1 + 2 * PF_MAX_FIELDS * pf::kRdMonomials;
+  double rd_coeffs[kMaxRdCoeffs] = {};
+  int rd_ncoeffs = 0;
+  pf::RdParams rd{};
   int tile = -1;      // kernel tile id in effect (2D or 3D table)
   int k = 0;          // temporal-blocking depth in effect
   int req_tile = -1;  // tile asked for by pf_set_tuning (-1 = library default)

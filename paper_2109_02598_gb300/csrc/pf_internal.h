@@ -10,7 +10,7 @@
 #include "pf_model.cuh"
 #include "pfgpu.h"
 
-#define PF_MAX_FIELDS 2
+#define PF_MAX_FIELDS 4  // fields of a grid: 1 or 2 for Models A-C and Gray-Scott, up to 4 for N species
 
 namespace pf {
 
@@ -29,6 +29,20 @@ struct FieldPtrs {
 struct FieldOut {
   float* f[PF_MAX_FIELDS];
 };
+
+// N coupled species (PF_MODEL_RD): du_i/dt = D_i lap u_i + sum_m K[i][m] prod_j u_j^E[m][j],
+// as the kernel takes it (pf_rdn.cu): D_i times the stencil factor 1/h^2 and the rates rounded
+// once to float32; monomial m's exponents packed two bits per field (field j at bits 2j).
+constexpr int kRdMonomials = 8;
+struct RdParams {
+  int nmono;
+  int E[kRdMonomials];
+  float D[PF_MAX_FIELDS];
+  float K[PF_MAX_FIELDS][kRdMonomials];
+  float dt;
+};
+cudaError_t launch_rd(const Geom& g, int nf, FieldPtrs in, FieldOut out, const RdParams& p,
+                      cudaStream_t s);
 
 // Set a kernel's dynamic shared-memory limit once per device (the attribute is per device;
 // `mask` has one bit per device ordinal below 64, set after success).

@@ -40,6 +40,20 @@ def _device_tag() -> str:
     return f"{torch.cuda.get_device_name(d)}|sm{major}{minor}"
 
 
+def rd_coeffs(D, E, K):
+    """The coefficient list of PF_MODEL_RD (N coupled species,
+    du_i/dt = D_i lap u_i + sum_m K[i][m] prod_j u_j^E[m][j]): D (N), the exponents E (M rows
+    of N integers in 0..3) and the rates K (N rows of M), flattened in that order after the
+    monomial count M."""
+    D = [float(x) for x in D]
+    E = [[int(e) for e in row] for row in E]
+    K = [[float(k) for k in row] for row in K]
+    if any(len(row) != len(D) for row in E) or len(K) != len(D) or any(len(r) != len(E) for r in K):
+        raise ValueError("E must be M x N and K N x M")
+    return tuple(D) + (float(len(E)),) + tuple(float(e) for row in E for e in row) + \
+        tuple(k for row in K for k in row)
+
+
 class Grid:
     """A periodic grid with ``n_fields`` float32 fields living on the GPU."""
 
@@ -95,8 +109,9 @@ class Grid:
 
     # ---------------------------------------------------------------- model
     def set_model(self, model: str, coeffs, dt: float, force: bool = False):
-        """model in {"ac", "ch", "gs", "c"}; coeffs AC (c1, c2), CH (c1, c2, M),
-        GS (Du, Dv, F, k), Model C (c1, c2, c3, c4, c5)."""
+        """model in {"ac", "ch", "gs", "c", "rd"}; coeffs AC (c1, c2), CH (c1, c2, M),
+        GS (Du, Dv, F, k), Model C (c1, c2, c3, c4, c5), RD (N coupled species, any field
+        count up to 4) the flat list of ``rd_coeffs(D, E, K)``."""
         c = (ctypes.c_double * len(coeffs))(*[float(x) for x in coeffs])
         check(self._lib.pf_set_model(self._h, MODEL_IDS[model], c, len(coeffs), float(dt),
                                      1 if force else 0))

@@ -36,7 +36,7 @@ def test_create_grid_rejects_bad_arguments(lib):
     n = (ctypes.c_int64 * 3)(16, 16, 16)
     assert lib.pf_create_grid(4, n, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
     assert "dim" in _err(lib)
-    assert lib.pf_create_grid(2, n, 3, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
+    assert lib.pf_create_grid(2, n, 5, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
     assert lib.pf_create_grid(2, n, 1, 0.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
     bad = (ctypes.c_int64 * 3)(0, 16, 16)
     assert lib.pf_create_grid(2, bad, 1, 1.0, None, ctypes.byref(h)) == _lib.PF_ERR_INVALID_ARG
