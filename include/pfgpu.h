@@ -124,14 +124,16 @@ void pf_destroy(pf_grid_t g);
 int pf_set_model(pf_grid_t g, int model, const double* coeffs, int n_coeffs, double dt,
                  int force);
 
-/* Copy field `field` in from `src` (dense float32 as above; host memory if
- * src_on_device == 0, else device memory). Host copies complete before return;
- * device copies are enqueued on the grid's stream.
+/* Copy field `field` in from `src` (host memory if src_on_device == 0, else device memory):
+ * a dense float32 array [nz][ny][nx], x fastest, the row-major uniform grid of Sec. 2.2.1
+ * ("Uniform Grid"); the library copies it into its padded rows. Host copies complete before
+ * return; device copies are enqueued on the grid's stream.
  * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
 int pf_write_field(pf_grid_t g, int field, const float* src, int src_on_device);
 
-/* Copy field `field` out to `dst` (dense float32). Host destinations are complete on
- * return (the stream is synchronized); device destinations are enqueued.
+/* Copy field `field` out to `dst`: a dense float32 array [nz][ny][nx], x fastest (the
+ * layout of Sec. 2.2.1, as pf_write_field). Host destinations are complete on return (the
+ * stream is synchronized); device destinations are enqueued.
  * Errors: PF_ERR_INVALID_ARG, PF_ERR_CUDA. */
 int pf_read_field(pf_grid_t g, int field, float* dst, int dst_on_device);
 
@@ -156,8 +158,14 @@ int pf_step(pf_grid_t g, int64_t n_steps);
 
 /* Deterministic reduction of the current state into *out (see PF_REDUCE_*): warp
  * shuffles to per-block partial sums in FP64, then one fixed-order FP64 sum.
+ *   PF_REDUCE_MASS    h^d sum_x phi_x of field `field` (the conserved quantity of Model B,
+ *                     Sec. 3, and of Model C's m);
+ *   PF_REDUCE_ENERGY  the discrete free energy (the paper does not write one out; the reading
+ *                     used is the functional whose gradient is Model A's right-hand side,
+ *                     with forward differences: see PF_REDUCE_ENERGY above), of field 0 for
+ *                     AC/CH, of both fields for Model C; `field` is ignored.
  * Synchronizes the stream. Errors: PF_ERR_INVALID_ARG, PF_ERR_STATE (energy without an
- * AC/CH model), PF_ERR_CUDA, PF_ERR_NONFINITE (*out is still written). */
+ * AC, CH or Model C model), PF_ERR_CUDA, PF_ERR_NONFINITE (*out is still written). */
 int pf_reduce(pf_grid_t g, int what, int field, double* out);
 
 /* Choose the Laplacian stencil of the step (PF_STENCIL_*; Sec. 2.2.2 lists these among the
