@@ -357,6 +357,12 @@ def run_gpu(args, rank, world, local):
         g2.close()
         g.close()
 
+    multi = None
+    if world > 1 and not args.no_companions:
+        try:
+            multi = multi_rank_companions(stream, rank, world, dev)
+        except Exception as exc:  # reported in the line, never fatal for the headline
+            multi = {"error": f"{type(exc).__name__}: {exc}"}
     if rank != 0:
         return
     hbm, peak_kind = _peaks()
@@ -407,6 +413,8 @@ def run_gpu(args, rank, world, local):
     }
     if not args.no_companions:
         line["companions"] = companions(stream, hbm)
+        if multi is not None:
+            line["companions"]["multi_rank"] = multi
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -436,6 +444,64 @@ def summary_line(line) -> str:
         parts.append(f"oracle 1 core {cb['single_core']['value']:.4f}, {cb['cores']} cores "
                      f"{cb['value']:.4f} GLUPS")
     return "; ".join(parts)
+
+
+def multi_rank_companions(stream, rank, world, dev):
+    """Under torchrun (every rank): the 512-instance batch split over the ranks by
+    shard_instances (no data exchange; weak in instances, strong in the batch), and the
+    256^3 Gray-Scott grid split into z-slabs over the ranks (strong scaling: boundary planes
+    exchanged over NCCL every k steps). Times are the slowest rank's, with a barrier on
+    both sides."""
+    import torch
+    import torch.distributed as dist
+    import paper_2109_02598_gb300 as pf
+    out = {}
+    with torch.cuda.stream(stream):
+        specs = synthetic.batch_instances(512, seed=4)
+        mine = pf.shard_instances([q["n"] ** 2 for q in specs], rank, world)
+        b = pf.Batch([dict(n=specs[i]["n"], Du=0.2, Dv=0.1, F=specs[i]["F"], k=specs[i]["k"])
+                      for i in mine], 0.5, stream=stream)
+        for j, i in enumerate(mine):
+            u, v = synthetic.batch_instance_init(specs[i]["n"], i)
+            b.write(j, 0, u).write(j, 1, v)
+        b.autotune(3)
+        b.run(2000)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ms = _time(stream, lambda: b.run(2000))
+        ms = _max_over_ranks(ms, world, dev)
+        sites = _sum_over_ranks(float(b.sites), world, dev)
+        b.close()
+        out["batched_gs2d_512x_sharded"] = {"ranks": world, "instances_here": len(mine),
+                                            "glups": sites * 2000 / (ms * 1e-3) / 1e9,
+                                            "ms": ms}
+        w = synthetic.WORKLOADS[WORKLOAD]
+        x0 = synthetic.workload_init(WORKLOAD)
+        k = 4
+        sg = pf.SlabGrid(x0[0].shape, 2, w["model"], w["coeffs"], w["dt"], w["h"], k=k,
+                         stream=stream)
+        sg.write_global(x0)
+        sg.step(2 * k)
+        torch.cuda.synchronize()
+        dist.barrier()
+        steps = 200
+        t0 = time.perf_counter()
+        sg.step(steps)
+        torch.cuda.synchronize()
+        dt = _max_over_ranks(time.perf_counter() - t0, world, dev)
+        sg.close()
+        out["slab_gs3d_256"] = {"ranks": world, "k_steps_per_exchange": k, "steps": steps,
+                                "glups": x0[0].size * steps / dt / 1e9,
+                                "scaling": "strong (one 256^3 grid split into z-slabs)"}
+    return out
+
+
+def _sum_over_ranks(x: float, world: int, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
 
 
 def _time(stream, fn, reps=1):

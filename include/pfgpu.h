@@ -218,6 +218,16 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
 /* Block until all work enqueued on the grid's stream is done. */
 int pf_synchronize(pf_grid_t g);
 
+/* Copy `count` consecutive planes along the slowest axis (z-planes of ny x nx floats in 3D,
+ * rows of nx floats in 2D), from plane `first`, of field `field`'s current state to a dense
+ * float32 buffer (to_buf = 1) or from one into it (to_buf = 0): the boundary layers that a
+ * domain split along that axis exchanges between neighbours (the paper's boundary layers of
+ * Sec. 2.2.1, here between the slabs of one grid). Host buffers synchronize the stream
+ * before return; device buffers are enqueued on it.
+ * Errors: PF_ERR_INVALID_ARG (range outside the grid, NULL buf), PF_ERR_CUDA. */
+int pf_copy_planes(pf_grid_t g, int field, int64_t first, int64_t count, float* buf,
+                   int to_buf, int buf_on_device);
+
 /* Current device addresses of field `field` in the padded layout, and that layout:
  * row pitch and plane stride in floats. For zero-copy interop only; the addresses
  * change after every pf_step (ping-pong). */

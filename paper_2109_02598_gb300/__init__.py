@@ -12,7 +12,8 @@ from .adjoint import (GrayScottAdjoint, PhaseFieldAdjoint, adjoint_backward,  # 
                       adjoint_forward)
 from .batch import Batch, shard_instances  # noqa: F401
 from .spectral import Spectral, porod_fit, structure_factor  # noqa: F401
+from .slab import SlabGrid, SlabLayout, slab_range  # noqa: F401
 
 __all__ = ["PF_TILE_BANDS", "Batch", "Grid", "shard_instances", "GrayScottAdjoint", "PhaseFieldAdjoint", "PfError",
            "Spectral", "adjoint_backward", "adjoint_forward", "load", "porod_fit",
-           "rd_coeffs", "structure_factor"]
+           "SlabGrid", "SlabLayout", "rd_coeffs", "slab_range", "structure_factor"]

@@ -63,6 +63,8 @@ SIGNATURES = {
                                     ctypes.c_double, ctypes.c_int]),
     "pf_write_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "pf_read_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
+    "pf_copy_planes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _vp,
+                                      ctypes.c_int, ctypes.c_int]),
     "pf_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pf_write_field_host_async": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "pf_read_field_host_async": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),

@@ -849,6 +849,33 @@ int pf_synchronize(pf_grid_t g) {
   return check_device_error(g);
 }
 
+int pf_copy_planes(pf_grid_t g, int field, int64_t first, int64_t count, float* buf,
+                   int to_buf, int buf_on_device) {
+  if (int rc = check_grid(g)) return rc;
+  if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);
+  const int64_t nslow = g->dim == 3 ? g->nz : g->ny;  // planes (3D) or rows (2D)
+  if (first < 0 || count < 0 || first > nslow || count > nslow - first)
+    return invalid("planes [%lld, %lld) outside [0, %lld)", (long long)first,
+                   (long long)(first + count), (long long)nslow);
+  if (count > 0 && buf == nullptr) return invalid("buf is NULL");
+  if (count == 0) return PF_OK;
+  // a plane (3D) is ny rows of nx floats; a 2D "plane" is one row
+  const int64_t rows_per = g->dim == 3 ? g->ny : 1;
+  const size_t w = sizeof(float) * g->nx;
+  float* dev = g->buf[g->cur][field] + first * (g->dim == 3 ? g->plane : g->pitch);
+  const cudaMemcpyKind kind = buf_on_device ? cudaMemcpyDeviceToDevice
+                              : to_buf      ? cudaMemcpyDeviceToHost
+                                            : cudaMemcpyHostToDevice;
+  if (to_buf)
+    PF_CUDA_TRY(cudaMemcpy2DAsync(buf, w, dev, sizeof(float) * g->pitch, w,
+                                  (size_t)(count * rows_per), kind, g->stream));
+  else
+    PF_CUDA_TRY(cudaMemcpy2DAsync(dev, sizeof(float) * g->pitch, buf, w, w,
+                                  (size_t)(count * rows_per), kind, g->stream));
+  if (!buf_on_device) return check_device_error(g);  // synchronizes the stream
+  return PF_OK;
+}
+
 int pf_field_view(pf_grid_t g, int field, float** dev_ptr, int64_t* pitch, int64_t* plane) {
   if (int rc = check_grid(g)) return rc;
   if (field < 0 || field >= g->nf) return invalid("field %d out of range", field);

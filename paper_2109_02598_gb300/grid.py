@@ -149,6 +149,43 @@ class Grid:
         check(self._lib.pf_write_field(self._h, field, a.ctypes.data_as(ctypes.c_void_p), 0))
         return self
 
+    def copy_planes(self, field: int, first: int, count: int, buf, to_buf: bool):
+        """Copy planes [first, first + count) along the slowest axis (z in 3D, y in 2D) of a
+        field to (``to_buf``) or from a dense float32 buffer: a numpy array, or a torch
+        tensor on the host or the grid's device, of shape (count, ...) of the other axes."""
+        if hasattr(buf, "data_ptr"):
+            if not buf.is_contiguous() or buf.dtype != _torch().float32:
+                raise ValueError("buf must be a contiguous float32 tensor")
+            ptr, on_dev = buf.data_ptr(), 1 if buf.is_cuda else 0
+        else:
+            if not (buf.flags.c_contiguous and buf.dtype == np.float32):
+                raise ValueError("buf must be a C-contiguous float32 array")
+            ptr, on_dev = buf.ctypes.data, 0
+        check(self._lib.pf_copy_planes(self._h, field, int(first), int(count),
+                                       ctypes.c_void_p(ptr), 1 if to_buf else 0, on_dev))
+        return buf
+
+    def mass_planes(self, field: int, first: int, count: int) -> float:
+        """h^d sum of a field over planes [first, first + count) along the slowest axis, by
+        the library's reduction (pf_reduce_noalloc on that part of the field)."""
+        torch = _torch()
+        ptr, pitch, plane = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.pf_field_view(self._h, field, ctypes.byref(ptr), ctypes.byref(pitch),
+                                      ctypes.byref(plane)))
+        nslow = self.shape[0]
+        if not (0 <= first and 0 < count and first + count <= nslow):
+            raise ValueError("plane range outside the grid")
+        step = plane.value if self.dim == 3 else pitch.value
+        n = (ctypes.c_int64 * 3)(self.shape[-1], count if self.dim == 2 else self.shape[1],
+                                 count if self.dim == 3 else 1)
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        check(self._lib.pf_reduce_noalloc(_lib.PF_REDUCE_MASS, self.dim, n, pitch.value,
+                                          ctypes.c_void_p(ptr.value + 4 * first * step), self.h,
+                                          0.0, 0.0, ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(_stream_handle(self.stream))))
+        self.synchronize()
+        return float(out.item())
+
     def write_fields(self, fields):
         for i, f in enumerate(fields):
             self.write_field(i, f)
