@@ -199,8 +199,15 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * It needs all P CTAs resident at once: if the device cannot host them (other work, a
  * restricted context), pf_step fails with PF_ERR_CUDA. Its exchange buffers (4 R nx 8-byte
  * words per CTA) are allocated at its first launch.
+ * 2D tile 128 x PF_TILE_STRIPS or 64 x PF_TILE_STRIPS selects the strip kernel (the
+ * standard stencil, any grid size; k in {1, 2, 4} for Allen-Cahn and Gray-Scott, {1, 2} for
+ * Models B and C): one warp per strip of 128 (or 64) columns walks down its rows with the k
+ * steps pipelined in registers, the row neighbours across lanes taken by warp shuffle; the
+ * outer k R columns (rounded up to 4, or 2; R = 1 for Allen-Cahn and Gray-Scott, 2 for
+ * Models B and C) on each side are recomputed halo, and no shared memory is used.
  * Results are bitwise identical to the tiled kernels. */
 #define PF_TILE_BANDS (-1) /* tile_y of the band kernel (with tile_x = nx) */
+#define PF_TILE_STRIPS (-2) /* tile_y of the strip kernel (with tile_x = 128 or 64) */
 int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps);
 
 /* The tuning in effect (after defaults are resolved). */
@@ -257,8 +264,10 @@ void pf_batch_destroy(pf_batch_t b);
 int pf_batch_write_field(pf_batch_t b, int inst, int field, const float* src, int on_device);
 int pf_batch_read_field(pf_batch_t b, int inst, int field, float* dst, int on_device);
 
-/* Tile (one of the 2D tiles of pf_set_tuning) and temporal depth k in {1, 2, 4} for every
- * instance; 0 keeps the current value. */
+/* Tile (one of the 2D tiles of pf_set_tuning, or 128 x PF_TILE_STRIPS for the strip kernel)
+ * and temporal depth k in {1, 2, 4} for every instance; 0 keeps the current value. With the
+ * strip kernel each instance's width is covered by strips of 128 columns and one narrower
+ * strip (64 or 32 columns) for the remainder, cut into tasks of 12 k rows. */
 int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps);
 int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps);
 

@@ -26,6 +26,7 @@ PF_ERR_STATE = -6
 PF_ERR_TIMEOUT = -7
 
 PF_TILE_BANDS = -1  # tile_y of the band kernel (with tile_x = nx)
+PF_TILE_STRIPS = -2  # tile_y of the strip kernel (with tile_x = 128 or 64)
 
 PF_MODEL_AC = 1
 PF_MODEL_CH = 2

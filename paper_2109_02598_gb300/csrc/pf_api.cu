@@ -159,8 +159,14 @@ int resolve_tuning(pf_grid_s* g) {
     g->tile = g->req_tile >= 0 ? g->req_tile : def;
     g->k = g->req_k > 0 ? g->req_k : 1;
     const bool on_chip = g->tile == kTileCluster2D || g->tile == kTileBands2D;
-    if (!on_chip && g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
-    if (on_chip) {
+    const bool strips = g->tile >= kTileStrips2D && g->tile < kTileStrips2D + kNumStrips2D;
+    if (!on_chip && !strips && g->model_set && !fe2d_supported(g->model, g->k)) g->k = 1;
+    if (strips) {
+      if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
+        g->tile = def;
+        g->k = 1;
+      }
+    } else if (on_chip) {
       if (!(g->model_set && tile_supported(g, g->tile, g->k))) {
         g->tile = def;
         g->k = 1;
@@ -197,6 +203,8 @@ bool tile_supported(pf_grid_s* g, int tile, int k) {
     return g->stencil == PF_ST_STD && fe2d_cluster_supported(g->model, k, grid_geom(g));
   if (g->dim == 2 && tile == kTileBands2D)
     return g->stencil == PF_ST_STD && k == 1 && fe2d_bands_supported(g->model, grid_geom(g));
+  if (g->dim == 2 && tile >= kTileStrips2D && tile < kTileStrips2D + kNumStrips2D)
+    return g->stencil == PF_ST_STD && fe2d_strips_supported(g->model, k);
   if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
   if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
   int tx, ty;
@@ -247,6 +255,9 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
   if (g->dim == 2 && tile == kTileCluster2D)
     return launch_fe2d_cluster(g->model, k, q, in, out, g->params, k, st);
   if (g->dim == 2 && tile == kTileBands2D) return launch_fe2d_bands(g, src, dst, k, st);
+  if (g->dim == 2 && tile >= kTileStrips2D && tile < kTileStrips2D + kNumStrips2D)
+    return launch_fe2d_strips(g->model, tile == kTileStrips2D ? 128 : 64, k, q, in, out,
+                              g->params, st);
   if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
   if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
   if (k == 2) {
@@ -327,7 +338,7 @@ using namespace pf;
 
 extern "C" {
 
-int pf_version(void) { return 10000; }
+int pf_version(void) { return 10100; }
 
 const char* pf_last_error(void) { return g_err; }
 
@@ -684,6 +695,13 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
                        "Cahn-Hilliard model, the standard stencil, k = 1, nx %% 4 == 0 with "
                        "64 <= nx <= 4096, and a band of the grid in each SM's shared memory",
                        tile_x);
+    } else if (tile_y == PF_TILE_STRIPS) {
+      tile = tile_x == 128 ? kTileStrips2D : tile_x == 64 ? kTileStrips2D + 1 : -1;
+      const int kk = k_steps > 0 ? k_steps : 1;
+      if (tile < 0 || g->stencil != PF_ST_STD || !(g->model_set && fe2d_strips_supported(g->model, kk)))
+        return invalid("the strip kernel (tile 128 or 64 x PF_TILE_STRIPS) needs a model set, "
+                       "the standard stencil and k = 1, 2 or 4 (Models A, Gray-Scott) or k = 1 "
+                       "or 2 (Models B, C)");
     } else if (tile_x == g->nx && g->ny % cs == 0 && tile_y == g->ny / cs) {
       tile = kTileCluster2D;  // the on-chip cluster kernel: full rows, ny / CS rows per CTA
       const int kk = k_steps > 0 ? k_steps : 1;
@@ -708,12 +726,13 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     if (!(g->model_set && fe3d_tb2_supported(g->model, tx, ty, grid_geom(g))))
       return invalid("3D k = 2 needs an AC/GS model, tile nx x 8 with nx = 128 or 256, ny %% 8 == 0");
   }
-  if (k_steps > 0 && g->dim == 2 && tile != kTileCluster2D && tile != kTileBands2D) {
+  const bool strip_tile = g->dim == 2 && tile >= kTileStrips2D && tile < kTileStrips2D + kNumStrips2D;
+  if (k_steps > 0 && g->dim == 2 && tile != kTileCluster2D && tile != kTileBands2D && !strip_tile) {
     const int model = g->model_set ? g->model : PF_MODEL_AC;
     if (!fe2d_supported(model, k_steps))
       return invalid("temporal blocking depth %d unsupported for this model", k_steps);
   }
-  if (g->stencil != PF_ST_STD && tile != kTileCluster2D && tile != kTileBands2D) {
+  if (g->stencil != PF_ST_STD && tile != kTileCluster2D && tile != kTileBands2D && !strip_tile) {
     const int t = tile >= 0 ? tile : 0;
     const int kk = k_steps > 0 ? k_steps : 1;
     const bool ok = g->dim == 2 ? fe2d_stencil_supported(g->stencil, t, kk)
@@ -741,6 +760,9 @@ int pf_get_tuning(pf_grid_t g, int* tile_x, int* tile_y, int* k_steps) {
   } else if (g->dim == 2 && g->tile == kTileBands2D) {
     tx = g->nx;
     ty = PF_TILE_BANDS;
+  } else if (g->dim == 2 && g->tile >= kTileStrips2D && g->tile < kTileStrips2D + kNumStrips2D) {
+    tx = g->tile == kTileStrips2D ? 128 : 64;
+    ty = PF_TILE_STRIPS;
   } else if (g->dim == 2) {
     tile2d_shape(g->tile, &tx, &ty);
   } else {
@@ -765,8 +787,8 @@ int pf_autotune(pf_grid_t g, int probe_launches, int* tile_x, int* tile_y, int* 
   PF_CUDA_TRY(cudaEventCreate(&e1));
   float best = INFINITY;
   int best_tile = g->tile, best_k = g->k;
-  // 2D: + the cluster kernel and the band kernel
-  const int ntiles = g->dim == 2 ? kNumTiles2D + 2 : kNumTiles3D;
+  // 2D: + the cluster kernel, the band kernel and the two strip widths
+  const int ntiles = g->dim == 2 ? kTileStrips2D + kNumStrips2D : kNumTiles3D;
   static const int ks[4] = {1, 2, 4, 8};  // 8: the cluster kernel only
   int rc = PF_OK;
   for (int t = 0; t < ntiles && rc == PF_OK; ++t) {

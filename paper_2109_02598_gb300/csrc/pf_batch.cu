@@ -4,8 +4,9 @@
 // the paper's multi-model driver (Sec. 2.4, "simultaneous-configs"), which runs a list of
 // models one after another on the CPU.
 //
-// Every instance runs the same tile body as the single-grid 2D kernel, so each instance's
-// state is bitwise identical to running it alone through pf_step with any tuning.
+// Every instance runs the same tile body (or strip body) as the single-grid 2D kernels, so
+// each instance's state is bitwise identical to running it alone through pf_step with any
+// tuning.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -32,8 +33,10 @@ struct pf_batch_s {
   pf::BatchInst* d_insts = nullptr;
   pf::BatchTile* d_tiles[pf::kNumTiles2D] = {};
   int ntiles[pf::kNumTiles2D] = {};
+  pf::BatchStrip* d_strips[3] = {};  // strip kernel work lists for k = 1, 2, 4
+  int nstrips[3] = {};
   int cur = 0;
-  int tile = 0;  // tile id in the 2D table
+  int tile = 0;  // tile id in the 2D table, or pf::kTileStrips2D (the strip kernel)
   int k = 1;
   // graph cache: one executable per starting buffer for the current (steps, tile, k)
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -75,7 +78,67 @@ static cudaError_t batch_tiles(pf_batch_s* b, int t) {
   return cudaSuccess;
 }
 
+static int kslot(int k) { return k == 4 ? 2 : k == 2 ? 1 : 0; }
+
+// Strip kernel work list for depth k: per instance (largest first), strips of 128 lanes'
+// columns over the width and one narrower strip for the remainder (64 or 32 columns where it
+// fits, else 64 plus 32), each cut into tasks of strip_task_rows rows; within a width, the
+// strips of one band of rows are consecutive, so neighbouring warps share halo columns.
+static cudaError_t batch_strips(pf_batch_s* b, int k) {
+  const int ks = kslot(k);
+  if (b->d_strips[ks] != nullptr) return cudaSuccess;
+  const int w4 = strip_out_cols(PF_MODEL_GS, k, 4), w2 = strip_out_cols(PF_MODEL_GS, k, 2);
+  const int w1 = strip_out_cols(PF_MODEL_GS, k, 1);
+  const int rows = strip_task_rows(PF_MODEL_GS, k);
+  if (w4 <= 0 || w2 <= 0 || w1 <= 0) return cudaErrorInvalidValue;
+  std::vector<int> order(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return b->nx[a] * b->ny[a] > b->nx[c] * b->ny[c];
+  });
+  std::vector<BatchStrip> list;
+  std::vector<std::pair<int, int>> strips;  // (x0, c) of one instance
+  for (int i : order) {
+    const int nx = (int)b->nx[i], ny = (int)b->ny[i];
+    strips.clear();
+    int x = 0;
+    for (; x + w4 <= nx; x += w4) strips.push_back({x, 4});
+    const int r = nx - x;
+    if (r > w2 + w1) {
+      strips.push_back({x, 4});
+    } else if (r > w2) {
+      strips.push_back({x, 2});
+      strips.push_back({x + w2, 1});
+    } else if (r > w1) {
+      strips.push_back({x, 2});
+    } else if (r > 0) {
+      strips.push_back({x, 1});
+    }
+    for (int y = 0; y < ny; y += rows)
+      for (const auto& st : strips)
+        list.push_back(BatchStrip{i, st.first, y, (short)std::min(rows, ny - y), (short)st.second});
+  }
+  // widest strips first: warps of one width run together, so an SM's warps share the code of
+  // one width rather than thrash the instruction cache with three
+  std::stable_sort(list.begin(), list.end(),
+                   [](const BatchStrip& a, const BatchStrip& c) { return a.c > c.c; });
+  if (list.size() > (size_t)INT32_MAX) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMalloc(&b->d_strips[ks], sizeof(BatchStrip) * list.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(b->d_strips[ks], list.data(), sizeof(BatchStrip) * list.size(),
+                 cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  b->nstrips[ks] = (int)list.size();
+  return cudaSuccess;
+}
+
 static cudaError_t batch_launch(pf_batch_s* b, int t, int k, int src, cudaStream_t s) {
+  if (t == kTileStrips2D) {
+    cudaError_t e = batch_strips(b, k);
+    if (e != cudaSuccess) return e;
+    return launch_batch_gs2d_strips(k, b->d_insts, b->d_strips[kslot(k)], b->nstrips[kslot(k)],
+                                    b->base[src], b->base[1 - src], s);
+  }
   cudaError_t e = batch_tiles(b, t);
   if (e != cudaSuccess) return e;
   return launch_batch_gs2d(t, k, b->d_insts, b->d_tiles[t], b->ntiles[t], b->base[src],
@@ -173,6 +236,8 @@ void pf_batch_destroy(pf_batch_t b) {
   drop_graphs(b);
   for (int t = 0; t < kNumTiles2D; ++t)
     if (b->d_tiles[t]) cudaFree(b->d_tiles[t]);
+  for (int i = 0; i < 3; ++i)
+    if (b->d_strips[i]) cudaFree(b->d_strips[i]);
   if (b->d_insts) cudaFree(b->d_insts);
   if (b->mem) cudaFree(b->mem);
   if (b->capture) cudaStreamDestroy(b->capture);
@@ -211,7 +276,10 @@ int pf_batch_read_field(pf_batch_t b, int inst, int field, float* dst, int on_de
 int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps) {
   if (int rc = check_batch(b)) return rc;
   int t = b->tile;
-  if (tile_x != 0 || tile_y != 0) {
+  if (tile_y == PF_TILE_STRIPS) {
+    if (tile_x != 128) return invalid("the batch's strip kernel takes tile 128 x PF_TILE_STRIPS");
+    t = kTileStrips2D;
+  } else if (tile_x != 0 || tile_y != 0) {
     t = tile2d_id(tile_x, tile_y);
     if (t < 0) return invalid("unsupported 2D tile %dx%d", tile_x, tile_y);
   }
@@ -224,8 +292,8 @@ int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps) {
 
 int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps) {
   if (int rc = check_batch(b)) return rc;
-  int tx, ty;
-  tile2d_shape(b->tile, &tx, &ty);
+  int tx = 128, ty = PF_TILE_STRIPS;
+  if (b->tile != kTileStrips2D) tile2d_shape(b->tile, &tx, &ty);
   if (tile_x) *tile_x = tx;
   if (tile_y) *tile_y = ty;
   if (k_steps) *k_steps = b->k;
@@ -244,7 +312,8 @@ int pf_batch_autotune(pf_batch_t b, int probe_launches, int* tile_x, int* tile_y
   int bt = b->tile, bk = b->k;
   static const int ks[3] = {1, 2, 4};
   cudaError_t e = cudaSuccess;
-  for (int t = 0; t < kNumTiles2D && e == cudaSuccess; ++t) {
+  for (int ti = 0; ti <= kNumTiles2D && e == cudaSuccess; ++ti) {
+    const int t = ti < kNumTiles2D ? ti : kTileStrips2D;  // the tiles, then the strip kernel
     for (int ki = 0; ki < 3 && e == cudaSuccess; ++ki) {
       const int k = ks[ki];
       e = batch_launch(b, t, k, b->cur, b->stream);  // warm-up (state unchanged)
@@ -277,7 +346,9 @@ int pf_batch_run(pf_batch_t b, int64_t n_steps) {
   if (n_steps == 0) return PF_OK;
   if (b->g_steps != n_steps || b->g_tile != b->tile || b->g_k != b->k) drop_graphs(b);
   if (b->exec[b->cur] == nullptr) {
-    cudaError_t e = batch_tiles(b, b->tile);  // allocate outside the capture
+    cudaError_t e = b->tile == kTileStrips2D ? cudaSuccess : batch_tiles(b, b->tile);
+    for (int k = b->k; k >= 1 && e == cudaSuccess && b->tile == kTileStrips2D; k >>= 1)
+      e = batch_strips(b, k);  // allocate outside the capture (every depth the plan uses)
     if (e != cudaSuccess) return cuda_fail(e, "pf_batch_run work list");
     PF_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
     int src = b->cur;

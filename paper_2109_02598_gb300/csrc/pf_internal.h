@@ -108,6 +108,14 @@ cudaError_t launch_fe2d_cluster(int model, int k, const Geom& q, FieldPtrs in, F
 constexpr int kTileBands2D = kNumTiles2D + 1;
 bool fe2d_bands_supported(int model, const Geom& q);
 
+// ---- 2D register-streaming kernel: one warp per strip of 32 C columns (pf_fe2d_strips.cu) --
+// tile ids kTileStrips2D (128 columns per warp, C = 4) and kTileStrips2D + 1 (64, C = 2)
+constexpr int kTileStrips2D = kNumTiles2D + 2;
+constexpr int kNumStrips2D = 2;
+bool fe2d_strips_supported(int model, int k);
+cudaError_t launch_fe2d_strips(int model, int lanes_cols, int k, const Geom& g, FieldPtrs in,
+                               FieldOut out, const ModelParams& m, cudaStream_t s);
+
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
 //           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);
@@ -130,6 +138,17 @@ struct BatchInst {
 struct BatchTile {
   int inst, x0, y0;
 };
+// A strip task of the batch (strip kernel): output columns from x0 of a strip of 32 c lanes'
+// columns (c = 4, 2 or 1), rows [y0, y0 + hy) of instance inst.
+struct BatchStrip {
+  int inst, x0, y0;
+  short hy, c;
+};
+int strip_out_cols(int model, int k, int c);  // output columns of a strip of 32 c columns
+int strip_task_rows(int model, int k);        // rows per batch strip task
+cudaError_t launch_batch_gs2d_strips(int k, const BatchInst* d_insts, const BatchStrip* d_tasks,
+                                     int ntasks, const float* in_base, float* out_base,
+                                     cudaStream_t s);
 cudaError_t prepare_batch_gs2d();  // set kernel attributes (call before any capture)
 cudaError_t launch_batch_gs2d(int tile_id, int k, const BatchInst* d_insts,
                               const BatchTile* d_tiles, int ntiles, const float* in_base,

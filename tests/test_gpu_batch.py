@@ -82,8 +82,10 @@ def test_batch_tunings_replays_and_autotune_agree_bitwise(pf):
         return out
 
     base = run((64, 16, 1), [12])
+    S = pf.PF_TILE_STRIPS
     for tuning, chunks in [((128, 16, 2), [12]), ((32, 32, 4), [5, 7]), ((128, 32, 4), [6, 6]),
-                           ((64, 16, 2), [3, 3, 3, 3]), ("auto", [12])]:
+                           ((64, 16, 2), [3, 3, 3, 3]), ((128, S, 4), [5, 7]),
+                           ((128, S, 2), [12]), ((128, S, 1), [4, 8]), ("auto", [12])]:
         got = run(tuning, chunks)
         for (a0, a1), (b0, b1) in zip(base, got):
             assert np.array_equal(a0, b0) and np.array_equal(a1, b1), tuning
@@ -193,3 +195,28 @@ def test_full_batch_every_instance_against_the_oracle(pf):
         for i in picks:
             err = _rel(thousand[i], long_ref[i].result(), "l2")
             assert err <= 1e-3, (i, sides[i], err)
+
+
+def test_full_batch_strip_kernel_is_bitwise_the_tiled_batch(pf):
+    # the 512-instance configuration: the strip kernel (mixed strip widths over every
+    # instance's width) gives every instance the bits of the tiled batch, at every depth
+    specs = synthetic.batch_instances(512, seed=4)
+    x0 = [synthetic.batch_instance_init(q["n"], i) for i, q in enumerate(specs)]
+
+    def run(tuning, steps):
+        b = pf.Batch([dict(n=q["n"], Du=0.2, Dv=0.1, F=q["F"], k=q["k"]) for q in specs], 0.5)
+        for i, (u, v) in enumerate(x0):
+            b.write(i, 0, u).write(i, 1, v)
+        b.set_tuning(*tuning)
+        b.run(steps)
+        out = [(b.read(i, 0), b.read(i, 1)) for i in range(len(specs))]
+        b.close()
+        return out
+
+    ref = run((32, 32, 4), 12)
+    for k in (4, 2, 1):
+        got = run((128, pf.PF_TILE_STRIPS, k), 12)
+        for i, ((a0, a1), (b0, b1)) in enumerate(zip(ref, got)):
+            assert np.array_equal(a0, b0) and np.array_equal(a1, b1), (i, specs[i]["n"], k)
+    with pytest.raises(pf.PfError, match="strip kernel"):
+        pf.Batch(make_specs([(16, 16)]), DT).set_tuning(64, pf.PF_TILE_STRIPS, 1)
