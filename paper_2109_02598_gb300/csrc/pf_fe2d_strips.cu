@@ -124,8 +124,15 @@ struct StripRun {
   static constexpr int NF = S::NF;
   static constexpr int R = S::R;
   static constexpr int NM = S::NM;
-  float w[K][NF][3][C];                // state of level s = 0..K-1
-  float mw[R == 2 ? K : 1][NM][3][C];  // radius 2: mu (and lap psi) of level s's state
+  float w[K][NF][3][C];                     // state of level s = 0..K-1
+  float mw[R == 2 ? K : 1][NM][3][C];       // radius 2: mu (and lap psi) of level s's state
+
+  // the task
+  FieldPtrs in;
+  FieldOut out;
+  int nx, ny, y0, hy, gx;
+  int64_t pitch;
+  bool st_lane, xin, xout;
 
   // Level s (1..K) at an iteration of phase P; its new row goes to o.
   template <int P, int s>
@@ -181,14 +188,15 @@ struct StripRun {
   // potential is valid from t = 5 s - 2, its state from 5 s, and the output needs it until
   // t = hy + 4 K + s - 1.
   static __device__ __forceinline__ int lo(int s) { return R == 1 ? 3 * s : 5 * s - 2; }
-  static __device__ __forceinline__ int hi(int s, int hy) { return hy + 2 * R * K + s; }
+  __device__ __forceinline__ int hi(int s) const { return hy + 2 * R * K + s; }
+  __device__ __forceinline__ int rows_in() const { return hy + 2 * R * K; }
 
   // Levels K-1 .. 1 at an iteration t of phase P (with G, levels outside their range are
   // skipped; without, every level is known to be in range).
   template <int P, bool G, int s>
-  __device__ __forceinline__ void inner_levels(int t, int hy, const ModelParams& m) {
+  __device__ __forceinline__ void inner_levels(int t, const ModelParams& m) {
     if constexpr (s >= 1) {
-      if (!G || (unsigned)(t - lo(s)) < (unsigned)(hi(s, hy) - lo(s))) {
+      if (!G || (unsigned)(t - lo(s)) < (unsigned)(hi(s) - lo(s))) {
         float o[NF][C];
         level<P, s>(m, o);
 #pragma unroll
@@ -196,7 +204,7 @@ struct StripRun {
 #pragma unroll
           for (int j = 0; j < C; ++j) w[s][f][P][j] = o[f][j];
       }
-      inner_levels<P, G, s - 1>(t, hy, m);
+      inner_levels<P, G, s - 1>(t, m);
     }
   }
 
@@ -205,10 +213,7 @@ struct StripRun {
   static constexpr int T0 = (2 * R + 1) * K;
 
   template <int P, bool G>
-  __device__ __forceinline__ void iteration(int t, const FieldPtrs& in, const FieldOut& out,
-                                            int nx, int ny, int64_t pitch, int gx, bool st_lane,
-                                            bool xin, bool xout, int y0, int hy,
-                                            const ModelParams& m) {
+  __device__ __forceinline__ void iteration(int t, const ModelParams& m) {
     // level K: output row y0 + t - T0 (radius 2: its chemical potential starts two
     // iterations before the first output row)
     if (!G || (unsigned)(t - lo(K)) < (unsigned)(T0 + hy - lo(K))) {
@@ -220,9 +225,9 @@ struct StripRun {
         for (int f = 0; f < NF; ++f) store_lane<C>(out.f[f] + row, gx, nx, xout, o[f]);
       }
     }
-    inner_levels<P, G, K - 1>(t, hy, m);
+    inner_levels<P, G, K - 1>(t, m);
     // level 0: input row ys + t, first read in the next iteration
-    if (!G || t < hy + 2 * R * K) {
+    if (!G || t < rows_in()) {
       const int64_t row = (int64_t)wrap_index(y0 - R * K + t, ny) * pitch;
 #pragma unroll
       for (int f = 0; f < NF; ++f) load_lane<C>(in.f[f] + row, gx, nx, xin, w[0][f][P]);
@@ -230,32 +235,39 @@ struct StripRun {
   }
 
   // Output rows [y0, y0 + hy) of the strip whose output columns start at x0.
-  __device__ __forceinline__ void run(const FieldPtrs& in, const FieldOut& out, int nx, int ny,
-                                      int64_t pitch, int x0, int y0, int hy,
+  __device__ __forceinline__ void run(const FieldPtrs& in_, const FieldOut& out_, int nx_,
+                                      int ny_, int64_t pitch_, int x0, int y0_, int hy_,
                                       const ModelParams& m) {
+    in = in_;
+    out = out_;
+    nx = nx_;
+    ny = ny_;
+    pitch = pitch_;
+    y0 = y0_;
+    hy = hy_;
     const int lane = threadIdx.x & 31;
-    const int gx = x0 - S::HXP + C * lane;
-    const bool st_lane = lane >= S::HXP / C && lane < (S::HXP + S::WO) / C;
+    gx = x0 - S::HXP + C * lane;
+    st_lane = lane >= S::HXP / C && lane < (S::HXP + S::WO) / C;
     // strips that reach past either end of the row (every strip of a narrow grid or batch
     // instance) take the periodic paths with the whole warp
-    const bool xin = __all_sync(0xffffffffu, gx >= 0 && gx + C <= nx);
-    const bool xout = __all_sync(0xffffffffu, !st_lane || gx + C <= nx);
-    const int t_main = hy + 2 * R * K;  // the input rows end here
+    xin = __all_sync(0xffffffffu, gx >= 0 && gx + C <= nx);
+    xout = __all_sync(0xffffffffu, !st_lane || gx + C <= nx);
+    const int t_main = rows_in();  // the input rows end here
     int t = 0;
     for (; t < T0; t += 3) {  // start-up: levels begin one after another
-      iteration<0, true>(t, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<1, true>(t + 1, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<2, true>(t + 2, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
+      iteration<0, true>(t, m);
+      iteration<1, true>(t + 1, m);
+      iteration<2, true>(t + 2, m);
     }
     for (; t + 3 <= t_main; t += 3) {  // steady state: every level, no range checks
-      iteration<0, false>(t, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<1, false>(t + 1, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<2, false>(t + 2, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
+      iteration<0, false>(t, m);
+      iteration<1, false>(t + 1, m);
+      iteration<2, false>(t + 2, m);
     }
     for (; t < T0 + hy; t += 3) {  // drain: levels finish one after another
-      iteration<0, true>(t, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<1, true>(t + 1, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
-      iteration<2, true>(t + 2, in, out, nx, ny, pitch, gx, st_lane, xin, xout, y0, hy, m);
+      iteration<0, true>(t, m);
+      iteration<1, true>(t + 1, m);
+      iteration<2, true>(t + 2, m);
     }
   }
 };
@@ -323,6 +335,7 @@ template <int MODEL, int K, int C>
 cudaError_t launch_strip(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
                          cudaStream_t s) {
   using S = StripCfg<MODEL, K, C>;
+  using Run = StripRun<MODEL, K, C>;
   static int resident[64] = {};  // resident warps of this kernel on the whole device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -337,7 +350,7 @@ cudaError_t launch_strip(const Geom& g, FieldPtrs in, FieldOut out, const ModelP
     resident[dev] = (b > 0 ? b : 1) * (sms > 0 ? sms : 1) * kStripWarps;
   }
   const int tasks_x = (g.nx + S::WO - 1) / S::WO;
-  const int hy = strip_rows(tasks_x, g.ny, resident[dev], 4 * StripRun<MODEL, K, C>::T0);
+  const int hy = strip_rows(tasks_x, g.ny, resident[dev], 4 * Run::T0);
   const int ntasks = tasks_x * ((g.ny + hy - 1) / hy);
   const int blocks = (ntasks + kStripWarps - 1) / kStripWarps;
   fe2d_strip_kernel<MODEL, K, C><<<blocks, kStripThreads, 0, s>>>(in, out, g, m, hy, tasks_x,
