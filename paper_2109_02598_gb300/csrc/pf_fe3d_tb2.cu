@@ -21,16 +21,19 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace pf {
 
 namespace {
 
-template <int MODEL, int W, int TY, int NS>
+template <int MODEL, int W, int TY, int NS, int V_ = 1>
 struct CfgB {
   static constexpr int NF = ModelTraits<MODEL>::NF;
   static constexpr int LX = W / 4;              // float4 columns per row
-  static constexpr int NT = LX * (TY + 2);      // one thread per first-level column
+  static constexpr int V = V_;                  // float4 columns per thread
+  static constexpr int TPR = LX / V;            // threads per row: one warp or two
+  static constexpr int NT = TPR * (TY + 2);     // one thread per first-level column group
   static constexpr int IN_ROWS = TY + 4;        // staged input rows (halo 2)
   static constexpr int IN_FIELD = IN_ROWS * W;  // floats per field per input stage
   static constexpr int IN_STAGE = NF * IN_FIELD;
@@ -40,17 +43,27 @@ struct CfgB {
   static constexpr uint32_t TX_BYTES = IN_STAGE * 4;
   static constexpr size_t SMEM =
       (size_t)(NS * IN_STAGE + 2 * L1_PLANE) * 4 + NS * 8 + 128;  // + barriers + align
-  static_assert(W % 32 == 0, "rows must be 128-byte multiples");
+  static_assert(TPR == 32 || TPR == 64, "a row is one warp or two");
 };
 
-// x-neighbour scalars of the float4 at column 4*x4 of a row of W floats (periodic). They
-// come from the centre float4 c that this thread already holds: the neighbouring lanes' c.w
-// and c.x by warp shuffle, and at the warp's two ends one load whose address is the same for
-// every lane (a broadcast). A warp covers 32 consecutive float4 columns of one row (W/4 is a
-// multiple of 32), so lanes 0 and 31 are the only ones whose neighbour lies in another warp.
-// Plain scalar loads of the two neighbours, four floats apart across the lanes, cost four
-// shared-memory wavefronts each (four lanes per bank); this costs two (GS 256^3: 484.5 ->
-// 501 GLUPS together with the ROWS schedule below).
+// x-neighbour scalars of a thread's V float4 columns 4 V lane .. 4 V lane + 4 V - 1 of a row
+// that one warp holds whole (the grid's full periodic row): the left neighbour of the first
+// column is the previous lane's last value, the right neighbour of the last column the next
+// lane's first value, lane 0 and lane 31 wrapping to each other. No shared-memory load: the
+// earlier layout (one float4 per thread, two warps per 256-wide row) took the values at the
+// warps' ends from shared memory, two loads per field and level.
+template <int V>
+__device__ __forceinline__ void x_edges_row(const float4 (&c)[V], float& xm, float& xp) {
+  const int lane = threadIdx.x & 31;
+  xm = __shfl_sync(0xffffffffu, c[V - 1].w, (lane + 31) & 31);
+  xp = __shfl_sync(0xffffffffu, c[0].x, (lane + 1) & 31);
+}
+
+// The same for a row that two warps share (one float4 column per thread, 256-wide rows):
+// the neighbouring lanes' c.w and c.x by warp shuffle, and at the warp's two ends one load
+// from the shared row whose address is the same for every lane (a broadcast). Plain scalar
+// loads of the two neighbours, four floats apart across the lanes, cost four shared-memory
+// wavefronts each (four lanes per bank); this costs two.
 template <int W>
 __device__ __forceinline__ void x_edges_c(const float* row, int x4, const float4& c, float& xm,
                                           float& xp) {
@@ -113,13 +126,108 @@ struct Tb2Sched {
 };
 constexpr int kTb2Items = 0, kTb2Balanced = 1, kTb2Rows = 2;
 
-template <int MODEL, int W, int TY, int NS>
-__global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
+// Per-thread state of one z-stream: z-windows of the input planes (level 1's z-neighbours and
+// centre) and of the first-level planes (level 2's), three slots each, slot = plane mod 3, so
+// the plane loop, unrolled by three, renames them instead of moving them.
+template <int MODEL, int W, int TY, int NS, int V_>
+struct Tb2Stream {
+  using C = CfgB<MODEL, W, TY, NS, V_>;
+  static constexpr int NF = C::NF;
+  static constexpr int V = C::V;
+  float4 iw[NF][3][V];  // input planes
+  float4 lw[NF][3][V];  // first-level planes
+
+  // Laplacians of the thread's V float4 columns: centre c (row `row` of a shared plane, read
+  // only where two warps share the row), rows above / below, z-neighbours.
+  __device__ __forceinline__ static void laps(const float4 (&c)[V], const float* row, int col0,
+                                              const float4 (&ym)[V], const float4 (&yp)[V],
+                                              const float4 (&zm)[V], const float4 (&zp)[V],
+                                              float lap_scale, float4 (&l)[V]) {
+    float xm, xp;
+    if constexpr (C::TPR == 32)
+      x_edges_row<V>(c, xm, xp);
+    else
+      x_edges_c<W>(row, col0 / 4, c[0], xm, xp);
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+      l[i] = lap3d_x4<MODEL>(c[i], ym[i], yp[i], zm[i], zp[i], i == 0 ? xm : c[i - 1].w,
+                             i == V - 1 ? xp : c[i + 1].x, lap_scale);
+  }
+
+  // Plane iteration j (phase P = j mod 3): level 1 on row r of first-level plane j from
+  // input planes j (slot P), j + 1 (P + 1, centre) and j + 2 (P + 2, read from stage sp
+  // now), into lw slot P and the shared plane l1w; then, for j >= 2 on rows 1 .. TY, level 2
+  // of output plane j - 2 from first-level planes j - 2 (P + 1), j - 1 (P + 2, with its
+  // y-neighbours from the shared plane l1r) and j (P), stored to HBM at off.
+  template <int P>
+  __device__ __forceinline__ void step(const float* sc, const float* sp, float* l1w,
+                                       const float* l1r, int r, int col0, bool level2,
+                                       const FieldOut& out, int64_t off, const ModelParams& m) {
+    constexpr int S0 = P, S1 = (P + 1) % 3, S2 = (P + 2) % 3;
+    float4 lap[NF][V];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const float* F = sc + f * C::IN_FIELD;
+      float4 ym[V], yp[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        ym[i] = *reinterpret_cast<const float4*>(F + r * W + col0 + 4 * i);
+        yp[i] = *reinterpret_cast<const float4*>(F + (r + 2) * W + col0 + 4 * i);
+        iw[f][S2][i] = *reinterpret_cast<const float4*>(sp + f * C::IN_FIELD + (r + 1) * W +
+                                                        col0 + 4 * i);
+      }
+      laps(iw[f][S1], F + (r + 1) * W, col0, ym, yp, iw[f][S0], iw[f][S2], m.lap_scale, lap[f]);
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      float4 c[NF], l[NF], res[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        c[f] = iw[f][S1][i];
+        l[f] = lap[f][i];
+      }
+      update4<MODEL>(c, l, res, m);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        lw[f][S0][i] = res[f];
+        *reinterpret_cast<float4*>(l1w + f * C::L1_FIELD + r * W + col0 + 4 * i) = res[f];
+      }
+    }
+    if (!level2) return;
+    float4 lap2[NF][V];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const float* F = l1r + f * C::L1_FIELD;
+      float4 ym[V], yp[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        ym[i] = *reinterpret_cast<const float4*>(F + (r - 1) * W + col0 + 4 * i);
+        yp[i] = *reinterpret_cast<const float4*>(F + (r + 1) * W + col0 + 4 * i);
+      }
+      laps(lw[f][S2], F + r * W, col0, ym, yp, lw[f][S1], lw[f][S0], m.lap_scale, lap2[f]);
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      float4 c[NF], l[NF], res[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        c[f] = lw[f][S2][i];
+        l[f] = lap2[f][i];
+      }
+      update4<MODEL>(c, l, res, m);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(out.f[f] + off + 4 * i) = res[f];
+    }
+  }
+};
+
+template <int MODEL, int W, int TY, int NS, int V_>
+__global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS, V_>::NT, 1)
     fe3d_tb2_kernel(const __grid_constant__ Tb2Maps maps, FieldOut out, Geom g, ModelParams m,
                     Tb2Sched sc_, int* err_flag) {
-  using C = CfgB<MODEL, W, TY, NS>;
+  using C = CfgB<MODEL, W, TY, NS, V_>;
   constexpr int NF = C::NF;
-  constexpr int LX = C::LX;
+  constexpr int V = C::V;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_sa = smem_addr(smem_raw);
   float* ring = reinterpret_cast<float*>(smem_raw + ((128 - (base_sa & 127)) & 127));
@@ -127,9 +235,9 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(l1 + 2 * C::L1_PLANE);
 
   const int tid = threadIdx.x;
-  const int x4 = tid % LX;
-  const int r = tid / LX;  // first-level row y0 - 1 + r; input row r + 1
-  const bool second = (r >= 1 && r <= TY);
+  const int r = tid / C::TPR;             // first-level row y0 - 1 + r; input row r + 1
+  const int col0 = 4 * V * (tid % C::TPR);  // first column of this thread's V float4 columns
+  const bool second = (r >= 1 && r <= TY);  // the same in the whole warp
   canary_fill(ring, (size_t)NS * C::IN_STAGE + 2 * C::L1_PLANE);  // TMA issues follow a proxy fence
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -176,6 +284,7 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
     pos = (int)((int64_t)units * p / np);
     pos_end = (int)((int64_t)units * (p + 1) / np);
   }
+  Tb2Stream<MODEL, W, TY, NS, V_> zs;
   for (;;) {
     int col, zlo, zhi, dir;
     if (sc_.mode == kTb2Items || (sc_.mode == kTb2Rows && (int)blockIdx.x < nfull)) {
@@ -215,44 +324,48 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
       for (int i = 0; i < n0; ++i) issue(q_base + i, y0, in_plane(i));
       q_issued = q_base + n0;
     }
-    // prologue: centre values of input planes 0 and 1 for this thread's column
-    float4 izm[NF], ic[NF], lzm[NF], lc[NF];
+    // prologue: this thread's columns of input planes 0 and 1 (window slots 0 and 1)
     err = !wait(q_base);
     if (!err) {
       const float* st = stage_ptr(q_base);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        izm[f] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          zs.iw[f][0][i] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W +
+                                                            col0 + 4 * i);
     }
     if (!err) err = !wait(q_base + 1);
     if (!err) {
       const float* st = stage_ptr(q_base + 1);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        ic[f] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          zs.iw[f][1][i] = *reinterpret_cast<const float4*>(st + f * C::IN_FIELD + (r + 1) * W +
+                                                            col0 + 4 * i);
     }
-    // first-level index j = 0 .. n+1 is plane zfirst + (j-1) dir, from input planes j, j+1,
-    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2 (o and o+2 in
-    // registers, o+1 in shared memory). The stages of input planes j+1, j+2 and the
-    // mbarrier phase of j+2 advance incrementally instead of by division.
-    uint32_t s1 = (q_base + 1) % NS, s2 = (q_base + 2) % NS;
-    uint32_t ph2 = ((q_base + 2) / NS) & 1u;
-    // Two first-level planes suffice: iteration j writes plane j into the slot of plane
+    // first-level plane j = 0 .. n+1 is plane zfirst + (j-1) dir, from input planes j, j+1,
+    // j+2; second-level output o = j - 2 uses first-level planes o, o+1, o+2 (in registers,
+    // o+1's rows above and below from shared memory). The stages of input planes j+1, j+2 and
+    // the mbarrier phase of j+2 advance incrementally instead of by division. Two first-level
+    // planes in shared memory suffice: iteration j writes plane j into the slot of plane
     // j - 2, which iteration j - 1 read last, and the barrier at the top of iteration j
     // separates the two.
-    float* l1w = l1;                       // first-level plane j
-    float* l1r = l1 + C::L1_PLANE;         // and j - 1
-    for (int j = 0; j < n + 2; ++j) {
-      if (__syncthreads_or(err)) break;
+    uint32_t s1 = (q_base + 1) % NS, s2 = (q_base + 2) % NS;
+    uint32_t ph2 = ((q_base + 2) / NS) & 1u;
+    // one plane iteration of phase P; false: stop (a wait ran out somewhere in the CTA)
+    auto plane = [&](auto phase, int j) -> bool {
+      constexpr int P = decltype(phase)::value;
+      if (__syncthreads_or(err)) return false;
       if (tid == 0 && j + NS < nin) {
         fence_proxy_async_smem();
         issue(q_base + j + NS, y0, in_plane(j + NS));
         q_issued = q_base + j + NS + 1;
       }
       err = !mbar_wait_bounded(&bars[s2], ph2, kWaitBudgetCycles);
-      err = __any_sync(0xffffffffu, err);  // the shuffles below need the whole warp
-      if (err) continue;
-      // ---- first level on row r of plane j (input centre plane j+1)
+      err = __any_sync(0xffffffffu, err);  // the shuffles need the whole warp
+      if (err) return true;                // the next barrier stops the CTA
       const float* sc = ring + s1 * C::IN_STAGE;
       const float* sp = ring + s2 * C::IN_STAGE;
       s1 = s2;
@@ -260,52 +373,18 @@ __global__ void __launch_bounds__(CfgB<MODEL, W, TY, NS>::NT, 1)
         s2 = 0;
         ph2 ^= 1u;
       }
-      float4 izp[NF], lap[NF], l1v[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const float* F = sc + f * C::IN_FIELD;
-        const float4 ym = *reinterpret_cast<const float4*>(F + r * W + 4 * x4);
-        const float4 yp = *reinterpret_cast<const float4*>(F + (r + 2) * W + 4 * x4);
-        izp[f] = *reinterpret_cast<const float4*>(sp + f * C::IN_FIELD + (r + 1) * W + 4 * x4);
-        float xm, xp;
-        x_edges_c<W>(F + (r + 1) * W, x4, ic[f], xm, xp);
-        lap[f] = lap3d_x4<MODEL>(ic[f], ym, yp, izm[f], izp[f], xm, xp, m.lap_scale);
-      }
-      update4<MODEL>(ic, lap, l1v, m);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        *reinterpret_cast<float4*>(l1w + f * C::L1_FIELD + r * W + 4 * x4) = l1v[f];
-        izm[f] = ic[f];
-        ic[f] = izp[f];
-      }
-      // ---- second level for output o = j - 2: centre is first-level plane j-1, whose
-      // rows were completed before this iteration's barrier
-      if (j >= 2 && second) {
-        const float* lp = l1r;
-        float4 lap2[NF], res[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const float* F = lp + f * C::L1_FIELD;
-          const float4 ym = *reinterpret_cast<const float4*>(F + (r - 1) * W + 4 * x4);
-          const float4 yp = *reinterpret_cast<const float4*>(F + (r + 1) * W + 4 * x4);
-          float xm, xp;
-          x_edges_c<W>(F + r * W, x4, lc[f], xm, xp);
-          lap2[f] = lap3d_x4<MODEL>(lc[f], ym, yp, lzm[f], l1v[f], xm, xp, m.lap_scale);
-        }
-        update4<MODEL>(lc, lap2, res, m);
-        const int z = zfirst + (j - 2) * dir;
-        const int64_t off = (int64_t)z * g.plane + (int64_t)(y0 + r - 1) * g.pitch + 4 * x4;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) *reinterpret_cast<float4*>(out.f[f] + off) = res[f];
-      }
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        lzm[f] = lc[f];
-        lc[f] = l1v[f];
-      }
-      float* const t = l1r;
-      l1r = l1w;
-      l1w = t;
+      float* l1w = l1 + (j & 1) * C::L1_PLANE;        // first-level plane j
+      const float* l1r = l1 + ((j + 1) & 1) * C::L1_PLANE;  // and j - 1
+      const int z = zfirst + (j - 2) * dir;
+      const int64_t off = (int64_t)z * g.plane + (int64_t)(y0 + r - 1) * g.pitch + col0;
+      zs.template step<P>(sc, sp, l1w, l1r, r, col0, j >= 2 && second, out, off, m);
+      return true;
+    };
+    const int nj = n + 2;
+    for (int j = 0; j < nj; j += 3) {
+      if (!plane(std::integral_constant<int, 0>(), j)) break;
+      if (j + 1 >= nj || !plane(std::integral_constant<int, 1>(), j + 1)) break;
+      if (j + 2 >= nj || !plane(std::integral_constant<int, 2>(), j + 2)) break;
     }
     q_base += nin;
   }
@@ -374,10 +453,10 @@ Tb2Sched tb2_schedule(int ncols, int nz, long long slots, long long* grid_out) {
   return s;
 }
 
-template <int MODEL, int W, int TY, int NS>
+template <int MODEL, int W, int TY, int NS, int V = 1>
 cudaError_t launch_tb2(pf_grid_s* gr, const Tb2Maps& maps, FieldOut out, cudaStream_t st) {
-  using C = CfgB<MODEL, W, TY, NS>;
-  auto kern = fe3d_tb2_kernel<MODEL, W, TY, NS>;
+  using C = CfgB<MODEL, W, TY, NS, V>;
+  auto kern = fe3d_tb2_kernel<MODEL, W, TY, NS, V>;
   static unsigned long long attr_mask = 0;  // per instantiation and device
   cudaError_t e = ensure_smem_attr(kern, C::SMEM, &attr_mask);
   if (e != cudaSuccess) return e;
