@@ -184,6 +184,10 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * 3D tiles 32x16, 64x8 (general kernel, every model and size) and 64x16, 128x8, 128x16
  * (TMA-staged kernel: AC and GS with nx % tile_x == 0 and ny % tile_y == 0); k = 1;
  * 3D k = 2 with tile nx x 8 (nx = 128 or 256; AC and GS).
+ * 3D tile 32x8 selects the box kernel (Models B and C, k = 1 or 2, nx % 4 == 0, any ny and
+ * nz): a CTA stages a whole 32 x 8 x 8 box with a halo of 2 k and runs k steps on regions that
+ * shrink to the box (the chemical potential one site wider than each step's result); for
+ * small grids (64^3), where the z-streaming kernels' plane-by-plane walk is the step's time.
  * 2D tile nx x (ny / CS) selects the on-chip cluster kernel (standard stencil, nx % 4 == 0,
  * ny % CS == 0, the grid in CS CTAs' shared memory; CS = 16 where the device allows clusters
  * of 16, else 8; k in {1, 2, 4, 8} for AC and GS, {1, 2} for CH and C, with k R <= ny / CS):

@@ -207,6 +207,7 @@ bool tile_supported(pf_grid_s* g, int tile, int k) {
     return g->stencil == PF_ST_STD && fe2d_strips_supported(g->model, k);
   if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
   if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
+  if (tile == kTileBox3D) return fe3d_box_supported(g->model, k, grid_geom(g));
   int tx, ty;
   tile3d_shape(tile, &tx, &ty);
   if (k == 2) return fe3d_tb2_supported(g->model, tx, ty, grid_geom(g));
@@ -260,6 +261,7 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
                               g->params, st);
   if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
   if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
+  if (tile == kTileBox3D) return launch_fe3d_box(g->model, k, q, in, out, g->params, st);
   if (k == 2) {
     int tx, ty;
     tile3d_shape(tile, &tx, &ty);
@@ -720,7 +722,7 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
   }
   if (k_steps < 0) return invalid("k_steps must be >= 0");
   if (g->dim == 3 && k_steps > 2) return invalid("3D grids support k = 1 and 2");
-  if (g->dim == 3 && k_steps == 2) {
+  if (g->dim == 3 && k_steps == 2 && tile != kTileBox3D) {
     int tx = tile_x, ty = tile_y;
     if (tile < 0) return invalid("k = 2 in 3D needs an explicit tile (nx x 8, nx = 128 or 256)");
     if (!(g->model_set && fe3d_tb2_supported(g->model, tx, ty, grid_geom(g))))
@@ -741,10 +743,15 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
       return invalid("this stencil runs with 2D tiles 64x16 or 128x32 and k <= 2, or 3D tiles "
                      "32x16 or 64x8 and k = 1");
   }
-  if (g->dim == 3 && k_steps != 2 && tile >= kFirstTmaTile3D &&
-      !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g))))
+  if (g->dim == 3 && tile == kTileBox3D) {
+    if (!(g->model_set && fe3d_box_supported(g->model, k_steps > 0 ? k_steps : 1, grid_geom(g))))
+      return invalid("3D tile 32x8 (the box kernel) needs Model B or C, k = 1 or 2 and "
+                     "nx %% 4 == 0");
+  } else if (g->dim == 3 && k_steps != 2 && tile >= kFirstTmaTile3D &&
+             !(g->model_set && fe3d_tma_supported(g->model, tile - kFirstTmaTile3D, grid_geom(g)))) {
     return invalid("3D tile %dx%d needs nx %% %d == 0 and ny %% %d == 0", tile_x, tile_y,
                    tile_x, tile_y);
+  }
   g->req_tile = tile;
   g->req_k = k_steps;
   drop_graphs(g);

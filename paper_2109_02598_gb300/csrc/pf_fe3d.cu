@@ -275,8 +275,8 @@ cudaError_t launch3_tile(int tile_id, const Geom& g, FieldPtrs in, FieldOut out,
 }  // namespace
 
 void tile3d_shape(int tile_id, int* tx, int* ty) {
-  static const int s[kNumTiles3D][2] = {{32, 16}, {64, 8},   {64, 16},
-                                        {128, 8}, {128, 16}, {256, 8}};
+  static const int s[kNumTiles3D][2] = {{32, 16}, {64, 8},   {64, 16}, {128, 8},
+                                        {128, 16}, {256, 8}, {32, 8}};
   *tx = s[tile_id][0];
   *ty = s[tile_id][1];
 }

@@ -120,8 +120,14 @@ cudaError_t launch_fe2d_strips(int model, int lanes_cols, int k, const Geom& g, 
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);
 //           2 = 64x16, 3 = 128x8, 4 = 128x16 (TMA kernel, AC/GS, nx % TX == ny % TY == 0);
 //           with k = 2: 3 = 128x8 and 5 = 256x8 (depth-2 TMA kernel, AC/GS, nx == TX).
-constexpr int kNumTiles3D = 6;
+//           6 = 32x8: the box kernel (Models B and C, nx % 4 == 0, k = 1 or 2; whole
+//           32x8x8 boxes per CTA).
+constexpr int kNumTiles3D = 7;
 constexpr int kFirstTmaTile3D = 2;
+constexpr int kTileBox3D = 6;
+bool fe3d_box_supported(int model, int k, const Geom& g);
+cudaError_t launch_fe3d_box(int model, int k, const Geom& g, FieldPtrs in, FieldOut out,
+                            const ModelParams& m, cudaStream_t s);
 void tile3d_shape(int tile_id, int* tx, int* ty);
 int tile3d_id(int tx, int ty);
 cudaError_t launch_fe3d(int model, int tile_id, const Geom& g, FieldPtrs in, FieldOut out,

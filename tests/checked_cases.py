@@ -9,7 +9,7 @@ that stages through shared memory:
 * the 2D tile body for every model, tile and depth on ragged grids;
 * the other 2D stencils;
 * the cluster and band kernels;
-* the general, TMA and depth-2 3D kernels;
+* the general, TMA, depth-2 and box 3D kernels;
 * the batch;
 * the adjoints.
 
@@ -98,6 +98,9 @@ def run_cases(pf):
         for tile in ((64, 16), (128, 8)):
             res[f"3d_tma_r2_{model}_{tile[0]}x{tile[1]}"] = run_grid(
                 pf, model, (9, 32, 128), 5, (tile[0], tile[1], 1))
+    for model in ("ch", "c"):  # the box kernel, both depths, boxes past every edge
+        for k in (1, 2):
+            res[f"3d_box_{model}_k{k}"] = run_grid(pf, model, (11, 13, 36), 5, (32, 8, k))
     # the batch
     shapes = [(64, 64), (97, 130), (5, 7), (33, 300)]
     specs = [dict(ny=s[0], nx=s[1], Du=0.2, Dv=0.1, F=0.03 + 0.005 * i, k=0.05 + 0.003 * i)
