@@ -103,6 +103,14 @@ __device__ __forceinline__ void store_lane(float* row, int gx, int nx, bool xout
   }
 }
 
+// Packed FP32 pairs (one instruction updates two sites, each lane's result the scalar
+// operation's bits; the *4 helpers of pf_model.cuh) where they measured faster: Gray-Scott
+// with 64-column strips (Gray-Scott 4096^2: 808 -> 879 GLUPS) and Allen-Cahn with 128-column
+// strips (Allen-Cahn 4096^2: 1340 -> 1483). Gray-Scott with 128-column strips measured slower
+// with them (791 -> 731), Allen-Cahn with 64-column strips the same.
+template <int MODEL, int C>
+constexpr bool kStripPacked = (MODEL == PF_MODEL_GS && C == 2) || (MODEL == PF_MODEL_AC && C == 4);
+
 // Laplacians of a lane's C sites from the rows above (u), at (c) and below (d); the x
 // neighbours beyond the lane come from the adjacent lanes.
 template <int MODEL, int C>
@@ -110,11 +118,30 @@ __device__ __forceinline__ void lap_lane(const float (&u)[C], const float (&c)[C
                                          const float (&d)[C], float scale, float (&l)[C]) {
   const float xl = __shfl_up_sync(0xffffffffu, c[C - 1], 1);
   const float xr = __shfl_down_sync(0xffffffffu, c[0], 1);
+  if constexpr (kStripPacked<MODEL, C> && C == 4) {
+    float4 r = lap2d_sum4(make_float4(c[0], c[1], c[2], c[3]), xl, xr,
+                          make_float4(u[0], u[1], u[2], u[3]),
+                          make_float4(d[0], d[1], d[2], d[3]));
+    if constexpr (MODEL != PF_MODEL_GS) r = mul4(scale, r);
+    l[0] = r.x;
+    l[1] = r.y;
+    l[2] = r.z;
+    l[3] = r.w;
+  } else if constexpr (kStripPacked<MODEL, C> && C == 2) {
+    // lap2d_sum of two sites: (xm + xp) + (ym + yp), then -4 c + that
+    const float2 sx = make_float2(__fadd_rn(xl, c[1]), __fadd_rn(c[0], xr));
+    const float2 sy = __fadd2_rn(make_float2(u[0], u[1]), make_float2(d[0], d[1]));
+    float2 r = __ffma2_rn(make_float2(-4.0f, -4.0f), make_float2(c[0], c[1]), __fadd2_rn(sx, sy));
+    if constexpr (MODEL != PF_MODEL_GS) r = __fmul2_rn(make_float2(scale, scale), r);
+    l[0] = r.x;
+    l[1] = r.y;
+  } else {
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const float left = j == 0 ? xl : c[j - 1];
-    const float right = j == C - 1 ? xr : c[j + 1];
-    l[j] = lap_scaled<MODEL>(lap2d_sum(c[j], left, right, u[j], d[j]), scale);
+    for (int j = 0; j < C; ++j) {
+      const float left = j == 0 ? xl : c[j - 1];
+      const float right = j == C - 1 ? xr : c[j + 1];
+      l[j] = lap_scaled<MODEL>(lap2d_sum(c[j], left, right, u[j], d[j]), scale);
+    }
   }
 }
 
@@ -141,15 +168,39 @@ struct StripRun {
     if constexpr (MODEL == PF_MODEL_AC) {
       float l[C];
       lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, l);
+      if constexpr (kStripPacked<MODEL, C> && C == 4) {
+        const float(&p)[C] = w[s - 1][0][sc];
+        const float4 r = ac_update4(make_float4(p[0], p[1], p[2], p[3]),
+                                    make_float4(l[0], l[1], l[2], l[3]), m);
+        o[0][0] = r.x;
+        o[0][1] = r.y;
+        o[0][2] = r.z;
+        o[0][3] = r.w;
+      } else {
 #pragma unroll
-      for (int j = 0; j < C; ++j) o[0][j] = ac_update(w[s - 1][0][sc][j], l[j], m);
+        for (int j = 0; j < C; ++j) o[0][j] = ac_update(w[s - 1][0][sc][j], l[j], m);
+      }
     } else if constexpr (MODEL == PF_MODEL_GS) {
       float lu[C], lv[C];
       lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, lu);
       lap_lane<MODEL, C>(w[s - 1][1][su], w[s - 1][1][sc], w[s - 1][1][sd], m.lap_scale, lv);
+      if constexpr (kStripPacked<MODEL, C> && C == 2) {
+        // the pair twice over in a float4 (gs_update4), the copy discarded
+        const float(&u)[C] = w[s - 1][0][sc];
+        const float(&v)[C] = w[s - 1][1][sc];
+        float4 un, vn;
+        gs_update4(make_float4(u[0], u[1], u[0], u[1]), make_float4(v[0], v[1], v[0], v[1]),
+                   make_float4(lu[0], lu[1], lu[0], lu[1]), make_float4(lv[0], lv[1], lv[0], lv[1]),
+                   m, un, vn);
+        o[0][0] = un.x;
+        o[0][1] = un.y;
+        o[1][0] = vn.x;
+        o[1][1] = vn.y;
+      } else {
 #pragma unroll
-      for (int j = 0; j < C; ++j)
-        gs_update(w[s - 1][0][sc][j], w[s - 1][1][sc][j], lu[j], lv[j], m, o[0][j], o[1][j]);
+        for (int j = 0; j < C; ++j)
+          gs_update(w[s - 1][0][sc][j], w[s - 1][1][sc][j], lu[j], lv[j], m, o[0][j], o[1][j]);
+      }
     } else {
       // chemical potential (Model C: and lap psi) of level s - 1's centre row, into slot P
       float(&mu)[3][C] = mw[s - 1][0];
