@@ -435,6 +435,9 @@ def summary_line(line) -> str:
         a = c["adjoint_gs2d_512"]
         parts.append(f"batched 512x {b['glups']:.1f} GLUPS = {b['vs_plain_gs2d_4096']:.3f} x plain "
                      f"4096^2 ({c['plain_gs2d_4096']['glups']:.1f})")
+        if "vs_plain_gs2d_512" in b:
+            parts.append(f"= {b['vs_plain_gs2d_512']:.3f} x plain 512^2 "
+                         f"({c['plain_gs2d_512']['glups']:.1f})")
         parts.append(f"adjoint 512^2x2000 = {a['ratio_vs_plain']:.2f} x plain forward")
         for k in ("ch2d_2048", "ch2d_8192", "ac2d_128"):
             if k in c:
@@ -520,8 +523,8 @@ def _time(stream, fn, reps=1):
 
 def companions(stream, hbm):
     """The other workloads, each timed on the device: the 512-instance batched Gray-Scott
-    run against a plain 2D grid, the adjoint against the plain forward run at the same
-    size, and the Cahn-Hilliard 2048^2 and 8192^2 and Allen-Cahn 128^2 steps."""
+    run against plain 2D grids of 4096^2 and 512^2, the adjoint against the plain forward run
+    at the same size, and the Cahn-Hilliard 2048^2 and 8192^2 and Allen-Cahn 128^2 steps."""
     import torch
     import paper_2109_02598_gb300 as pf
     out = {}
@@ -539,6 +542,17 @@ def companions(stream, hbm):
         pglups = 4096 * 4096 * 200 / (ms * 1e-3) / 1e9
         out["plain_gs2d_4096"] = {"glups": pglups, "tuning": list(t2)}
         out["batched_gs2d_512x"]["vs_plain_gs2d_4096"] = bglups / pglups
+        g.close()
+        # ---- and a plain 512^2 grid, the size of the batch's largest instances
+        u, v = synthetic.gray_scott_init((512, 512), seed=10, n_seeds=16, side=8)
+        g = pf.Grid((512, 512), 2, stream=stream).set_model("gs", (0.2, 0.1, 0.04, 0.06), 0.5)
+        g.write_fields((u, v))
+        t5 = g.autotune(5)
+        g.step(2000)  # records the graph of this run length
+        ms = _time(stream, lambda: g.step(2000))
+        p5 = 512 * 512 * 2000 / (ms * 1e-3) / 1e9
+        out["plain_gs2d_512"] = {"glups": p5, "tuning": list(t5)}
+        out["batched_gs2d_512x"]["vs_plain_gs2d_512"] = bglups / p5
         g.close()
         # ---- adjoint 512^2, 2000 steps, sqrt(N) checkpoints vs the plain forward run
         out["adjoint_gs2d_512"] = adjoint_timing(stream, 512, 2000)
