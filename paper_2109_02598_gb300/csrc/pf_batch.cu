@@ -8,6 +8,7 @@
 // each instance's state is bitwise identical to running it alone through pf_step with any
 // tuning.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -82,25 +83,64 @@ static int kslot(int k) { return k == 4 ? 2 : k == 2 ? 1 : 0; }
 
 // Strip kernel work list for depth k: per instance (largest first), strips of 128 lanes'
 // columns over the width and one narrower strip for the remainder (64 or 32 columns where it
-// fits, else 64 plus 32), each cut into tasks of strip_task_rows rows; within a width, the
-// strips of one band of rows are consecutive, so neighbouring warps share halo columns.
+// fits, else 64 plus 32), each cut into tasks of hy rows; widest strips first (warps of one
+// width then run together and share their code in the instruction cache), and within a
+// width the strips of one band of rows are consecutive, so neighbouring warps share halo
+// columns.
+//
+// The task height hy is chosen for the launch as a whole. The device starts the one-warp
+// tasks in list order as warps finish, so a list a little longer than a whole number of
+// waves leaves most warps idle while the last tasks run (one 4096^2 instance: 3010 tasks of
+// 48 rows on 2432 resident warps ran 46 % slower than 2415 tasks of 60 rows). Each
+// candidate height's list is played through that dispatch on the resident warps, with a
+// task costing its iterations (rows + the levels' start-up) times its strip's width
+// weight, and the shortest makespan wins (the taller height on a tie).
+struct StripPlan {
+  std::vector<std::vector<std::pair<int, int>>> strips;  // per instance: (x0, c)
+  std::vector<int> order;                                // instances, largest first
+};
+
+static double strip_makespan(const pf_batch_s* b, const StripPlan& plan, int hy, int k,
+                             int resident, std::vector<double>& slots) {
+  static const double weight[5] = {0, 0.4, 0.6, 0, 1.0};  // per strip width c = 1, 2, 4
+  slots.assign((size_t)resident, 0.0);
+  std::make_heap(slots.begin(), slots.end(), std::greater<double>());
+  double span = 0;
+  for (int c : {4, 2, 1}) {
+    for (int i : plan.order) {
+      const int ny = (int)b->ny[i];
+      for (int y = 0; y < ny; y += hy) {
+        const double cost = (std::min(hy, ny - y) + 3.0 * k) * weight[c];
+        for (const auto& st : plan.strips[i]) {
+          if (st.second != c) continue;
+          std::pop_heap(slots.begin(), slots.end(), std::greater<double>());
+          slots.back() += cost;
+          span = std::max(span, slots.back());
+          std::push_heap(slots.begin(), slots.end(), std::greater<double>());
+        }
+      }
+    }
+  }
+  return span;
+}
+
 static cudaError_t batch_strips(pf_batch_s* b, int k) {
   const int ks = kslot(k);
   if (b->d_strips[ks] != nullptr) return cudaSuccess;
   const int w4 = strip_out_cols(PF_MODEL_GS, k, 4), w2 = strip_out_cols(PF_MODEL_GS, k, 2);
   const int w1 = strip_out_cols(PF_MODEL_GS, k, 1);
-  const int rows = strip_task_rows(PF_MODEL_GS, k);
   if (w4 <= 0 || w2 <= 0 || w1 <= 0) return cudaErrorInvalidValue;
-  std::vector<int> order(b->n);
-  for (int i = 0; i < b->n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+  StripPlan plan;
+  plan.order.resize(b->n);
+  for (int i = 0; i < b->n; ++i) plan.order[i] = i;
+  std::stable_sort(plan.order.begin(), plan.order.end(), [&](int a, int c) {
     return b->nx[a] * b->ny[a] > b->nx[c] * b->ny[c];
   });
-  std::vector<BatchStrip> list;
-  std::vector<std::pair<int, int>> strips;  // (x0, c) of one instance
-  for (int i : order) {
-    const int nx = (int)b->nx[i], ny = (int)b->ny[i];
-    strips.clear();
+  plan.strips.resize(b->n);
+  int64_t strip_rows_total = 0;  // rows of every strip: the task count at hy = 1
+  for (int i = 0; i < b->n; ++i) {
+    auto& strips = plan.strips[i];
+    const int nx = (int)b->nx[i];
     int x = 0;
     for (; x + w4 <= nx; x += w4) strips.push_back({x, 4});
     const int r = nx - x;
@@ -114,14 +154,32 @@ static cudaError_t batch_strips(pf_batch_s* b, int k) {
     } else if (r > 0) {
       strips.push_back({x, 1});
     }
-    for (int y = 0; y < ny; y += rows)
-      for (const auto& st : strips)
-        list.push_back(BatchStrip{i, st.first, y, (short)std::min(rows, ny - y), (short)st.second});
+    strip_rows_total += (int64_t)strips.size() * b->ny[i];
   }
-  // widest strips first: warps of one width run together, so an SM's warps share the code of
-  // one width rather than thrash the instruction cache with three
-  std::stable_sort(list.begin(), list.end(),
-                   [](const BatchStrip& a, const BatchStrip& c) { return a.c > c.c; });
+  // candidate heights: from the floor up, skipping those whose lists would be too long to
+  // play through cheaply (a list of a few million tasks is past every tail effect anyway)
+  const int resident = batch_gs2d_strips_resident(k);
+  const int floor_rows = strip_task_rows(PF_MODEL_GS, k);
+  int hy = 0;
+  double best = 0;
+  std::vector<double> slots;
+  for (int h = floor_rows; h <= 192; h += 4) {
+    if (strip_rows_total / h > (int64_t)1 << 22 && h < 192) continue;
+    const double span = strip_makespan(b, plan, h, k, resident, slots);
+    if (hy == 0 || span <= best) {
+      best = span;
+      hy = h;
+    }
+  }
+  std::vector<BatchStrip> list;
+  for (int c : {4, 2, 1})
+    for (int i : plan.order) {
+      const int ny = (int)b->ny[i];
+      for (int y = 0; y < ny; y += hy)
+        for (const auto& st : plan.strips[i])
+          if (st.second == c)
+            list.push_back(BatchStrip{i, st.first, y, (short)std::min(hy, ny - y), (short)c});
+    }
   if (list.size() > (size_t)INT32_MAX) return cudaErrorInvalidValue;
   cudaError_t e = cudaMalloc(&b->d_strips[ks], sizeof(BatchStrip) * list.size());
   if (e != cudaSuccess) return e;

@@ -454,11 +454,36 @@ int strip_out_cols(int model, int k, int c) {
   return 0;
 }
 
-// Batch tasks are as long as the plain kernel's floor (several waves of them over a batch):
-// four times the levels' start-up.
+// The shortest batch task considered: twice the levels' start-up.
 int strip_task_rows(int model, int k) {
   const int r = (model == PF_MODEL_CH || model == PF_MODEL_C) ? 2 : 1;
-  return 4 * (2 * r + 1) * k;
+  return 2 * (2 * r + 1) * k;
+}
+
+int batch_gs2d_strips_resident(int k) {
+  static int resident[3][64] = {};  // k = 1, 2, 4; per device
+  const int ki = k == 4 ? 2 : k == 2 ? 1 : 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (resident[ki][dev] == 0) {
+    int b = 0, sms = 0;
+    cudaError_t e = k == 4   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &b, batch_gs2d_strip_kernel<4>, kStripThreads, 0)
+                    : k == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &b, batch_gs2d_strip_kernel<2>, kStripThreads, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &b, batch_gs2d_strip_kernel<1>, kStripThreads, 0);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    resident[ki][dev] = (b > 0 ? b : 1) * (sms > 0 ? sms : 1) * kStripWarps;
+  }
+  return resident[ki][dev];
 }
 
 cudaError_t launch_batch_gs2d_strips(int k, const BatchInst* d_insts, const BatchStrip* d_tasks,

@@ -151,7 +151,8 @@ struct BatchStrip {
   short hy, c;
 };
 int strip_out_cols(int model, int k, int c);  // output columns of a strip of 32 c columns
-int strip_task_rows(int model, int k);        // rows per batch strip task
+int strip_task_rows(int model, int k);        // fewest rows per batch strip task
+int batch_gs2d_strips_resident(int k);         // warps of the batch strip kernel on the device
 cudaError_t launch_batch_gs2d_strips(int k, const BatchInst* d_insts, const BatchStrip* d_tasks,
                                      int ntasks, const float* in_base, float* out_base,
                                      cudaStream_t s);
