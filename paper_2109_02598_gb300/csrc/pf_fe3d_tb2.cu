@@ -96,16 +96,17 @@ __device__ __forceinline__ void update4(const float4* c, const float4* lap, floa
 // 7-point Laplacians of four sites: centre c, z-neighbours zm/zp, rows above/below and the
 // two x-edge scalars of the centre row. Gray-Scott's stencil factor is carried in D_u and D_v
 // (its lap_scale is 1), so its final multiply is left out, as lap_scaled does: the same bits,
-// eight instructions fewer per float4 and level (GS 256^3: 503 -> 521 GLUPS).
+// eight instructions fewer per float4 and level (GS 256^3: 503 -> 521 GLUPS). The sums run as
+// packed FP32 pairs (lap3d_sum4: lap3d_sum's operations in its order, each lane's bits
+// unchanged) while the update stays scalar, which splits the arithmetic between the heavy FMA
+// pipe (the pairs) and both pipes (the scalars): GS 256^3 558 -> 596 GLUPS. Packing the
+// update too loads the heavy pipe alone (measured slower before this change).
 template <int MODEL>
 __device__ __forceinline__ float4 lap3d_x4(const float4& c, const float4& ym, const float4& yp,
                                            const float4& zm, const float4& zp, float xm,
                                            float xp, float lap_scale) {
-  float4 l;
-  l.x = lap_scaled<MODEL>(lap3d_sum(c.x, xm, c.y, ym.x, yp.x, zm.x, zp.x), lap_scale);
-  l.y = lap_scaled<MODEL>(lap3d_sum(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y), lap_scale);
-  l.z = lap_scaled<MODEL>(lap3d_sum(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z), lap_scale);
-  l.w = lap_scaled<MODEL>(lap3d_sum(c.w, c.z, xp, ym.w, yp.w, zm.w, zp.w), lap_scale);
+  float4 l = lap3d_sum4(c, xm, xp, ym, yp, zm, zp);
+  if constexpr (MODEL != PF_MODEL_GS) l = mul4(lap_scale, l);  // lap_scaled
   return l;
 }
 
