@@ -104,12 +104,19 @@ __device__ __forceinline__ void store_lane(float* row, int gx, int nx, bool xout
 }
 
 // Packed FP32 pairs (one instruction updates two sites, each lane's result the scalar
-// operation's bits; the *4 helpers of pf_model.cuh) where they measured faster: Gray-Scott
-// with 64-column strips (Gray-Scott 4096^2: 808 -> 879 GLUPS) and Allen-Cahn with 128-column
-// strips (Allen-Cahn 4096^2: 1340 -> 1483). Gray-Scott with 128-column strips measured slower
-// with them (791 -> 731), Allen-Cahn with 64-column strips the same.
+// operation's bits; the *4 helpers of pf_model.cuh). A packed pair issues to the heavy FMA pipe
+// only, so packing everything can be slower than scalar code that spreads over both pipes;
+// the choices below are the measured ones. Laplacian sums (kStripPackedLap): packed for 2 and
+// 4 columns a lane except Gray-Scott with 128-column strips (787 -> 775 GLUPS at 4096^2);
+// Model B 8192^2 823 -> 858, Model C 4096^2 383 -> 388, Allen-Cahn with 64-column strips 1296
+// -> 1307. Updates (kStripPacked): Gray-Scott with 64-column strips (Gray-Scott 4096^2: 808 ->
+// 879 GLUPS) and Allen-Cahn with 128-column strips (Allen-Cahn 4096^2: 1340 -> 1483);
+// Gray-Scott with 128-column strips measured slower with them (791 -> 731), Allen-Cahn with
+// 64-column strips the same.
 template <int MODEL, int C>
 constexpr bool kStripPacked = (MODEL == PF_MODEL_GS && C == 2) || (MODEL == PF_MODEL_AC && C == 4);
+template <int MODEL, int C>
+constexpr bool kStripPackedLap = (C == 2 || C == 4) && !(MODEL == PF_MODEL_GS && C == 4);
 
 // Laplacians of a lane's C sites from the rows above (u), at (c) and below (d); the x
 // neighbours beyond the lane come from the adjacent lanes.
@@ -118,7 +125,7 @@ __device__ __forceinline__ void lap_lane(const float (&u)[C], const float (&c)[C
                                          const float (&d)[C], float scale, float (&l)[C]) {
   const float xl = __shfl_up_sync(0xffffffffu, c[C - 1], 1);
   const float xr = __shfl_down_sync(0xffffffffu, c[0], 1);
-  if constexpr (kStripPacked<MODEL, C> && C == 4) {
+  if constexpr (kStripPackedLap<MODEL, C> && C == 4) {
     float4 r = lap2d_sum4(make_float4(c[0], c[1], c[2], c[3]), xl, xr,
                           make_float4(u[0], u[1], u[2], u[3]),
                           make_float4(d[0], d[1], d[2], d[3]));
@@ -127,7 +134,7 @@ __device__ __forceinline__ void lap_lane(const float (&u)[C], const float (&c)[C
     l[1] = r.y;
     l[2] = r.z;
     l[3] = r.w;
-  } else if constexpr (kStripPacked<MODEL, C> && C == 2) {
+  } else if constexpr (kStripPackedLap<MODEL, C> && C == 2) {
     // lap2d_sum of two sites: (xm + xp) + (ym + yp), then -4 c + that
     const float2 sx = make_float2(__fadd_rn(xl, c[1]), __fadd_rn(c[0], xr));
     const float2 sy = __fadd2_rn(make_float2(u[0], u[1]), make_float2(d[0], d[1]));
