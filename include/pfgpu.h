@@ -268,10 +268,13 @@ void pf_batch_destroy(pf_batch_t b);
 int pf_batch_write_field(pf_batch_t b, int inst, int field, const float* src, int on_device);
 int pf_batch_read_field(pf_batch_t b, int inst, int field, float* dst, int on_device);
 
-/* Tile (one of the 2D tiles of pf_set_tuning, or 128 x PF_TILE_STRIPS for the strip kernel)
- * and temporal depth k in {1, 2, 4} for every instance; 0 keeps the current value. With the
- * strip kernel each instance's width is covered by strips of 128 columns and one narrower
- * strip (64 or 32 columns) for the remainder, cut into tasks of 12 k rows. */
+/* Tile (one of the 2D tiles of pf_set_tuning, or 128 or 64 x PF_TILE_STRIPS for the strip
+ * kernel) and temporal depth k in {1, 2, 4} for every instance; 0 keeps the current value.
+ * With the strip kernel each instance's width is split evenly over the fewest strips of 128
+ * (or 64) columns that cover it, their output boundaries multiples of 4, and cut into tasks
+ * of one height for the whole batch (at least 6 k rows), chosen by playing the task list
+ * through the device's in-order dispatch onto its resident warps. Other tile_x values with
+ * PF_TILE_STRIPS return PF_ERR_INVALID_ARG. */
 int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps);
 int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps);
 

@@ -34,10 +34,10 @@ struct pf_batch_s {
   pf::BatchInst* d_insts = nullptr;
   pf::BatchTile* d_tiles[pf::kNumTiles2D] = {};
   int ntiles[pf::kNumTiles2D] = {};
-  pf::BatchStrip* d_strips[3] = {};  // strip kernel work lists for k = 1, 2, 4
-  int nstrips[3] = {};
+  pf::BatchStrip* d_strips[6] = {};  // strip kernel work lists: (c = 4, 2) x (k = 1, 2, 4)
+  int nstrips[6] = {};
   int cur = 0;
-  int tile = 0;  // tile id in the 2D table, or pf::kTileStrips2D (the strip kernel)
+  int tile = 0;  // tile id in the 2D table, or pf::kTileStrips2D (+ 1): the strip kernel
   int k = 1;
   // graph cache: one executable per starting buffer for the current (steps, tile, k)
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -81,121 +81,118 @@ static cudaError_t batch_tiles(pf_batch_s* b, int t) {
 
 static int kslot(int k) { return k == 4 ? 2 : k == 2 ? 1 : 0; }
 
-// Strip kernel work list for depth k: per instance (largest first), strips of 128 lanes'
-// columns over the width and one narrower strip for the remainder (64 or 32 columns where it
-// fits, else 64 plus 32), each cut into tasks of hy rows; widest strips first (warps of one
-// width then run together and share their code in the instruction cache), and within a
-// width the strips of one band of rows are consecutive, so neighbouring warps share halo
-// columns.
+// Strip kernel work list for strips of 32 c columns (c = 4 or 2) and depth k: per instance
+// (largest first), its width split evenly over the fewest strips that cover it, each cut
+// into tasks of hy rows; the strips of one band of rows are consecutive, so neighbouring
+// warps share halo columns. One width for every strip: a narrower strip for an instance's
+// remainder columns takes about as long per row as a full one (its warp waits on its row
+// loads instead of sharing the issue slots), so remainder strips cost a whole strip each
+// (measured: 512 instances of sides a multiple of 120, 682 GLUPS; the same sides plus one
+// column, each with a 32-column remainder strip, 449).
+//
+// Split: s = ceil(nx / W) strips (W = the strip's output columns rounded down to a multiple
+// of 4), boundaries b_j = 4 ceil(j nx / 4 s), b_s = nx. Then b_j - j nx / s lies in [0, 4), so
+// an inner strip's width is a multiple of 4 below nx / s + 4 <= W + 4, i.e. at most W, and
+// the last one is at most nx / s <= W; every width is positive once nx >= 4 s (for s >= 2,
+// nx > W >= 24). The boundaries keep every strip's vector loads aligned.
 //
 // The task height hy is chosen for the launch as a whole. The device starts the one-warp
 // tasks in list order as warps finish, so a list a little longer than a whole number of
 // waves leaves most warps idle while the last tasks run (one 4096^2 instance: 3010 tasks of
 // 48 rows on 2432 resident warps ran 46 % slower than 2415 tasks of 60 rows). Each
 // candidate height's list is played through that dispatch on the resident warps, with a
-// task costing its iterations (rows + the levels' start-up) times its strip's width
-// weight, and the shortest makespan wins (the taller height on a tie).
-struct StripPlan {
-  std::vector<std::vector<std::pair<int, int>>> strips;  // per instance: (x0, c)
-  std::vector<int> order;                                // instances, largest first
-};
+// task costing its iterations (rows + the levels' start-up), and the shortest makespan wins
+// (the taller height on a tie).
+static std::vector<int> strip_bounds(int nx, int w) {
+  const int s = (nx + w - 1) / w;
+  std::vector<int> b(s + 1);
+  for (int j = 0; j < s; ++j) b[j] = 4 * (int)(((int64_t)j * nx + 4 * s - 1) / (4 * s));
+  b[s] = nx;
+  return b;
+}
 
-static double strip_makespan(const pf_batch_s* b, const StripPlan& plan, int hy, int k,
-                             int resident, std::vector<double>& slots) {
-  static const double weight[5] = {0, 0.4, 0.6, 0, 1.0};  // per strip width c = 1, 2, 4
+static double strip_makespan(const pf_batch_s* b, const std::vector<int>& order,
+                             const std::vector<int>& nstrips, int hy, int k, int resident,
+                             std::vector<double>& slots) {
   slots.assign((size_t)resident, 0.0);
   std::make_heap(slots.begin(), slots.end(), std::greater<double>());
   double span = 0;
-  for (int c : {4, 2, 1}) {
-    for (int i : plan.order) {
-      const int ny = (int)b->ny[i];
-      for (int y = 0; y < ny; y += hy) {
-        const double cost = (std::min(hy, ny - y) + 3.0 * k) * weight[c];
-        for (const auto& st : plan.strips[i]) {
-          if (st.second != c) continue;
-          std::pop_heap(slots.begin(), slots.end(), std::greater<double>());
-          slots.back() += cost;
-          span = std::max(span, slots.back());
-          std::push_heap(slots.begin(), slots.end(), std::greater<double>());
-        }
+  for (int i : order) {
+    const int ny = (int)b->ny[i];
+    for (int y = 0; y < ny; y += hy) {
+      const double cost = std::min(hy, ny - y) + 3.0 * k;
+      for (int j = 0; j < nstrips[i]; ++j) {
+        std::pop_heap(slots.begin(), slots.end(), std::greater<double>());
+        slots.back() += cost;
+        span = std::max(span, slots.back());
+        std::push_heap(slots.begin(), slots.end(), std::greater<double>());
       }
     }
   }
   return span;
 }
 
-static cudaError_t batch_strips(pf_batch_s* b, int k) {
-  const int ks = kslot(k);
-  if (b->d_strips[ks] != nullptr) return cudaSuccess;
-  const int w4 = strip_out_cols(PF_MODEL_GS, k, 4), w2 = strip_out_cols(PF_MODEL_GS, k, 2);
-  const int w1 = strip_out_cols(PF_MODEL_GS, k, 1);
-  if (w4 <= 0 || w2 <= 0 || w1 <= 0) return cudaErrorInvalidValue;
-  StripPlan plan;
-  plan.order.resize(b->n);
-  for (int i = 0; i < b->n; ++i) plan.order[i] = i;
-  std::stable_sort(plan.order.begin(), plan.order.end(), [&](int a, int c) {
-    return b->nx[a] * b->ny[a] > b->nx[c] * b->ny[c];
+static int strip_c(int t) { return t == kTileStrips2D ? 4 : 2; }
+static int strip_slot(int t, int k) { return (t - kTileStrips2D) * 3 + kslot(k); }
+
+static cudaError_t batch_strips(pf_batch_s* b, int t, int k) {
+  const int c = strip_c(t), slot = strip_slot(t, k);
+  if (b->d_strips[slot] != nullptr) return cudaSuccess;
+  const int w = strip_out_cols(PF_MODEL_GS, k, c) / 4 * 4;
+  if (w <= 0) return cudaErrorInvalidValue;
+  std::vector<int> order(b->n), nstrips(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int q) {
+    return b->nx[a] * b->ny[a] > b->nx[q] * b->ny[q];
   });
-  plan.strips.resize(b->n);
   int64_t strip_rows_total = 0;  // rows of every strip: the task count at hy = 1
   for (int i = 0; i < b->n; ++i) {
-    auto& strips = plan.strips[i];
-    const int nx = (int)b->nx[i];
-    int x = 0;
-    for (; x + w4 <= nx; x += w4) strips.push_back({x, 4});
-    const int r = nx - x;
-    if (r > w2 + w1) {
-      strips.push_back({x, 4});
-    } else if (r > w2) {
-      strips.push_back({x, 2});
-      strips.push_back({x + w2, 1});
-    } else if (r > w1) {
-      strips.push_back({x, 2});
-    } else if (r > 0) {
-      strips.push_back({x, 1});
-    }
-    strip_rows_total += (int64_t)strips.size() * b->ny[i];
+    nstrips[i] = (int)((b->nx[i] + w - 1) / w);
+    strip_rows_total += (int64_t)nstrips[i] * b->ny[i];
   }
   // candidate heights: from the floor up, skipping those whose lists would be too long to
   // play through cheaply (a list of a few million tasks is past every tail effect anyway)
-  const int resident = batch_gs2d_strips_resident(k);
+  const int resident = batch_gs2d_strips_resident(k, c);
   const int floor_rows = strip_task_rows(PF_MODEL_GS, k);
   int hy = 0;
   double best = 0;
   std::vector<double> slots;
   for (int h = floor_rows; h <= 192; h += 4) {
     if (strip_rows_total / h > (int64_t)1 << 22 && h < 192) continue;
-    const double span = strip_makespan(b, plan, h, k, resident, slots);
+    const double span = strip_makespan(b, order, nstrips, h, k, resident, slots);
     if (hy == 0 || span <= best) {
       best = span;
       hy = h;
     }
   }
   std::vector<BatchStrip> list;
-  for (int c : {4, 2, 1})
-    for (int i : plan.order) {
-      const int ny = (int)b->ny[i];
-      for (int y = 0; y < ny; y += hy)
-        for (const auto& st : plan.strips[i])
-          if (st.second == c)
-            list.push_back(BatchStrip{i, st.first, y, (short)std::min(hy, ny - y), (short)c});
-    }
+  for (int i : order) {
+    const int ny = (int)b->ny[i];
+    const std::vector<int> xb = strip_bounds((int)b->nx[i], w);
+    for (int y = 0; y < ny; y += hy)
+      for (size_t j = 0; j + 1 < xb.size(); ++j) {
+        const int wo = xb[j + 1] - xb[j];
+        if (wo <= 0 || wo > w) return cudaErrorInvalidValue;  // excluded by the split's bound
+        list.push_back(BatchStrip{i, xb[j], y, (short)std::min(hy, ny - y), (short)wo});
+      }
+  }
   if (list.size() > (size_t)INT32_MAX) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMalloc(&b->d_strips[ks], sizeof(BatchStrip) * list.size());
+  cudaError_t e = cudaMalloc(&b->d_strips[slot], sizeof(BatchStrip) * list.size());
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(b->d_strips[ks], list.data(), sizeof(BatchStrip) * list.size(),
+  e = cudaMemcpy(b->d_strips[slot], list.data(), sizeof(BatchStrip) * list.size(),
                  cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  b->nstrips[ks] = (int)list.size();
+  b->nstrips[slot] = (int)list.size();
   return cudaSuccess;
 }
 
 static cudaError_t batch_launch(pf_batch_s* b, int t, int k, int src, cudaStream_t s) {
-  if (t == kTileStrips2D) {
-    cudaError_t e = batch_strips(b, k);
+  if (t == kTileStrips2D || t == kTileStrips2D + 1) {
+    cudaError_t e = batch_strips(b, t, k);
     if (e != cudaSuccess) return e;
-    return launch_batch_gs2d_strips(k, b->d_insts, b->d_strips[kslot(k)], b->nstrips[kslot(k)],
-                                    b->base[src], b->base[1 - src], s);
+    const int slot = strip_slot(t, k);
+    return launch_batch_gs2d_strips(strip_c(t), k, b->d_insts, b->d_strips[slot],
+                                    b->nstrips[slot], b->base[src], b->base[1 - src], s);
   }
   cudaError_t e = batch_tiles(b, t);
   if (e != cudaSuccess) return e;
@@ -294,7 +291,7 @@ void pf_batch_destroy(pf_batch_t b) {
   drop_graphs(b);
   for (int t = 0; t < kNumTiles2D; ++t)
     if (b->d_tiles[t]) cudaFree(b->d_tiles[t]);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 6; ++i)
     if (b->d_strips[i]) cudaFree(b->d_strips[i]);
   if (b->d_insts) cudaFree(b->d_insts);
   if (b->mem) cudaFree(b->mem);
@@ -335,8 +332,9 @@ int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps) {
   if (int rc = check_batch(b)) return rc;
   int t = b->tile;
   if (tile_y == PF_TILE_STRIPS) {
-    if (tile_x != 128) return invalid("the batch's strip kernel takes tile 128 x PF_TILE_STRIPS");
-    t = kTileStrips2D;
+    if (tile_x != 128 && tile_x != 64)
+      return invalid("the batch's strip kernel takes tile 128 or 64 x PF_TILE_STRIPS");
+    t = tile_x == 128 ? kTileStrips2D : kTileStrips2D + 1;
   } else if (tile_x != 0 || tile_y != 0) {
     t = tile2d_id(tile_x, tile_y);
     if (t < 0) return invalid("unsupported 2D tile %dx%d", tile_x, tile_y);
@@ -350,8 +348,8 @@ int pf_batch_set_tuning(pf_batch_t b, int tile_x, int tile_y, int k_steps) {
 
 int pf_batch_get_tuning(pf_batch_t b, int* tile_x, int* tile_y, int* k_steps) {
   if (int rc = check_batch(b)) return rc;
-  int tx = 128, ty = PF_TILE_STRIPS;
-  if (b->tile != kTileStrips2D) tile2d_shape(b->tile, &tx, &ty);
+  int tx = b->tile == kTileStrips2D ? 128 : 64, ty = PF_TILE_STRIPS;
+  if (b->tile < kTileStrips2D) tile2d_shape(b->tile, &tx, &ty);
   if (tile_x) *tile_x = tx;
   if (tile_y) *tile_y = ty;
   if (k_steps) *k_steps = b->k;
@@ -370,8 +368,9 @@ int pf_batch_autotune(pf_batch_t b, int probe_launches, int* tile_x, int* tile_y
   int bt = b->tile, bk = b->k;
   static const int ks[3] = {1, 2, 4};
   cudaError_t e = cudaSuccess;
-  for (int ti = 0; ti <= kNumTiles2D && e == cudaSuccess; ++ti) {
-    const int t = ti < kNumTiles2D ? ti : kTileStrips2D;  // the tiles, then the strip kernel
+  for (int ti = 0; ti < kNumTiles2D + 2 && e == cudaSuccess; ++ti) {
+    // the tiles, then the strip kernel with 128- and 64-column strips
+    const int t = ti < kNumTiles2D ? ti : kTileStrips2D + (ti - kNumTiles2D);
     for (int ki = 0; ki < 3 && e == cudaSuccess; ++ki) {
       const int k = ks[ki];
       e = batch_launch(b, t, k, b->cur, b->stream);  // warm-up (state unchanged)
@@ -404,9 +403,10 @@ int pf_batch_run(pf_batch_t b, int64_t n_steps) {
   if (n_steps == 0) return PF_OK;
   if (b->g_steps != n_steps || b->g_tile != b->tile || b->g_k != b->k) drop_graphs(b);
   if (b->exec[b->cur] == nullptr) {
-    cudaError_t e = b->tile == kTileStrips2D ? cudaSuccess : batch_tiles(b, b->tile);
-    for (int k = b->k; k >= 1 && e == cudaSuccess && b->tile == kTileStrips2D; k >>= 1)
-      e = batch_strips(b, k);  // allocate outside the capture (every depth the plan uses)
+    const bool strips = b->tile >= kTileStrips2D;
+    cudaError_t e = strips ? cudaSuccess : batch_tiles(b, b->tile);
+    for (int k = b->k; k >= 1 && e == cudaSuccess && strips; k >>= 1)
+      e = batch_strips(b, b->tile, k);  // allocate outside the capture (every depth used)
     if (e != cudaSuccess) return cuda_fail(e, "pf_batch_run work list");
     PF_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
     int src = b->cur;

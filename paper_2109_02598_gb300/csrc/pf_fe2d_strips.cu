@@ -37,12 +37,17 @@ struct StripCfg {
   static constexpr int WO = 32 * C - 2 * HXP;       // output columns per strip
   static constexpr int NM = MODEL == PF_MODEL_C ? 2 : 1;  // mu (and Model C's lap psi)
   // Floats a lane holds in windows: the warps per SM the register allocation must allow
-  // follow from it (65536 / (32 x MINW) registers per thread), the most that needs no spills.
-  // Measured on Gray-Scott 4096^2 at K = 4, C = 4: 16 warps of 128 registers run 681 GLUPS,
-  // 12 warps of 154 registers 550.
+  // follow from it (65536 / (32 x MINW) registers per thread). The kernels wait mostly on
+  // their row loads, so more resident warps pay until spills cost more than they hide: with
+  // fewer than 96 floats of windows, 32 warps (64 registers, the most one-warp CTAs can
+  // reach: 32 CTAs per SM) with at most a few spilled words (measured: Model B 8192^2 at
+  // K = 2, C = 4 843 -> 1107 GLUPS, Gray-Scott 4096^2 at K = 4, C = 2 870 -> 907, Model C
+  // 4096^2 at K = 2, C = 2 381 -> 487, against 20 warps); with 96 or more, 16 or 12 warps
+  // (Gray-Scott 4096^2 at K = 4, C = 4: 16 warps of 128 registers 681 GLUPS, 12 of 154
+  // registers 550, 32 of 64 registers 378 with kilobytes of spills).
   static constexpr int WIN = K * 3 * C * (NF + (R == 2 ? NM : 0));
   static constexpr int MINW = (WIN > 96 || (MODEL == PF_MODEL_C && WIN == 96)) ? 12
-                              : WIN >= 96 ? 16 : WIN >= 40 ? 20 : 32;
+                              : WIN >= 96 ? 16 : 32;
   static_assert(WO > 0, "strip too narrow for this depth");
 };
 
@@ -292,9 +297,10 @@ struct StripRun {
     }
   }
 
-  // Output rows [y0, y0 + hy) of the strip whose output columns start at x0.
+  // Output rows [y0, y0 + hy) and columns [x0, x0 + wo) of the strip whose output columns
+  // start at x0 (wo <= WO, a multiple of C unless the strip ends at the row's end).
   __device__ __forceinline__ void run(const FieldPtrs& in_, const FieldOut& out_, int nx_,
-                                      int ny_, int64_t pitch_, int x0, int y0_, int hy_,
+                                      int ny_, int64_t pitch_, int x0, int wo, int y0_, int hy_,
                                       const ModelParams& m) {
     in = in_;
     out = out_;
@@ -305,7 +311,7 @@ struct StripRun {
     hy = hy_;
     const int lane = threadIdx.x & 31;
     gx = x0 - S::HXP + C * lane;
-    st_lane = lane >= S::HXP / C && lane < (S::HXP + S::WO) / C;
+    st_lane = lane >= S::HXP / C && lane < (S::HXP + wo + C - 1) / C;
     // strips that reach past either end of the row (every strip of a narrow grid or batch
     // instance) take the periodic paths with the whole warp
     xin = __all_sync(0xffffffffu, gx >= 0 && gx + C <= nx);
@@ -343,13 +349,13 @@ __global__ void __launch_bounds__(kStripThreads, (StripCfg<MODEL, K, C>::MINW / 
   const int tx = task - ty * tasks_x;
   const int y0 = ty * hy;
   StripRun<MODEL, K, C> r;
-  r.run(in, out, g.nx, g.ny, g.pitch, tx * S::WO, y0, min(hy, g.ny - y0), m);
+  r.run(in, out, g.nx, g.ny, g.pitch, tx * S::WO, S::WO, y0, min(hy, g.ny - y0), m);
 }
 
-// Batched Gray-Scott: warp w runs strip task w of the list; the remainder of an instance's
-// width goes to a narrower strip (c = 2 or 1), so the kernel holds the three widths.
-template <int K>
-__global__ void __launch_bounds__(kStripThreads, (StripCfg<PF_MODEL_GS, K, 4>::MINW / kStripWarps))
+// Batched Gray-Scott: warp w runs strip task w of the list, a strip of 32 C columns whose
+// output width the task gives (every instance's width is split evenly over its strips).
+template <int K, int C>
+__global__ void __launch_bounds__(kStripThreads, (StripCfg<PF_MODEL_GS, K, C>::MINW / kStripWarps))
     batch_gs2d_strip_kernel(const BatchInst* __restrict__ insts,
                             const BatchStrip* __restrict__ tasks, int ntasks,
                             const float* in_base, float* out_base) {
@@ -364,16 +370,8 @@ __global__ void __launch_bounds__(kStripThreads, (StripCfg<PF_MODEL_GS, K, 4>::M
   in.f[1] = in_base + I.off + plane;
   out.f[0] = out_base + I.off;
   out.f[1] = out_base + I.off + plane;
-  if (t.c == 4) {
-    StripRun<PF_MODEL_GS, K, 4> r;
-    r.run(in, out, I.nx, I.ny, I.pitch, t.x0, t.y0, t.hy, I.m);
-  } else if (t.c == 2) {
-    StripRun<PF_MODEL_GS, K, 2> r;
-    r.run(in, out, I.nx, I.ny, I.pitch, t.x0, t.y0, t.hy, I.m);
-  } else {
-    StripRun<PF_MODEL_GS, K, 1> r;
-    r.run(in, out, I.nx, I.ny, I.pitch, t.x0, t.y0, t.hy, I.m);
-  }
+  StripRun<PF_MODEL_GS, K, C> r;
+  r.run(in, out, I.nx, I.ny, I.pitch, t.x0, t.wo, t.y0, t.hy, I.m);
 }
 
 // Rows per task. A task's first and last rows carry the levels' start-up and drain, which
@@ -435,13 +433,28 @@ cudaError_t launch_strip_c(int lanes_cols, int k, const Geom& g, FieldPtrs in, F
   return cudaErrorInvalidValue;
 }
 
-template <int K>
+template <int K, int C>
 cudaError_t launch_batch_k(const BatchInst* d_insts, const BatchStrip* d_tasks, int ntasks,
                            const float* in_base, float* out_base, cudaStream_t s) {
   const int blocks = (ntasks + kStripWarps - 1) / kStripWarps;
-  batch_gs2d_strip_kernel<K><<<blocks, kStripThreads, 0, s>>>(d_insts, d_tasks, ntasks, in_base,
-                                                              out_base);
+  batch_gs2d_strip_kernel<K, C><<<blocks, kStripThreads, 0, s>>>(d_insts, d_tasks, ntasks,
+                                                                 in_base, out_base);
   return cudaGetLastError();
+}
+
+template <int K, int C>
+int batch_resident_kc() {
+  int b = 0, sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_gs2d_strip_kernel<K, C>,
+                                                      kStripThreads, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (b > 0 ? b : 1) * (sms > 0 ? sms : 1) * kStripWarps;
 }
 
 template <int MODEL, int K>
@@ -467,39 +480,40 @@ int strip_task_rows(int model, int k) {
   return 2 * (2 * r + 1) * k;
 }
 
-int batch_gs2d_strips_resident(int k) {
-  static int resident[3][64] = {};  // k = 1, 2, 4; per device
-  const int ki = k == 4 ? 2 : k == 2 ? 1 : 0;
+int batch_gs2d_strips_resident(int k, int c) {
+  static int resident[2][3][64] = {};  // c = 4, 2; k = 1, 2, 4; per device
+  const int ci = c == 2 ? 1 : 0, ki = k == 4 ? 2 : k == 2 ? 1 : 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {
     cudaGetLastError();
     return 1;
   }
-  if (resident[ki][dev] == 0) {
-    int b = 0, sms = 0;
-    cudaError_t e = k == 4   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &b, batch_gs2d_strip_kernel<4>, kStripThreads, 0)
-                    : k == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &b, batch_gs2d_strip_kernel<2>, kStripThreads, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &b, batch_gs2d_strip_kernel<1>, kStripThreads, 0);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return 1;
-    }
-    resident[ki][dev] = (b > 0 ? b : 1) * (sms > 0 ? sms : 1) * kStripWarps;
+  int& r = resident[ci][ki][dev];
+  if (r == 0) {
+    if (c == 2)
+      r = k == 4 ? batch_resident_kc<4, 2>() : k == 2 ? batch_resident_kc<2, 2>()
+                                                      : batch_resident_kc<1, 2>();
+    else
+      r = k == 4 ? batch_resident_kc<4, 4>() : k == 2 ? batch_resident_kc<2, 4>()
+                                                      : batch_resident_kc<1, 4>();
+    if (r == 0) return 1;  // not cached: asked again next time
   }
-  return resident[ki][dev];
+  return r;
 }
 
-cudaError_t launch_batch_gs2d_strips(int k, const BatchInst* d_insts, const BatchStrip* d_tasks,
-                                     int ntasks, const float* in_base, float* out_base,
-                                     cudaStream_t s) {
+cudaError_t launch_batch_gs2d_strips(int c, int k, const BatchInst* d_insts,
+                                     const BatchStrip* d_tasks, int ntasks, const float* in_base,
+                                     float* out_base, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
-  if (k == 1) return launch_batch_k<1>(d_insts, d_tasks, ntasks, in_base, out_base, s);
-  if (k == 2) return launch_batch_k<2>(d_insts, d_tasks, ntasks, in_base, out_base, s);
-  if (k == 4) return launch_batch_k<4>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+  if (c == 4) {
+    if (k == 1) return launch_batch_k<1, 4>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+    if (k == 2) return launch_batch_k<2, 4>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+    if (k == 4) return launch_batch_k<4, 4>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+  } else if (c == 2) {
+    if (k == 1) return launch_batch_k<1, 2>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+    if (k == 2) return launch_batch_k<2, 2>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+    if (k == 4) return launch_batch_k<4, 2>(d_insts, d_tasks, ntasks, in_base, out_base, s);
+  }
   return cudaErrorInvalidValue;
 }
 

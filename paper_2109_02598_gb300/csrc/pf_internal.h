@@ -144,18 +144,19 @@ struct BatchInst {
 struct BatchTile {
   int inst, x0, y0;
 };
-// A strip task of the batch (strip kernel): output columns from x0 of a strip of 32 c lanes'
-// columns (c = 4, 2 or 1), rows [y0, y0 + hy) of instance inst.
+// A strip task of the batch (strip kernel of 32 c lanes' columns, c = 4 or 2 for the whole
+// launch): output columns [x0, x0 + wo) and rows [y0, y0 + hy) of instance inst; x0 is a
+// multiple of 4 and wo too unless the strip ends at the instance's last column.
 struct BatchStrip {
   int inst, x0, y0;
-  short hy, c;
+  short hy, wo;
 };
 int strip_out_cols(int model, int k, int c);  // output columns of a strip of 32 c columns
 int strip_task_rows(int model, int k);        // fewest rows per batch strip task
-int batch_gs2d_strips_resident(int k);         // warps of the batch strip kernel on the device
-cudaError_t launch_batch_gs2d_strips(int k, const BatchInst* d_insts, const BatchStrip* d_tasks,
-                                     int ntasks, const float* in_base, float* out_base,
-                                     cudaStream_t s);
+int batch_gs2d_strips_resident(int k, int c);  // warps of the batch strip kernel on the device
+cudaError_t launch_batch_gs2d_strips(int c, int k, const BatchInst* d_insts,
+                                     const BatchStrip* d_tasks, int ntasks, const float* in_base,
+                                     float* out_base, cudaStream_t s);
 cudaError_t prepare_batch_gs2d();  // set kernel attributes (call before any capture)
 cudaError_t launch_batch_gs2d(int tile_id, int k, const BatchInst* d_insts,
                               const BatchTile* d_tiles, int ntiles, const float* in_base,

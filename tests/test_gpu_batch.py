@@ -85,7 +85,8 @@ def test_batch_tunings_replays_and_autotune_agree_bitwise(pf):
     S = pf.PF_TILE_STRIPS
     for tuning, chunks in [((128, 16, 2), [12]), ((32, 32, 4), [5, 7]), ((128, 32, 4), [6, 6]),
                            ((64, 16, 2), [3, 3, 3, 3]), ((128, S, 4), [5, 7]),
-                           ((128, S, 2), [12]), ((128, S, 1), [4, 8]), ("auto", [12])]:
+                           ((128, S, 2), [12]), ((128, S, 1), [4, 8]), ((64, S, 4), [12]),
+                           ((64, S, 2), [5, 7]), ((64, S, 1), [12]), ("auto", [12])]:
         got = run(tuning, chunks)
         for (a0, a1), (b0, b1) in zip(base, got):
             assert np.array_equal(a0, b0) and np.array_equal(a1, b1), tuning
@@ -198,8 +199,9 @@ def test_full_batch_every_instance_against_the_oracle(pf):
 
 
 def test_full_batch_strip_kernel_is_bitwise_the_tiled_batch(pf):
-    # the 512-instance configuration: the strip kernel (mixed strip widths over every
-    # instance's width) gives every instance the bits of the tiled batch, at every depth
+    # the 512-instance configuration: the strip kernel (every instance's width split evenly
+    # over strips of 128 or 64 columns) gives every instance the bits of the tiled batch, at
+    # every depth
     specs = synthetic.batch_instances(512, seed=4)
     x0 = [synthetic.batch_instance_init(q["n"], i) for i, q in enumerate(specs)]
 
@@ -214,9 +216,9 @@ def test_full_batch_strip_kernel_is_bitwise_the_tiled_batch(pf):
         return out
 
     ref = run((32, 32, 4), 12)
-    for k in (4, 2, 1):
-        got = run((128, pf.PF_TILE_STRIPS, k), 12)
+    for width, k in ((128, 4), (128, 2), (128, 1), (64, 4), (64, 2), (64, 1)):
+        got = run((width, pf.PF_TILE_STRIPS, k), 12)
         for i, ((a0, a1), (b0, b1)) in enumerate(zip(ref, got)):
-            assert np.array_equal(a0, b0) and np.array_equal(a1, b1), (i, specs[i]["n"], k)
+            assert np.array_equal(a0, b0) and np.array_equal(a1, b1), (i, specs[i]["n"], width, k)
     with pytest.raises(pf.PfError, match="strip kernel"):
-        pf.Batch(make_specs([(16, 16)]), DT).set_tuning(64, pf.PF_TILE_STRIPS, 1)
+        pf.Batch(make_specs([(16, 16)]), DT).set_tuning(96, pf.PF_TILE_STRIPS, 1)
