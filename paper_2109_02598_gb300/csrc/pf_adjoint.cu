@@ -24,6 +24,7 @@
 // Parameter-gradient partials are summed per CTA in FP64 (each CTA owns one slot, so the
 // order is fixed and the result deterministic) and added up in a fixed order at the end.
 #include <cmath>
+#include <vector>
 
 #include "pf_fe2d_tile.cuh"
 #include "pf_grid.h"
@@ -316,8 +317,8 @@ dim3 adj_grid(const pf_grid_s* g) {
 float* ckpt_field(pf_grid_s* g, int64_t i, int f) {
   return g->adj.ckpt + (i * g->nf + f) * g->field_elems;
 }
-float* seg_field(pf_grid_s* g, int64_t j, int f) {
-  return g->adj.seg + (j * g->nf + f) * g->field_elems;
+float* seg_field(pf_grid_s* g, int b, int64_t j, int f) {
+  return g->adj.seg + (((int64_t)b * (g->adj.interval - 1) + j) * g->nf + f) * g->field_elems;
 }
 float* lam_field(pf_grid_s* g, int b, int f) {
   return g->adj.lam + (b * g->nf + f) * g->field_elems;
@@ -347,26 +348,49 @@ void adjoint_release(pf_grid_s* g) {
   a = AdjointState();
 }
 
-// Enqueue the whole reverse pass on stream st (recorded into a graph by the caller):
+// Enqueue the whole reverse pass on stream st, which the caller is recording into a graph:
 // zero the gradient slots, then per segment from last to first recompute its states and
 // run its reverse steps, then sum the slots. *lb_out receives the buffer holding lambda^0.
+//
+// Two branches: the reverse steps on st, the recomputation on st2 (forked into the same
+// capture). With two segment buffers, segment s - 1 is recomputed into one buffer while
+// segment s's reverse steps read the other, so the two chains of small launches overlap:
+// recomputing segment s waits for its checkpoint only and for the reverse steps of segment
+// s + 2 (the last reader of its buffer); the reverse steps of segment s wait for its
+// recomputation. Each chain keeps its order, so every kernel sees the same inputs as in a
+// serial pass and the result is the same bits.
 static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStream_t st,
-                                   int* lb_out) {
+                                   cudaStream_t st2, int* lb_out) {
   AdjointState& a = g->adj;
   const Geom q = grid_geom(g);
   const dim3 grid = adj_grid(g);
   const int gs_ty = gs_adj_ty(q, g->device);
   const int64_t nctas = (int64_t)grid.x * grid.y;
-  cudaError_t e = cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, st);
-  int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
   const int64_t C = a.interval;
+  const int nb = a.seg_bufs > 0 ? a.seg_bufs : 1;
+  // per segment: its recomputation done (on st2), its reverse steps done (on st)
+  std::vector<cudaEvent_t> rec((size_t)a.n_ckpt, nullptr), rev((size_t)a.n_ckpt, nullptr);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  for (int64_t s = 0; s < a.n_ckpt && e == cudaSuccess; ++s) {
+    e = cudaEventCreateWithFlags(&rec[(size_t)s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&rev[(size_t)s], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, fork, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.gpart, 0, sizeof(double) * 4 * nctas, st);
+  int lb = 0;  // lambda ping-pong buffer holding the current adjoint state
   for (int64_t s = a.n_ckpt - 1; s >= 0 && e == cudaSuccess; --s) {
     const int64_t s0 = s * C;
     const int64_t len = std::min(C, a.n_steps - s0);
+    const int b = (int)(s % nb);
     // states x^{s0} .. x^{s0+len-1}: slot 0 is the checkpoint, slots 1.. are recomputed
     auto state = [&](int64_t j, int f) -> float* {
-      return j == 0 ? ckpt_field(g, s, f) : seg_field(g, j - 1, f);
+      return j == 0 ? ckpt_field(g, s, f) : seg_field(g, b, j - 1, f);
     };
+    // recompute on st2, once the buffer's previous reader (segment s + nb) is done
+    if (s + nb < a.n_ckpt) e = cudaStreamWaitEvent(st2, rev[(size_t)(s + nb)], 0);
     for (int64_t j = 1; j < len && e == cudaSuccess; ++j) {
       FieldPtrs in{};
       FieldOut out{};
@@ -374,8 +398,10 @@ static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStrea
         in.f[f] = state(j - 1, f);
         out.f[f] = state(j, f);
       }
-      e = launch_fe2d(g->model, 0, 1, q, in, out, m, st);
+      e = launch_fe2d(g->model, 0, 1, q, in, out, m, st2);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(rec[(size_t)s], st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, rec[(size_t)s], 0);
     for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j) {
       FieldPtrs xs{}, li{};
       FieldOut lo{};
@@ -396,11 +422,22 @@ static cudaError_t enqueue_reverse(pf_grid_s* g, const ModelParams& m, cudaStrea
       e = cudaGetLastError();
       lb = 1 - lb;
     }
+    if (e == cudaSuccess) e = cudaEventRecord(rev[(size_t)s], st);
   }
+  // join the second branch before the capture ends (also on an error, so that it can end)
+  cudaError_t ej = cudaEventRecord(join, st2);
+  if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, join, 0);
+  if (e == cudaSuccess) e = ej;
   if (e == cudaSuccess) {
     adj_final_kernel<<<1, 256, 0, st>>>(a.gpart, nctas, a.gout);
     e = cudaGetLastError();
   }
+  for (cudaEvent_t ev : rec)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : rev)
+    if (ev) cudaEventDestroy(ev);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
   *lb_out = lb;
   return e;
 }
@@ -428,8 +465,19 @@ int pf_adj_forward(pf_grid_t g, int64_t n_steps, int64_t ckpt_interval) {
     if (a.seg) cudaFree(a.seg);
     a.ckpt = nullptr;
     a.seg = nullptr;
+    a.seg_bufs = 0;
     PF_CUDA_TRY(cudaMalloc(&a.ckpt, state * n_ckpt));
-    if (C > 1) PF_CUDA_TRY(cudaMalloc(&a.seg, state * (C - 1)));
+    if (C > 1) {
+      // two segment buffers where there are two segments and the memory allows, else one
+      // (the reverse pass then recomputes and reverses one segment after the other)
+      if (n_ckpt > 1 && cudaMalloc(&a.seg, 2 * state * (C - 1)) == cudaSuccess) {
+        a.seg_bufs = 2;
+      } else {
+        cudaGetLastError();  // a failed first try leaves no sticky error
+        PF_CUDA_TRY(cudaMalloc(&a.seg, state * (C - 1)));
+        a.seg_bufs = 1;
+      }
+    }
     a.n_ckpt = n_ckpt;
     a.interval = C;
   }
@@ -488,9 +536,11 @@ int pf_adj_backward(pf_grid_t g, const float* dLdu_N, const float* dLdv_N, int o
     g->adj_exec = nullptr;
     if (g->capture == nullptr)
       PF_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
+    if (g->capture2 == nullptr)
+      PF_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture2, cudaStreamNonBlocking));
     PF_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeRelaxed));
     int lb = 0;
-    cudaError_t e = enqueue_reverse(g, m, g->capture, &lb);
+    cudaError_t e = enqueue_reverse(g, m, g->capture, g->capture2, &lb);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(g->capture, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {

@@ -408,6 +408,7 @@ void pf_destroy(pf_grid_t g) {
   pf::fe2d_bands_release(g);
   drop_graphs(g);
   if (g->capture) cudaStreamDestroy(g->capture);
+  if (g->capture2) cudaStreamDestroy(g->capture2);
   if (g->base) cudaFree(g->base);
   if (g->red_partials) cudaFree(g->red_partials);
   if (g->red_host) cudaFreeHost(g->red_host);

@@ -58,7 +58,10 @@ struct AdjointState {
   int64_t interval = 0;      // checkpoint interval C
   int64_t n_ckpt = 0;        // checkpoints stored (states 0, C, 2C, ...)
   float* ckpt = nullptr;     // n_ckpt * nf * field_elems floats
-  float* seg = nullptr;      // (C + 1) * nf * field_elems floats: one recomputed segment
+  float* seg = nullptr;      // seg_bufs * (C - 1) * nf * field_elems floats: recomputed
+                             // segments (two buffers: one is recomputed while the reverse
+                             // steps read the other)
+  int seg_bufs = 0;          // 2, or 1 where the second buffer could not be allocated
   float* lam = nullptr;      // 2 * nf * field_elems floats: adjoint ping-pong
   double* gpart = nullptr;   // per-CTA parameter-gradient partials (4 per CTA)
   double* gout = nullptr;    // 4 final sums (device)
@@ -113,6 +116,7 @@ struct pf_grid_s {
   // CUDA-graph cache of pf_step: a few recorded launch sequences, keyed by
   // (steps, tile, k, starting buffer), least recently used replaced first
   cudaStream_t capture = nullptr;  // private stream used only to record graphs
+  cudaStream_t capture2 = nullptr;  // second branch of the adjoint's reverse-pass graph
   struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t steps = -1;
