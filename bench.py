@@ -443,6 +443,13 @@ def summary_line(line) -> str:
         for k in ("ch2d_2048", "ch2d_8192", "ac2d_128"):
             if k in c:
                 parts.append(f"{k} {c[k]['glups']:.1f} GLUPS")
+        wr = c.get("widened_rows", {})
+        if "error" in wr:
+            parts.append(f"widened rows: {wr['error']}")
+        for r in wr.get("stencils_gs", []):
+            parts.append(f"gs {r['shape']} {r['stencil']} {r['glups']:.1f}")
+        for r in wr.get("species3", []):
+            parts.append(f"3 species {r['shape']} {r['glups']:.1f}")
     cb = line.get("cpu_baseline")
     if cb:
         parts.append(f"oracle 1 core {cb['single_core']['value']:.4f}, {cb['cores']} cores "
@@ -605,6 +612,103 @@ def companions(stream, hbm):
             "note": "paper times are whole-program runs of its semi-implicit spectral solver "
                     "on 2016-2017 desktop CPUs (context only)"}
         out["paper_table_spectral"] = paper_table_spectral(stream)
+    try:  # reported in the line, never fatal for the headline
+        out["widened_rows"] = widened_rows(stream, hbm)
+    except Exception as exc:
+        out["widened_rows"] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
+
+
+def _grid_rate(pf, stream, shape, model, coeffs, dt, x0, steps, stencil="std"):
+    """GLUPS and tuning of ``steps`` forward-Euler steps of one grid, autotuned, timed on the
+    device after one untimed call of the same length (which records its graph)."""
+    g = pf.Grid(shape, len(x0), stream=stream).set_model(model, coeffs, dt)
+    if stencil != "std":
+        g.set_stencil(stencil)
+    g.write_fields(x0)
+    t = g.autotune(3)
+    g.step(steps)
+    ms = _time(stream, lambda: g.step(steps))
+    g.close()
+    return int(np.prod(shape)) * steps / (ms * 1e-3) / 1e9, list(t)
+
+
+def _host_us(fn, reps):
+    """Host wall time (us) per call of a call that ends with a host synchronisation."""
+    fn()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    return (time.perf_counter() - t0) * 1e6 / reps
+
+
+def widened_rows(stream, hbm):
+    """The rows beyond the headline step, each measured on the device: the isotropic and
+    fourth-order Laplacians (Sec. 2.2.2) beside the 5-/7-point one on the same grids, three
+    coupled reaction-diffusion species (Sec. 2.3's coupled equations of motion), and the
+    analysis calls (mass and free-energy reductions, the structure factor of Sec. 3 and the
+    Porod fit), the last timed per call with its host synchronisation. ``hbm_frac_k1`` is the
+    k = 1 byte count (every field read and written once per update) over the measured copy
+    bandwidth."""
+    import torch
+    import paper_2109_02598_gb300 as pf
+    out = {}
+    gs = (0.2, 0.1, 0.04, 0.06)
+    with torch.cuda.stream(stream):
+        # ---- Laplacian stencils on Gray-Scott 4096^2 (200 steps) and 256^3 (20 steps)
+        rows = []
+        for shape, steps, stencils in (((4096, 4096), 200, ("std", "iso", "4th")),
+                                       ((256, 256, 256), 20, ("std", "iso", "iso27"))):
+            x0 = synthetic.gray_scott_init(shape, seed=11, n_seeds=1024 if len(shape) == 2 else 20,
+                                           side=8)
+            for st in stencils:
+                glups, t = _grid_rate(pf, stream, shape, "gs", gs, 0.5, x0, steps, st)
+                rows.append({"shape": "x".join(str(v) for v in shape[::-1]), "stencil": st,
+                             "points": {"std": 5 if len(shape) == 2 else 7, "iso": 9 if len(shape) == 2
+                                        else 19, "4th": 9, "iso27": 27}[st],
+                             "steps": steps, "glups": glups, "tuning": t,
+                             "hbm_frac_k1": glups * BYTES_PER_LUP["gs"] / hbm})
+        out["stencils_gs"] = rows
+        # ---- three coupled species: a constant source, linear, quadratic, cubic and mixed
+        # monomials; 24 B per update at k = 1
+        D = (0.2, 0.05, 0.12)
+        E = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 2, 0], [2, 0, 1], [0, 0, 3]]
+        K = [[0.03, -0.03, 0.0, 0.1, -1.0, 0.0, 0.0], [0.0, 0.0, -0.09, 0.0, 1.0, -0.4, 0.0],
+             [0.0, 0.05, 0.0, -0.2, 0.0, 0.4, -0.3]]
+        rows = []
+        for shape, steps in (((4096, 4096), 100), ((256, 256, 256), 20)):
+            n = int(np.prod(shape))
+            x0 = tuple(synthetic.uniform(12, 60 + i, n, 0.05, 0.9).reshape(shape).astype(np.float32)
+                       for i in range(3))
+            glups, t = _grid_rate(pf, stream, shape, "rd", pf.rd_coeffs(D, E, K), 0.2, x0, steps)
+            rows.append({"shape": "x".join(str(v) for v in shape[::-1]), "species": 3,
+                         "monomials": len(E), "steps": steps, "glups": glups, "tuning": t,
+                         "hbm_frac_k1": glups * 24.0 / hbm})
+        out["species3"] = rows
+        # ---- analysis calls on resident grids: mass (one field, 4 B per site) and energy
+        rows = []
+        for shape, model, coeffs, dt, nf in (((256, 256, 256), "ac", (1.0, 1.0), 0.05, 1),
+                                             ((2048, 2048), "ac", (1.0, 1.0), 0.05, 1),
+                                             ((128, 128, 128), "c", (1.0,) * 5, 0.005, 2)):
+            x0 = synthetic.paper_timing_init(model, shape)[:nf]
+            g = pf.Grid(shape, nf, stream=stream).set_model(model, coeffs, dt)
+            g.write_fields(x0)
+            sites = int(np.prod(shape))
+            m_us = _host_us(lambda: g.mass(0), 20)
+            e_us = _host_us(g.energy, 10)
+            rows.append({"shape": "x".join(str(v) for v in shape[::-1]), "model": model,
+                         "mass_us": m_us, "mass_gbs": sites * 4 / (m_us * 1e-6) / 1e9,
+                         "energy_us": e_us, "energy_fields": nf})
+            if len(shape) == 2 or model == "c":
+                s_us = _host_us(lambda: g.structure_factor(0, 32), 5)
+                c, mean, cnt = g.structure_factor(0, 32)
+                f_us = _host_us(lambda: pf.porod_fit(c, mean, cnt, float(c[len(c) // 2]),
+                                                     float(c[-2])), 50)
+                rows[-1].update({"structure_factor_us": s_us, "porod_fit_us": f_us})
+            g.close()
+        out["analysis"] = rows
+        out["note"] = ("stencils and species on the forward-Euler step, timed with CUDA events; "
+                       "analysis calls by host wall time per call including the synchronisation")
     return out
 
 
