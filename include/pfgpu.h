@@ -203,12 +203,13 @@ int pf_set_stencil(pf_grid_t g, int stencil);
  * It needs all P CTAs resident at once: if the device cannot host them (other work, a
  * restricted context), pf_step fails with PF_ERR_CUDA. Its exchange buffers (4 R nx 8-byte
  * words per CTA) are allocated at its first launch.
- * 2D tile 128 x PF_TILE_STRIPS or 64 x PF_TILE_STRIPS selects the strip kernel (the
- * standard stencil, any grid size; k in {1, 2, 4} for Allen-Cahn and Gray-Scott, {1, 2} for
- * Models B and C): one warp per strip of 128 (or 64) columns walks down its rows with the k
- * steps pipelined in registers, the row neighbours across lanes taken by warp shuffle; the
- * outer k R columns (rounded up to 4, or 2; R = 1 for Allen-Cahn and Gray-Scott, 2 for
- * Models B and C) on each side are recomputed halo, and no shared memory is used.
+ * 2D tile 128 x PF_TILE_STRIPS or 64 x PF_TILE_STRIPS selects the strip kernel (any grid
+ * size; k in {1, 2, 4} for Allen-Cahn and Gray-Scott with the 5-point or the isotropic
+ * 9-point stencil, {1, 2} for Models B and C with the 5-point stencil): one warp per strip of
+ * 128 (or 64) columns walks down its rows with the k steps pipelined in registers, the row
+ * neighbours across lanes taken by warp shuffle; the outer k R columns (rounded up to 4, or
+ * 2; R = 1 for Allen-Cahn and Gray-Scott, 2 for Models B and C) on each side are recomputed
+ * halo, and no shared memory is used.
  * Results are bitwise identical to the tiled kernels. */
 #define PF_TILE_BANDS (-1) /* tile_y of the band kernel (with tile_x = nx) */
 #define PF_TILE_STRIPS (-2) /* tile_y of the strip kernel (with tile_x = 128 or 64) */

@@ -204,7 +204,7 @@ bool tile_supported(pf_grid_s* g, int tile, int k) {
   if (g->dim == 2 && tile == kTileBands2D)
     return g->stencil == PF_ST_STD && k == 1 && fe2d_bands_supported(g->model, grid_geom(g));
   if (g->dim == 2 && tile >= kTileStrips2D && tile < kTileStrips2D + kNumStrips2D)
-    return g->stencil == PF_ST_STD && fe2d_strips_supported(g->model, k);
+    return fe2d_strips_supported(g->model, k, g->stencil);
   if (g->dim == 2) return fe2d_supported(g->model, k) && fe2d_stencil_supported(g->stencil, tile, k);
   if (g->stencil != PF_ST_STD) return (tile == 0 || tile == 1) && k == 1;
   if (tile == kTileBox3D) return fe3d_box_supported(g->model, k, grid_geom(g));
@@ -257,8 +257,8 @@ cudaError_t launch_step(pf_grid_s* g, int tile, int k, int src, int dst, cudaStr
     return launch_fe2d_cluster(g->model, k, q, in, out, g->params, k, st);
   if (g->dim == 2 && tile == kTileBands2D) return launch_fe2d_bands(g, src, dst, k, st);
   if (g->dim == 2 && tile >= kTileStrips2D && tile < kTileStrips2D + kNumStrips2D)
-    return launch_fe2d_strips(g->model, tile == kTileStrips2D ? 128 : 64, k, q, in, out,
-                              g->params, st);
+    return launch_fe2d_strips(g->model, g->stencil, tile == kTileStrips2D ? 128 : 64, k, q, in,
+                              out, g->params, st);
   if (g->dim == 2) return launch_fe2d_stencil(g->stencil, g->model, tile, k, q, in, out, g->params, st);
   if (g->stencil != PF_ST_STD) return launch_fe3d(g->model, tile, q, in, out, g->params, st, g->stencil);
   if (tile == kTileBox3D) return launch_fe3d_box(g->model, k, q, in, out, g->params, st);
@@ -701,10 +701,10 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     } else if (tile_y == PF_TILE_STRIPS) {
       tile = tile_x == 128 ? kTileStrips2D : tile_x == 64 ? kTileStrips2D + 1 : -1;
       const int kk = k_steps > 0 ? k_steps : 1;
-      if (tile < 0 || g->stencil != PF_ST_STD || !(g->model_set && fe2d_strips_supported(g->model, kk)))
-        return invalid("the strip kernel (tile 128 or 64 x PF_TILE_STRIPS) needs a model set, "
-                       "the standard stencil and k = 1, 2 or 4 (Models A, Gray-Scott) or k = 1 "
-                       "or 2 (Models B, C)");
+      if (tile < 0 || !(g->model_set && fe2d_strips_supported(g->model, kk, g->stencil)))
+        return invalid("the strip kernel (tile 128 or 64 x PF_TILE_STRIPS) needs a model set "
+                       "and k = 1, 2 or 4 (Models A, Gray-Scott: the 5- or 9-point stencil) or "
+                       "k = 1 or 2 (Models B, C: the 5-point stencil)");
     } else if (tile_x == g->nx && g->ny % cs == 0 && tile_y == g->ny / cs) {
       tile = kTileCluster2D;  // the on-chip cluster kernel: full rows, ny / CS rows per CTA
       const int kk = k_steps > 0 ? k_steps : 1;

@@ -23,6 +23,11 @@
 // The per-site arithmetic is that of the tile body (lap2d_sum with the same operands in the
 // same order, ac_update, ch_mu, ch_update, gs_update, mc_mu, mc_update), so every path gives
 // the same bits.
+//
+// Allen-Cahn and Gray-Scott also run with the isotropic 9-point Laplacian (Sec. 2.2.2): its
+// diagonal neighbours lie in the rows above and below, which the windows hold already, and
+// the ones beyond a lane come by two more shuffles per row. Its radius is still one site, so
+// the halo columns and the level schedule are those of the 5-point stencil.
 #include "pf_internal.h"
 #include "pf_model.cuh"
 
@@ -124,13 +129,31 @@ template <int MODEL, int C>
 constexpr bool kStripPackedLap = (C == 2 || C == 4) && !(MODEL == PF_MODEL_GS && C == 4);
 
 // Laplacians of a lane's C sites from the rows above (u), at (c) and below (d); the x
-// neighbours beyond the lane come from the adjacent lanes.
-template <int MODEL, int C>
+// neighbours beyond the lane come from the adjacent lanes. ST: PF_ST_STD (5-point) or
+// PF_ST_ISO (9-point, lap2d_iso with the tile body's operands in its order: the axial
+// neighbours, then up-left, up-right, down-left, down-right).
+template <int MODEL, int C, int ST>
 __device__ __forceinline__ void lap_lane(const float (&u)[C], const float (&c)[C],
                                          const float (&d)[C], float scale, float (&l)[C]) {
+  static_assert(ST == PF_ST_STD || ST == PF_ST_ISO, "radius-1 stencils only");
   const float xl = __shfl_up_sync(0xffffffffu, c[C - 1], 1);
   const float xr = __shfl_down_sync(0xffffffffu, c[0], 1);
-  if constexpr (kStripPackedLap<MODEL, C> && C == 4) {
+  if constexpr (ST == PF_ST_ISO) {
+    const float ul = __shfl_up_sync(0xffffffffu, u[C - 1], 1);
+    const float ur = __shfl_down_sync(0xffffffffu, u[0], 1);
+    const float dl = __shfl_up_sync(0xffffffffu, d[C - 1], 1);
+    const float dr = __shfl_down_sync(0xffffffffu, d[0], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const float left = j == 0 ? xl : c[j - 1];
+      const float right = j == C - 1 ? xr : c[j + 1];
+      const float up_l = j == 0 ? ul : u[j - 1];
+      const float up_r = j == C - 1 ? ur : u[j + 1];
+      const float dn_l = j == 0 ? dl : d[j - 1];
+      const float dn_r = j == C - 1 ? dr : d[j + 1];
+      l[j] = lap2d_iso(c[j], left, right, u[j], d[j], up_l, up_r, dn_l, dn_r, scale);
+    }
+  } else if constexpr (kStripPackedLap<MODEL, C> && C == 4) {
     float4 r = lap2d_sum4(make_float4(c[0], c[1], c[2], c[3]), xl, xr,
                           make_float4(u[0], u[1], u[2], u[3]),
                           make_float4(d[0], d[1], d[2], d[3]));
@@ -157,8 +180,10 @@ __device__ __forceinline__ void lap_lane(const float (&u)[C], const float (&c)[C
   }
 }
 
-template <int MODEL, int K, int C>
+template <int MODEL, int K, int C, int ST = PF_ST_STD>
 struct StripRun {
+  static_assert(ST == PF_ST_STD || ModelTraits<MODEL>::R == 1,
+                "the 9-point stencil runs on the radius-1 models");
   using S = StripCfg<MODEL, K, C>;
   static constexpr int NF = S::NF;
   static constexpr int R = S::R;
@@ -179,7 +204,7 @@ struct StripRun {
     constexpr int su = P, sc = (P + 1) % 3, sd = (P + 2) % 3;
     if constexpr (MODEL == PF_MODEL_AC) {
       float l[C];
-      lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, l);
+      lap_lane<MODEL, C, ST>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, l);
       if constexpr (kStripPacked<MODEL, C> && C == 4) {
         const float(&p)[C] = w[s - 1][0][sc];
         const float4 r = ac_update4(make_float4(p[0], p[1], p[2], p[3]),
@@ -194,8 +219,8 @@ struct StripRun {
       }
     } else if constexpr (MODEL == PF_MODEL_GS) {
       float lu[C], lv[C];
-      lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, lu);
-      lap_lane<MODEL, C>(w[s - 1][1][su], w[s - 1][1][sc], w[s - 1][1][sd], m.lap_scale, lv);
+      lap_lane<MODEL, C, ST>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, lu);
+      lap_lane<MODEL, C, ST>(w[s - 1][1][su], w[s - 1][1][sc], w[s - 1][1][sd], m.lap_scale, lv);
       if constexpr (kStripPacked<MODEL, C> && C == 2) {
         // the pair twice over in a float4 (gs_update4), the copy discarded
         const float(&u)[C] = w[s - 1][0][sc];
@@ -218,13 +243,13 @@ struct StripRun {
       float(&mu)[3][C] = mw[s - 1][0];
       if constexpr (MODEL == PF_MODEL_CH) {
         float l[C];
-        lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, l);
+        lap_lane<MODEL, C, ST>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale, l);
 #pragma unroll
         for (int j = 0; j < C; ++j) mu[P][j] = ch_mu(w[s - 1][0][sc][j], l[j], m);
       } else {
         float lm[C];
-        lap_lane<MODEL, C>(w[s - 1][1][su], w[s - 1][1][sc], w[s - 1][1][sd], m.lap_scale, lm);
-        lap_lane<MODEL, C>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale,
+        lap_lane<MODEL, C, ST>(w[s - 1][1][su], w[s - 1][1][sc], w[s - 1][1][sd], m.lap_scale, lm);
+        lap_lane<MODEL, C, ST>(w[s - 1][0][su], w[s - 1][0][sc], w[s - 1][0][sd], m.lap_scale,
                            mw[s - 1][1][P]);
 #pragma unroll
         for (int j = 0; j < C; ++j)
@@ -233,7 +258,7 @@ struct StripRun {
       // the row one above: its mu rows sit in slots P + 1, P + 2, P, its state in level
       // s - 1's oldest slot P, and (Model C) its lap psi in slot P + 2
       float lmu[C];
-      lap_lane<MODEL, C>(mu[sc], mu[sd], mu[su], m.lap_scale, lmu);
+      lap_lane<MODEL, C, ST>(mu[sc], mu[sd], mu[su], m.lap_scale, lmu);
       if constexpr (MODEL == PF_MODEL_CH) {
 #pragma unroll
         for (int j = 0; j < C; ++j) o[0][j] = ch_update(w[s - 1][0][su][j], lmu[j], m);
@@ -338,7 +363,7 @@ struct StripRun {
 
 // One warp per task: strips of WO output columns by rows of hy (the last row of tasks is
 // shorter); consecutive warps take neighbouring strips of the same rows.
-template <int MODEL, int K, int C>
+template <int MODEL, int K, int C, int ST>
 __global__ void __launch_bounds__(kStripThreads, (StripCfg<MODEL, K, C>::MINW / kStripWarps))
     fe2d_strip_kernel(FieldPtrs in, FieldOut out, Geom g, ModelParams m, int hy, int tasks_x,
                       int ntasks) {
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(kStripThreads, (StripCfg<MODEL, K, C>::MINW / 
   const int ty = task / tasks_x;
   const int tx = task - ty * tasks_x;
   const int y0 = ty * hy;
-  StripRun<MODEL, K, C> r;
+  StripRun<MODEL, K, C, ST> r;
   r.run(in, out, g.nx, g.ny, g.pitch, tx * S::WO, S::WO, y0, min(hy, g.ny - y0), m);
 }
 
@@ -387,11 +412,11 @@ int strip_rows(int tasks_x, int ny, int resident_warps, int min_rows) {
   return min_rows < ny ? min_rows : ny;
 }
 
-template <int MODEL, int K, int C>
+template <int MODEL, int K, int C, int ST>
 cudaError_t launch_strip(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams& m,
                          cudaStream_t s) {
   using S = StripCfg<MODEL, K, C>;
-  using Run = StripRun<MODEL, K, C>;
+  using Run = StripRun<MODEL, K, C, ST>;
   static int resident[64] = {};  // resident warps of this kernel on the whole device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -399,7 +424,7 @@ cudaError_t launch_strip(const Geom& g, FieldPtrs in, FieldOut out, const ModelP
   if (dev >= 64) return cudaErrorInvalidDevice;
   if (resident[dev] == 0) {
     int b = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fe2d_strip_kernel<MODEL, K, C>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fe2d_strip_kernel<MODEL, K, C, ST>,
                                                       kStripThreads, 0);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -409,27 +434,27 @@ cudaError_t launch_strip(const Geom& g, FieldPtrs in, FieldOut out, const ModelP
   const int hy = strip_rows(tasks_x, g.ny, resident[dev], 4 * Run::T0);
   const int ntasks = tasks_x * ((g.ny + hy - 1) / hy);
   const int blocks = (ntasks + kStripWarps - 1) / kStripWarps;
-  fe2d_strip_kernel<MODEL, K, C><<<blocks, kStripThreads, 0, s>>>(in, out, g, m, hy, tasks_x,
-                                                                  ntasks);
+  fe2d_strip_kernel<MODEL, K, C, ST><<<blocks, kStripThreads, 0, s>>>(in, out, g, m, hy,
+                                                                      tasks_x, ntasks);
   return cudaGetLastError();
 }
 
-template <int MODEL, int C>
+template <int MODEL, int C, int ST>
 cudaError_t launch_strip_k(int k, const Geom& g, FieldPtrs in, FieldOut out,
                            const ModelParams& m, cudaStream_t s) {
-  if (k == 1) return launch_strip<MODEL, 1, C>(g, in, out, m, s);
-  if (k == 2) return launch_strip<MODEL, 2, C>(g, in, out, m, s);
+  if (k == 1) return launch_strip<MODEL, 1, C, ST>(g, in, out, m, s);
+  if (k == 2) return launch_strip<MODEL, 2, C, ST>(g, in, out, m, s);
   if constexpr (ModelTraits<MODEL>::R == 1) {
-    if (k == 4) return launch_strip<MODEL, 4, C>(g, in, out, m, s);
+    if (k == 4) return launch_strip<MODEL, 4, C, ST>(g, in, out, m, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int MODEL>
+template <int MODEL, int ST = PF_ST_STD>
 cudaError_t launch_strip_c(int lanes_cols, int k, const Geom& g, FieldPtrs in, FieldOut out,
                            const ModelParams& m, cudaStream_t s) {
-  if (lanes_cols == 128) return launch_strip_k<MODEL, 4>(k, g, in, out, m, s);
-  if (lanes_cols == 64) return launch_strip_k<MODEL, 2>(k, g, in, out, m, s);
+  if (lanes_cols == 128) return launch_strip_k<MODEL, 4, ST>(k, g, in, out, m, s);
+  if (lanes_cols == 64) return launch_strip_k<MODEL, 2, ST>(k, g, in, out, m, s);
   return cudaErrorInvalidValue;
 }
 
@@ -517,15 +542,23 @@ cudaError_t launch_batch_gs2d_strips(int c, int k, const BatchInst* d_insts,
   return cudaErrorInvalidValue;
 }
 
-bool fe2d_strips_supported(int model, int k) {
+bool fe2d_strips_supported(int model, int k, int stencil) {
+  if (stencil == PF_ST_ISO) return (model == PF_MODEL_AC || model == PF_MODEL_GS) &&
+                                   (k == 1 || k == 2 || k == 4);
+  if (stencil != PF_ST_STD) return false;
   if (model == PF_MODEL_AC || model == PF_MODEL_GS) return k == 1 || k == 2 || k == 4;
   if (model == PF_MODEL_CH || model == PF_MODEL_C) return k == 1 || k == 2;
   return false;
 }
 
-cudaError_t launch_fe2d_strips(int model, int lanes_cols, int k, const Geom& g, FieldPtrs in,
-                               FieldOut out, const ModelParams& m, cudaStream_t s) {
-  if (!fe2d_strips_supported(model, k)) return cudaErrorInvalidValue;
+cudaError_t launch_fe2d_strips(int model, int stencil, int lanes_cols, int k, const Geom& g,
+                               FieldPtrs in, FieldOut out, const ModelParams& m, cudaStream_t s) {
+  if (!fe2d_strips_supported(model, k, stencil)) return cudaErrorInvalidValue;
+  if (stencil == PF_ST_ISO) {
+    if (model == PF_MODEL_AC)
+      return launch_strip_c<PF_MODEL_AC, PF_ST_ISO>(lanes_cols, k, g, in, out, m, s);
+    return launch_strip_c<PF_MODEL_GS, PF_ST_ISO>(lanes_cols, k, g, in, out, m, s);
+  }
   switch (model) {
     case PF_MODEL_AC: return launch_strip_c<PF_MODEL_AC>(lanes_cols, k, g, in, out, m, s);
     case PF_MODEL_GS: return launch_strip_c<PF_MODEL_GS>(lanes_cols, k, g, in, out, m, s);

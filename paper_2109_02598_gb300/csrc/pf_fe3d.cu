@@ -1,12 +1,12 @@
-// 3D forward-Euler step, z-streaming (Sec. 2.4.1 solver, Sec. 2.2.2 7-point stencil,
-// Sec. 3 models).  General kernel for any grid size: a CTA owns a TX x TY column of the
-// xy plane and a chunk of tz planes; it streams through z keeping a ring of three
-// planes (z-1, z, z+1) with a periodic xy halo in shared memory, so every input value is
-// fetched from HBM once per CTA plus the halo.  Model B keeps three phi planes (halo 2)
-// and three mu planes (halo 1); mu is computed on chip and never stored.  Model C keeps
-// both of its fields in the phi planes and the chemical potential of m in the mu planes.
-#include "pf_internal.h"
-#include "pf_tma.cuh"
+// 3D forward-Euler step, z-streaming (Sec. 2.4.1 solver, Sec. 2.2.2 7-, 19- and 27-point
+// stencils, Sec. 3 models).  General kernels for any grid size: a CTA owns a TX x TY column
+// of the xy plane and a chunk of tz planes; it streams through z keeping a ring of planes
+// with a periodic xy halo in shared memory, so every input value is fetched from HBM once
+// per CTA plus the halo.  Allen-Cahn and Gray-Scott: four planes (z-1, z, z+1 and z+2 in
+// flight), four sites per thread.  Model B keeps three phi planes (halo 2) and three mu
+// planes (halo 1); mu is computed on chip and never stored.  Model C keeps both of its
+// fields in the phi planes and the chemical potential of m in the mu planes.
+#include "pf_stage.cuh"
 
 namespace pf {
 
@@ -80,59 +80,170 @@ __device__ __forceinline__ float lap3d_planes(const float* b, const float* c, co
   }
 }
 
-// AC and Gray-Scott (stencil radius 1).
+// AC and Gray-Scott (stencil radius 1): a CTA of 128 threads streams its TX x TY column
+// through a four-plane ring (planes z-1, z, z+1 and z+2 in flight) whose rows carry four
+// halo columns a side, staged by 16-byte copies; each thread takes four consecutive sites
+// of a row per plane, reads its rows as 16-byte words and its x-edges as scalars, and forms
+// every Laplacian from the same operands in the same order as lap3d_planes.
+constexpr int kNT31 = 128;
+
+template <int MODEL, int TX, int TY>
+struct Cfg31 {
+  static constexpr int NF = ModelTraits<MODEL>::NF;
+  static constexpr int WS = TX + 8, HT = TY + 2;  // columns x0-4 .. x0+TX+3, rows y0-1 .. y0+TY
+  static constexpr int PL = WS * HT;              // floats per field and plane
+  static constexpr int SLOT = NF * PL;
+  static_assert((TX / 4) * TY == kNT31, "one group of four sites per thread and plane");
+};
+
+// The values of one row around a thread's four sites: v[0] = x - 1, v[1..4] the sites,
+// v[5] = x + 4. The x-edges come from the neighbouring lanes of the same row by shuffle and
+// from shared memory only at the row's ends (first / last: the thread's group is the first /
+// last of its tile row): scalar loads at a stride of four floats would meet four rows of a
+// warp in the same eight banks. Every lane of the warp calls it.
+__device__ __forceinline__ void row6(const float* r, float (&v)[6], bool first, bool last) {
+  const float4 q = *reinterpret_cast<const float4*>(r);
+  const float sl = __shfl_up_sync(0xffffffffu, q.w, 1);
+  const float sr = __shfl_down_sync(0xffffffffu, q.x, 1);
+  v[0] = first ? r[-1] : sl;
+  v[1] = q.x;
+  v[2] = q.y;
+  v[3] = q.z;
+  v[4] = q.w;
+  v[5] = last ? r[4] : sr;
+}
+__device__ __forceinline__ void row4(const float* r, float (&v)[6]) {
+  const float4 q = *reinterpret_cast<const float4*>(r);
+  v[1] = q.x;
+  v[2] = q.y;
+  v[3] = q.z;
+  v[4] = q.w;
+}
+
+// Laplacians of the four sites of one field at position p (the first site) of the planes b,
+// c, a (rows WS floats apart): lap3d_planes's operands and order, site s at index s + 1.
+template <int ST, int WS>
+__device__ __forceinline__ void lap3d_group(const float* b, const float* c, const float* a,
+                                            int p, bool first, bool last, float scale,
+                                            float (&l)[4], float (&u)[4]) {
+  float c0[6], c1[6], c2[6];  // plane z: rows y - 1, y, y + 1
+  float b1[6], a1[6];         // planes z -+ 1: row y
+  row6(c + p, c1, first, last);
+  if constexpr (ST == PF_ST_STD) {
+    row4(c + p - WS, c0);
+    row4(c + p + WS, c2);
+    row4(b + p, b1);
+    row4(a + p, a1);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      l[s] = lap3d(c1[s + 1], c1[s], c1[s + 2], c0[s + 1], c2[s + 1], b1[s + 1], a1[s + 1], scale);
+  } else {
+    float b0[6], b2[6], a0[6], a2[6];
+    row6(c + p - WS, c0, first, last);
+    row6(c + p + WS, c2, first, last);
+    row6(b + p, b1, first, last);
+    row6(a + p, a1, first, last);
+    if constexpr (ST == PF_ST_ISO) {
+      row4(b + p - WS, b0);
+      row4(b + p + WS, b2);
+      row4(a + p - WS, a0);
+      row4(a + p + WS, a2);
+    } else {
+      row6(b + p - WS, b0, first, last);
+      row6(b + p + WS, b2, first, last);
+      row6(a + p - WS, a0, first, last);
+      row6(a + p + WS, a2, first, last);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int x = s + 1;
+      const float faces = __fadd_rn(__fadd_rn(__fadd_rn(c1[x - 1], c1[x + 1]),
+                                              __fadd_rn(c0[x], c2[x])),
+                                    __fadd_rn(b1[x], a1[x]));
+      const float exy = __fadd_rn(__fadd_rn(c0[x - 1], c0[x + 1]), __fadd_rn(c2[x - 1], c2[x + 1]));
+      const float eb = __fadd_rn(__fadd_rn(b1[x - 1], b1[x + 1]), __fadd_rn(b0[x], b2[x]));
+      const float ea = __fadd_rn(__fadd_rn(a1[x - 1], a1[x + 1]), __fadd_rn(a0[x], a2[x]));
+      const float edges = __fadd_rn(exy, __fadd_rn(eb, ea));
+      if constexpr (ST == PF_ST_ISO) {
+        l[s] = lap3d_iso(c1[x], faces, edges, scale);
+      } else {
+        const float cb = __fadd_rn(__fadd_rn(b0[x - 1], b0[x + 1]), __fadd_rn(b2[x - 1], b2[x + 1]));
+        const float ca = __fadd_rn(__fadd_rn(a0[x - 1], a0[x + 1]), __fadd_rn(a2[x - 1], a2[x + 1]));
+        l[s] = lap3d_iso27(c1[x], faces, edges, __fadd_rn(cb, ca), scale);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) u[s] = c1[s + 1];
+}
+
 template <int MODEL, int TX, int TY, int ST>
-__global__ void __launch_bounds__(kNT3) fe3d_r1_kernel(FieldPtrs in, FieldOut out, Geom g,
-                                                       ModelParams m, int tz) {
-  using C = Cfg3<MODEL, TX, TY>;
-  constexpr int W = C::W;
-  constexpr int PL = C::PL;
+__global__ void __launch_bounds__(kNT31) fe3d_r1_kernel(FieldPtrs in, FieldOut out, Geom g,
+                                                        ModelParams m, int tz) {
+  using C = Cfg31<MODEL, TX, TY>;
+  constexpr int NF = C::NF, WS = C::WS, PL = C::PL, SLOT = C::SLOT;
   extern __shared__ __align__(16) float sm[];
   const int x0 = blockIdx.x * TX;
   const int y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * tz;
   const int z1 = min(z0 + tz, g.nz);
-  canary_fill(sm, C::SMEM_FLOATS);
-  load_plane3d<C>(in, g, x0, y0, z0 - 1, 0, sm);
-  load_plane3d<C>(in, g, x0, y0, z0, 1, sm);
-  int sb = 0, sc = 1, sa = 2;
-  for (int z = z0; z < z1; ++z) {
-    load_plane3d<C>(in, g, x0, y0, z + 1, sa, sm);
-    __syncthreads();
-    const int64_t zoff = (int64_t)z * g.plane;
-    for (int i = threadIdx.x; i < TX * TY; i += kNT3) {
-      const int rr = i / TX;
-      const int r = 1 + rr;
-      const int c = 1 + (i - rr * TX);
-      const int p = r * W + c;
-      const int gx = x0 + c - 1;
-      const int gy = y0 + r - 1;
-      float val[C::NF];
-      if constexpr (MODEL == PF_MODEL_AC) {
-        const float* cp = sm + sc * PL;
-        const float l = lap3d_planes<ST>(sm + sb * PL, cp, sm + sa * PL, p, W, m.lap_scale);
-        val[0] = ac_update(cp[p], l, m);
-      } else {
-        const float* cu = sm + (sc * 2) * PL;
-        const float* cv = cu + PL;
-        const float lu = lap3d_planes<ST>(sm + (sb * 2) * PL, cu, sm + (sa * 2) * PL, p, W,
-                                          m.lap_scale);
-        const float lv = lap3d_planes<ST>(sm + (sb * 2 + 1) * PL, cv, sm + (sa * 2 + 1) * PL, p,
-                                          W, m.lap_scale);
-        gs_update(cu[p], cv[p], lu, lv, m, val[0], val[1]);
-      }
-      if (gx < g.nx && gy < g.ny) {
-        const int64_t off = zoff + (int64_t)gy * g.pitch + gx;
+  canary_fill(sm, (size_t)4 * SLOT);
+  // plane p sits in slot (p - z0 + 1) % 4; planes z0 - 1, z0, z0 + 1 first, one group each
 #pragma unroll
-        for (int f = 0; f < C::NF; ++f) out.f[f][off] = val[f];
+  for (int k = 0; k < 3; ++k) {
+    stage_rows4<NF>(in, g, x0, y0, (int64_t)wrap_index(z0 - 1 + k, g.nz) * g.plane, WS, C::HT,
+                    PL, sm + k * SLOT, kNT31);
+    cp_async_commit();
+  }
+  const int rr = threadIdx.x / (TX / 4), j = threadIdx.x - rr * (TX / 4);
+  const int gy = y0 + rr, gx = x0 + 4 * j;
+  const bool active = gy < g.ny && gx < g.nx;
+  const bool first = j == 0, last = j == TX / 4 - 1;
+  const int p = (rr + 1) * WS + 4 + 4 * j;
+  for (int z = z0; z < z1; ++z) {
+    const int i = z - z0;
+    // plane z + 2 into the slot of plane z - 2 (free since the barrier closing the last
+    // iteration); it is the next iteration's z + 1 plane
+    if (z + 2 <= z1)
+      stage_rows4<NF>(in, g, x0, y0, (int64_t)wrap_index(z + 2, g.nz) * g.plane, WS, C::HT, PL,
+                      sm + ((i + 3) & 3) * SLOT, kNT31);
+    cp_async_commit();         // possibly empty: the group count stays one per iteration
+    cp_async_wait_group<1>();  // all but the newest group: plane z + 1 has landed
+    __syncthreads();
+    {  // every lane computes (the x-edges are shuffled); lanes past the grid store nothing
+      const float* b = sm + (i & 3) * SLOT;        // plane z - 1
+      const float* c = sm + ((i + 1) & 3) * SLOT;  // plane z
+      const float* a = sm + ((i + 2) & 3) * SLOT;  // plane z + 1
+      float res[NF][4];
+      if constexpr (MODEL == PF_MODEL_AC) {
+        float l[4], u[4];
+        lap3d_group<ST, WS>(b, c, a, p, first, last, m.lap_scale, l, u);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) res[0][s] = ac_update(u[s], l[s], m);
+      } else {
+        float lu[4], lv[4], u[4], v[4];
+        lap3d_group<ST, WS>(b, c, a, p, first, last, m.lap_scale, lu, u);
+        lap3d_group<ST, WS>(b + PL, c + PL, a + PL, p, first, last, m.lap_scale, lv, v);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gs_update(u[s], v[s], lu[s], lv[s], m, res[0][s], res[1][s]);
+      }
+      if (active) {
+        const int64_t off = (int64_t)z * g.plane + (int64_t)gy * g.pitch + gx;
+        if (gx + 3 < g.nx) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            *reinterpret_cast<float4*>(out.f[f] + off) =
+                make_float4(res[f][0], res[f][1], res[f][2], res[f][3]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            for (int e = 0; e < 4 && gx + e < g.nx; ++e) out.f[f][off + e] = res[f][e];
+        }
       }
     }
-    __syncthreads();
-    const int t = sb;
-    sb = sc;
-    sc = sa;
-    sa = t;
+    __syncthreads();  // every thread is done with plane z - 1 before its slot is refilled
   }
+  cp_async_wait_all();  // nothing in flight at exit (the last groups are empty)
 }
 
 // Model B and Model C: mu planes computed on chip from the staged phi planes (halo 2).
@@ -249,9 +360,15 @@ cudaError_t launch3(const Geom& g, FieldPtrs in, FieldOut out, const ModelParams
     if (e != cudaSuccess) return e;
     fe3d_r2_kernel<MODEL, TX, TY, ST><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
   } else {
-    cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY, ST>, smem, &attr_mask);
+    using C1 = Cfg31<MODEL, TX, TY>;
+    const size_t smem1 = sizeof(float) * 4 * C1::SLOT;
+    cudaError_t e = ensure_smem_attr(fe3d_r1_kernel<MODEL, TX, TY, ST>, smem1, &attr_mask);
     if (e != cudaSuccess) return e;
-    fe3d_r1_kernel<MODEL, TX, TY, ST><<<grid, kNT3, smem, s>>>(in, out, g, m, tz);
+    static int resident[64] = {};  // per device
+    const int tz1 = one_wave_tz(
+        g.nz, bx * by, resident_ctas(fe3d_r1_kernel<MODEL, TX, TY, ST>, kNT31, smem1, resident));
+    const dim3 grid1(bx, by, (g.nz + tz1 - 1) / tz1);
+    fe3d_r1_kernel<MODEL, TX, TY, ST><<<grid1, kNT31, smem1, s>>>(in, out, g, m, tz1);
   }
   return cudaGetLastError();
 }

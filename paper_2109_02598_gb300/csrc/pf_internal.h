@@ -112,9 +112,10 @@ bool fe2d_bands_supported(int model, const Geom& q);
 // tile ids kTileStrips2D (128 columns per warp, C = 4) and kTileStrips2D + 1 (64, C = 2)
 constexpr int kTileStrips2D = kNumTiles2D + 2;
 constexpr int kNumStrips2D = 2;
-bool fe2d_strips_supported(int model, int k);
-cudaError_t launch_fe2d_strips(int model, int lanes_cols, int k, const Geom& g, FieldPtrs in,
-                               FieldOut out, const ModelParams& m, cudaStream_t s);
+// stencil: PF_ST_STD for every model, PF_ST_ISO (9-point) for Allen-Cahn and Gray-Scott
+bool fe2d_strips_supported(int model, int k, int stencil);
+cudaError_t launch_fe2d_strips(int model, int stencil, int lanes_cols, int k, const Geom& g,
+                               FieldPtrs in, FieldOut out, const ModelParams& m, cudaStream_t s);
 
 // ---- 3D z-streaming forward-Euler kernels (k = 1) -------------------------------
 // Tile ids: 0 = 32x16, 1 = 64x8 (general kernel, any size, all models);

@@ -101,6 +101,27 @@ def run_cases(pf):
     for model in ("ch", "c"):  # the box kernel, both depths, boxes past every edge
         for k in (1, 2):
             res[f"3d_box_{model}_k{k}"] = run_grid(pf, model, (11, 13, 36), 5, (32, 8, k))
+    # N coupled species (3 and 4 fields): the 2D tile and the 3D plane ring, ragged shapes,
+    # z-chunks of one plane and of several
+    rd3 = pf.rd_coeffs((0.2, 0.05, 0.12),
+                       [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 2, 0], [2, 0, 1], [0, 0, 3]],
+                       [[0.03, -0.03, 0.0, 0.1, -1.0, 0.0, 0.0],
+                        [0.0, 0.0, -0.09, 0.0, 1.0, -0.4, 0.0],
+                        [0.0, 0.05, 0.0, -0.2, 0.0, 0.4, -0.3]])
+    rd4 = pf.rd_coeffs((0.1, 0.15, 0.05, 0.02),
+                       [[1, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1], [1, 0, 0, 0], [0, 0, 0, 0]],
+                       [[-1.2, 0.5, 0.3, -0.05, 0.0], [-1.2, 0.5, 0.0, 0.0, 0.05],
+                        [1.2, -0.7, 0.0, 0.0, 0.0], [0.0, 0.2, -0.3, 0.0, 0.0]])
+    for nf, c in ((3, rd3), (4, rd4)):
+        for shape in ((33, 70), (10, 20, 36), (3, 17, 33), (40, 16, 64)):
+            n = int(np.prod(shape))
+            x0 = tuple(synthetic.uniform(90 + nf, 60 + i, n, 0.05, 0.9).reshape(shape)
+                       .astype(np.float32) for i in range(nf))
+            g = pf.Grid(shape, nf).set_model("rd", c, 0.2)
+            g.write_fields(x0)
+            g.step(7)
+            res[f"rd{nf}_{'x'.join(map(str, shape))}"] = list(g.read_fields())
+            g.close()
     # the batch
     shapes = [(64, 64), (97, 130), (5, 7), (33, 300)]
     specs = [dict(ny=s[0], nx=s[1], Du=0.2, Dv=0.1, F=0.03 + 0.005 * i, k=0.05 + 0.003 * i)

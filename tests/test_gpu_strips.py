@@ -1,6 +1,7 @@
 """The 2D strip kernel (tile 128 or 64 x PF_TILE_STRIPS): one warp per strip of columns, the
 k steps pipelined in registers. It must give the tiled kernels' bits for every model, width,
-depth and grid shape (ragged widths, grids narrower than a strip, fewer rows than a task, a
+depth and grid shape, with the 5-point stencil and (Models A and Gray-Scott) the isotropic
+9-point one (ragged widths, grids narrower than a strip, fewer rows than a task, a
 single row or column), and meet the oracle bars: one step rel L-inf <= 1e-6, 1000 steps rel
 L2 <= 1e-3."""
 import numpy as np
@@ -115,7 +116,70 @@ def test_strips_spacing_and_rules(pf):
         g.set_tuning(96, pf.PF_TILE_STRIPS, 1)  # widths 128 and 64 only
     with pytest.raises(pf.PfError, match="strip kernel"):
         g.set_tuning(128, pf.PF_TILE_STRIPS, 8)
-    g.set_stencil("iso")
+    g.set_stencil("4th")  # radius 2: the three-row windows do not hold it
     with pytest.raises(pf.PfError, match="strip kernel"):
         g.set_tuning(128, pf.PF_TILE_STRIPS, 1)
+    g.set_stencil("iso")
+    g.set_tuning(128, pf.PF_TILE_STRIPS, 4)
+    assert g.tuning == (128, pf.PF_TILE_STRIPS, 4)
+    g.set_stencil("4th")  # the strip tuning no longer applies: back to the default tile
+    assert g.tuning[1] != pf.PF_TILE_STRIPS
     g.close()
+    g = pf.Grid((64, 64), 1).set_model("ch", (1.0, 1.0, 1.0), 0.01).set_stencil("iso")
+    with pytest.raises(pf.PfError, match="strip kernel"):
+        g.set_tuning(128, pf.PF_TILE_STRIPS, 1)  # Model B: the 5-point stencil only
+    g.close()
+
+
+# ---------------------------------------------------------------- isotropic 9-point stencil
+
+def run_iso(pf, model, x0, n, tuning, dt, h=0.9):
+    g = pf.Grid(x0[0].shape, len(x0), h).set_stencil("iso")
+    g.set_model(model, COEFFS[model], dt)
+    g.set_tuning(*tuning)
+    assert g.tuning == tuning
+    g.write_fields(x0)
+    g.step(n)
+    out = g.read_fields()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("model", ["ac", "gs"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_iso_strips_are_bitwise_the_tiled_kernel(pf, model, shape):
+    # the tiled kernels take the 9-point stencil at k = 1 and 2; the strips at k = 1, 2, 4
+    # give their bits at the same step count
+    x0 = fields_for(model, shape, seed=7)
+    dt = DT[model] * 0.5
+    ref = run_iso(pf, model, x0, 12, (64, 16, 1), dt)
+    for k in (1, 2, 4):
+        for width in (128, 64):
+            got = run_iso(pf, model, x0, 12, (width, pf.PF_TILE_STRIPS, k), dt)
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), (model, shape, k, width)
+
+
+@pytest.mark.parametrize("model", ["ac", "gs"])
+def test_iso_strips_vs_oracle(pf, model):
+    shape = (96, 260)
+    x0 = fields_for(model, shape, seed=8)
+    dt, h = DT[model] * 0.5, 0.9
+    one = run_iso(pf, model, x0, 1, (64, pf.PF_TILE_STRIPS, 1), dt, h)
+    ref1 = oracle.euler_step(model, x0, COEFFS[model], dt, h, stencil="9iso")
+    assert max(np.abs(a.astype(np.float64) - b).max() / np.abs(b).max()
+               for a, b in zip(one, ref1)) <= 1e-6
+    got = run_iso(pf, model, x0, 1000, (64, pf.PF_TILE_STRIPS, 4), dt, h)
+    ref = oracle.run(model, x0, COEFFS[model], dt, 1000, h, stencil="9iso")
+    num = np.sqrt(sum(((a.astype(np.float64) - b) ** 2).sum() for a, b in zip(got, ref)))
+    assert num / np.sqrt(sum((b ** 2).sum() for b in ref)) <= 1e-3
+
+
+def test_iso_strips_full_size_bitwise_tiled(pf):
+    # Gray-Scott 4096^2 with the 9-point stencil, 8 steps: every site, both widths, k = 4
+    x0 = fields_for("gs", (4096, 4096), seed=9)
+    ref = run_iso(pf, "gs", x0, 8, (128, 32, 2), DT["gs"], 1.0)
+    for width in (128, 64):
+        got = run_iso(pf, "gs", x0, 8, (width, pf.PF_TILE_STRIPS, 4), DT["gs"], 1.0)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), width
