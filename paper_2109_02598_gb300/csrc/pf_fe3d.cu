@@ -81,10 +81,17 @@ __device__ __forceinline__ float lap3d_planes(const float* b, const float* c, co
 }
 
 // AC and Gray-Scott (stencil radius 1): a CTA of 128 threads streams its TX x TY column
-// through a four-plane ring (planes z-1, z, z+1 and z+2 in flight) whose rows carry four
-// halo columns a side, staged by 16-byte copies; each thread takes four consecutive sites
-// of a row per plane, reads its rows as 16-byte words and its x-edges as scalars, and forms
-// every Laplacian from the same operands in the same order as lap3d_planes.
+// through a four-plane ring in shared memory (rows with four halo columns a side, staged by
+// 16-byte copies two planes ahead), and each thread takes four consecutive sites of a row.
+// When a plane enters, each thread reads its three rows once and forms, per site and field,
+// the plane's sums in the order every stencil uses them: F = the site, E = (x-1 + x+1) +
+// (y-1 + y+1) and, for the 19- and 27-point stencils, C = (the four in-plane diagonals).
+// The sums of planes z-1, z and z+1 stay in registers, in slots named by plane mod 3 (the
+// plane loop unrolled by three, so no register moves), and the Laplacian of plane z is
+//   7-point:  E(z) + (F(z-1) + F(z+1)), less 6 c;
+//   19-point: faces = E(z) + (F(z-1) + F(z+1)), edges = C(z) + (E(z-1) + E(z+1));
+//   27-point: and corners = C(z-1) + C(z+1);
+// the operands and order of lap3d_planes, so the bits of every other 3D path.
 constexpr int kNT31 = 128;
 
 template <int MODEL, int TX, int TY>
@@ -120,130 +127,149 @@ __device__ __forceinline__ void row4(const float* r, float (&v)[6]) {
   v[4] = q.w;
 }
 
-// Laplacians of the four sites of one field at position p (the first site) of the planes b,
-// c, a (rows WS floats apart): lap3d_planes's operands and order, site s at index s + 1.
-template <int ST, int WS>
-__device__ __forceinline__ void lap3d_group(const float* b, const float* c, const float* a,
-                                            int p, bool first, bool last, float scale,
-                                            float (&l)[4], float (&u)[4]) {
-  float c0[6], c1[6], c2[6];  // plane z: rows y - 1, y, y + 1
-  float b1[6], a1[6];         // planes z -+ 1: row y
-  row6(c + p, c1, first, last);
-  if constexpr (ST == PF_ST_STD) {
-    row4(c + p - WS, c0);
-    row4(c + p + WS, c2);
-    row4(b + p, b1);
-    row4(a + p, a1);
+template <int MODEL, int TX, int TY, int ST>
+struct R1Run {
+  using Cf = Cfg31<MODEL, TX, TY>;
+  static constexpr int NF = Cf::NF, WS = Cf::WS, PL = Cf::PL, SLOT = Cf::SLOT;
+  static constexpr bool kDiag = ST != PF_ST_STD;  // the 19- and 27-point stencils need C
+  float F[3][NF][4], E[3][NF][4], C[3][NF][kDiag ? 4 : 1];
+
+  const float* sm;
+  FieldOut out;
+  Geom g;
+  int x0, y0, z0, z1, gy, gx, p;
+  bool first, last, active;
+
+  // The sums of the plane in ring slot rs into window slot W.
+  template <int W>
+  __device__ __forceinline__ void enter(int rs) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      l[s] = lap3d(c1[s + 1], c1[s], c1[s + 2], c0[s + 1], c2[s + 1], b1[s + 1], a1[s + 1], scale);
-  } else {
-    float b0[6], b2[6], a0[6], a2[6];
-    row6(c + p - WS, c0, first, last);
-    row6(c + p + WS, c2, first, last);
-    row6(b + p, b1, first, last);
-    row6(a + p, a1, first, last);
-    if constexpr (ST == PF_ST_ISO) {
-      row4(b + p - WS, b0);
-      row4(b + p + WS, b2);
-      row4(a + p - WS, a0);
-      row4(a + p + WS, a2);
-    } else {
-      row6(b + p - WS, b0, first, last);
-      row6(b + p + WS, b2, first, last);
-      row6(a + p - WS, a0, first, last);
-      row6(a + p + WS, a2, first, last);
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int x = s + 1;
-      const float faces = __fadd_rn(__fadd_rn(__fadd_rn(c1[x - 1], c1[x + 1]),
-                                              __fadd_rn(c0[x], c2[x])),
-                                    __fadd_rn(b1[x], a1[x]));
-      const float exy = __fadd_rn(__fadd_rn(c0[x - 1], c0[x + 1]), __fadd_rn(c2[x - 1], c2[x + 1]));
-      const float eb = __fadd_rn(__fadd_rn(b1[x - 1], b1[x + 1]), __fadd_rn(b0[x], b2[x]));
-      const float ea = __fadd_rn(__fadd_rn(a1[x - 1], a1[x + 1]), __fadd_rn(a0[x], a2[x]));
-      const float edges = __fadd_rn(exy, __fadd_rn(eb, ea));
-      if constexpr (ST == PF_ST_ISO) {
-        l[s] = lap3d_iso(c1[x], faces, edges, scale);
+    for (int f = 0; f < NF; ++f) {
+      const float* q = sm + rs * SLOT + f * PL + p;
+      float r0[6], r1[6], r2[6];  // rows y - 1, y, y + 1
+      row6(q, r1, first, last);
+      if constexpr (kDiag) {
+        row6(q - WS, r0, first, last);
+        row6(q + WS, r2, first, last);
       } else {
-        const float cb = __fadd_rn(__fadd_rn(b0[x - 1], b0[x + 1]), __fadd_rn(b2[x - 1], b2[x + 1]));
-        const float ca = __fadd_rn(__fadd_rn(a0[x - 1], a0[x + 1]), __fadd_rn(a2[x - 1], a2[x + 1]));
-        l[s] = lap3d_iso27(c1[x], faces, edges, __fadd_rn(cb, ca), scale);
+        row4(q - WS, r0);
+        row4(q + WS, r2);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int x = s + 1;
+        F[W][f][s] = r1[x];
+        E[W][f][s] = __fadd_rn(__fadd_rn(r1[x - 1], r1[x + 1]), __fadd_rn(r0[x], r2[x]));
+        if constexpr (kDiag)
+          C[W][f][s] = __fadd_rn(__fadd_rn(r0[x - 1], r0[x + 1]), __fadd_rn(r2[x - 1], r2[x + 1]));
       }
     }
   }
+
+  // Laplacian of site s of field f on plane z from window slots Bs (z-1), Cs (z), As (z+1).
+  template <int Bs, int Cs, int As>
+  __device__ __forceinline__ float lap(int f, int s, float scale) const {
+    const float c = F[Cs][f][s];
+    const float faces = __fadd_rn(E[Cs][f][s], __fadd_rn(F[Bs][f][s], F[As][f][s]));
+    if constexpr (ST == PF_ST_STD) {
+      return __fmul_rn(__fmaf_rn(-6.0f, c, faces), scale);  // lap3d
+    } else {
+      const float edges = __fadd_rn(C[Cs][f][s], __fadd_rn(E[Bs][f][s], E[As][f][s]));
+      if constexpr (ST == PF_ST_ISO)
+        return lap3d_iso(c, faces, edges, scale);
+      else
+        return lap3d_iso27(c, faces, edges, __fadd_rn(C[Bs][f][s], C[As][f][s]), scale);
+    }
+  }
+
+  // Plane z at phase P (window slot of plane z-1): wait for plane z+1, stage plane z+3, take
+  // plane z+1's sums, update plane z.
+  template <int P>
+  __device__ __forceinline__ void iteration(int z, const FieldPtrs& in, const ModelParams& m) {
+    constexpr int Bs = P, Cs = (P + 1) % 3, As = (P + 2) % 3;
+    const int i = z - z0;
+    cp_async_wait_group<1>();  // plane z + 1 has landed (plane z + 2 may be in flight)
+    __syncthreads();           // ... for every thread; and every read of plane z - 1's ring
+                               // slot (in the iteration before the last) is done
+    if (z + 3 <= z1)
+      stage_rows4<NF>(in, g, x0, y0, (int64_t)wrap_index(z + 3, g.nz) * g.plane, WS, Cf::HT, PL,
+                      const_cast<float*>(sm) + (i & 3) * SLOT, kNT31);
+    cp_async_commit();  // possibly empty: one group per iteration
+    enter<As>((i + 2) & 3);
+    float res[NF][4];
+    if constexpr (MODEL == PF_MODEL_AC) {
 #pragma unroll
-  for (int s = 0; s < 4; ++s) u[s] = c1[s + 1];
-}
+      for (int s = 0; s < 4; ++s)
+        res[0][s] = ac_update(F[Cs][0][s], lap<Bs, Cs, As>(0, s, m.lap_scale), m);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        gs_update(F[Cs][0][s], F[Cs][1][s], lap<Bs, Cs, As>(0, s, m.lap_scale),
+                  lap<Bs, Cs, As>(1, s, m.lap_scale), m, res[0][s], res[1][s]);
+    }
+    if (active) {
+      const int64_t off = (int64_t)z * g.plane + (int64_t)gy * g.pitch + gx;
+      if (gx + 3 < g.nx) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          *reinterpret_cast<float4*>(out.f[f] + off) =
+              make_float4(res[f][0], res[f][1], res[f][2], res[f][3]);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (gx + e < g.nx) out.f[f][off + e] = res[f][e];
+      }
+    }
+  }
+};
 
 template <int MODEL, int TX, int TY, int ST>
 __global__ void __launch_bounds__(kNT31) fe3d_r1_kernel(FieldPtrs in, FieldOut out, Geom g,
                                                         ModelParams m, int tz) {
-  using C = Cfg31<MODEL, TX, TY>;
-  constexpr int NF = C::NF, WS = C::WS, PL = C::PL, SLOT = C::SLOT;
-  extern __shared__ __align__(16) float sm[];
-  const int x0 = blockIdx.x * TX;
-  const int y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * tz;
-  const int z1 = min(z0 + tz, g.nz);
-  canary_fill(sm, (size_t)4 * SLOT);
-  // plane p sits in slot (p - z0 + 1) % 4; planes z0 - 1, z0, z0 + 1 first, one group each
+  using Run = R1Run<MODEL, TX, TY, ST>;
+  using Cf = typename Run::Cf;
+  constexpr int NF = Cf::NF, WS = Cf::WS, PL = Cf::PL, SLOT = Cf::SLOT;
+  extern __shared__ __align__(16) float smem[];
+  Run r;
+  r.sm = smem;
+  r.out = out;
+  r.g = g;
+  r.x0 = blockIdx.x * TX;
+  r.y0 = blockIdx.y * TY;
+  r.z0 = blockIdx.z * tz;
+  r.z1 = min(r.z0 + tz, g.nz);
+  const int rr = threadIdx.x / (TX / 4), j = threadIdx.x - rr * (TX / 4);
+  r.gy = r.y0 + rr;
+  r.gx = r.x0 + 4 * j;
+  r.active = r.gy < g.ny && r.gx < g.nx;  // lanes past the grid compute but store nothing
+  r.first = j == 0;
+  r.last = j == TX / 4 - 1;
+  r.p = (rr + 1) * WS + 4 + 4 * j;
+  canary_fill(smem, (size_t)4 * SLOT);
+  // plane q sits in ring slot (q - z0 + 1) % 4: planes z0 - 1 .. z0 + 2 first, one group each
+  // (z0 + 2 is needed only when the chunk has a second plane)
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    stage_rows4<NF>(in, g, x0, y0, (int64_t)wrap_index(z0 - 1 + k, g.nz) * g.plane, WS, C::HT,
-                    PL, sm + k * SLOT, kNT31);
+  for (int k = 0; k < 4; ++k) {
+    if (k < 3 || r.z0 + 1 < r.z1)
+      stage_rows4<NF>(in, g, r.x0, r.y0, (int64_t)wrap_index(r.z0 - 1 + k, g.nz) * g.plane, WS,
+                      Cf::HT, PL, smem + k * SLOT, kNT31);
     cp_async_commit();
   }
-  const int rr = threadIdx.x / (TX / 4), j = threadIdx.x - rr * (TX / 4);
-  const int gy = y0 + rr, gx = x0 + 4 * j;
-  const bool active = gy < g.ny && gx < g.nx;
-  const bool first = j == 0, last = j == TX / 4 - 1;
-  const int p = (rr + 1) * WS + 4 + 4 * j;
-  for (int z = z0; z < z1; ++z) {
-    const int i = z - z0;
-    // plane z + 2 into the slot of plane z - 2 (free since the barrier closing the last
-    // iteration); it is the next iteration's z + 1 plane
-    if (z + 2 <= z1)
-      stage_rows4<NF>(in, g, x0, y0, (int64_t)wrap_index(z + 2, g.nz) * g.plane, WS, C::HT, PL,
-                      sm + ((i + 3) & 3) * SLOT, kNT31);
-    cp_async_commit();         // possibly empty: the group count stays one per iteration
-    cp_async_wait_group<1>();  // all but the newest group: plane z + 1 has landed
-    __syncthreads();
-    {  // every lane computes (the x-edges are shuffled); lanes past the grid store nothing
-      const float* b = sm + (i & 3) * SLOT;        // plane z - 1
-      const float* c = sm + ((i + 1) & 3) * SLOT;  // plane z
-      const float* a = sm + ((i + 2) & 3) * SLOT;  // plane z + 1
-      float res[NF][4];
-      if constexpr (MODEL == PF_MODEL_AC) {
-        float l[4], u[4];
-        lap3d_group<ST, WS>(b, c, a, p, first, last, m.lap_scale, l, u);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) res[0][s] = ac_update(u[s], l[s], m);
-      } else {
-        float lu[4], lv[4], u[4], v[4];
-        lap3d_group<ST, WS>(b, c, a, p, first, last, m.lap_scale, lu, u);
-        lap3d_group<ST, WS>(b + PL, c + PL, a + PL, p, first, last, m.lap_scale, lv, v);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) gs_update(u[s], v[s], lu[s], lv[s], m, res[0][s], res[1][s]);
-      }
-      if (active) {
-        const int64_t off = (int64_t)z * g.plane + (int64_t)gy * g.pitch + gx;
-        if (gx + 3 < g.nx) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f)
-            *reinterpret_cast<float4*>(out.f[f] + off) =
-                make_float4(res[f][0], res[f][1], res[f][2], res[f][3]);
-        } else {
-#pragma unroll
-          for (int f = 0; f < NF; ++f)
-            for (int e = 0; e < 4 && gx + e < g.nx; ++e) out.f[f][off + e] = res[f][e];
-        }
-      }
-    }
-    __syncthreads();  // every thread is done with plane z - 1 before its slot is refilled
+  cp_async_wait_group<2>();  // planes z0 - 1 and z0
+  __syncthreads();
+  r.template enter<0>(0);  // window slot of plane q: (q - z0 + 1) % 3
+  r.template enter<1>(1);
+  int z = r.z0;
+  for (; z + 3 <= r.z1; z += 3) {
+    r.template iteration<0>(z, in, m);
+    r.template iteration<1>(z + 1, in, m);
+    r.template iteration<2>(z + 2, in, m);
   }
-  cp_async_wait_all();  // nothing in flight at exit (the last groups are empty)
+  if (z < r.z1) r.template iteration<0>(z, in, m);
+  if (z + 1 < r.z1) r.template iteration<1>(z + 1, in, m);
+  cp_async_wait_all();  // nothing in flight at exit
 }
 
 // Model B and Model C: mu planes computed on chip from the staged phi planes (halo 2).

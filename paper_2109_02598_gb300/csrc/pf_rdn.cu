@@ -69,7 +69,9 @@ __device__ __forceinline__ void rd_store4(const FieldOut& out, int64_t off, int 
   } else {
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-      for (int e = 0; e < 4 && gx + e < nx; ++e) out.f[f][off + e] = res[f][e];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (gx + e < nx) out.f[f][off + e] = res[f][e];
   }
 }
 
