@@ -34,6 +34,12 @@ UNIT = "GLUPS"
 WORKLOAD = "gs3d_256"
 BYTES_PER_LUP = {"gs": 16.0, "ac": 8.0, "ch": 8.0}  # k = 1: read + write every field once
 TMA_TILES = {(64, 16), (128, 8), (128, 16)}
+# Three coupled species (D, exponents E, rates K): a constant source, linear, quadratic,
+# cubic and mixed monomials
+RD3 = ((0.2, 0.05, 0.12),
+       [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 2, 0], [2, 0, 1], [0, 0, 3]],
+       [[0.03, -0.03, 0.0, 0.1, -1.0, 0.0, 0.0], [0.0, 0.0, -0.09, 0.0, 1.0, -0.4, 0.0],
+        [0.0, 0.05, 0.0, -0.2, 0.0, 0.4, -0.3]])
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel as it is now
 # (profiles/fe3d_tb2_gs3d_256.md, profiles/fe3d_tma_gs3d_256.md); reported only for that
 # kernel and tile.
@@ -671,10 +677,7 @@ def widened_rows(stream, hbm):
         out["stencils_gs"] = rows
         # ---- three coupled species: a constant source, linear, quadratic, cubic and mixed
         # monomials; 24 B per update at k = 1
-        D = (0.2, 0.05, 0.12)
-        E = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 2, 0], [2, 0, 1], [0, 0, 3]]
-        K = [[0.03, -0.03, 0.0, 0.1, -1.0, 0.0, 0.0], [0.0, 0.0, -0.09, 0.0, 1.0, -0.4, 0.0],
-             [0.0, 0.05, 0.0, -0.2, 0.0, 0.4, -0.3]]
+        D, E, K = RD3
         rows = []
         for shape, steps in (((4096, 4096), 100), ((256, 256, 256), 20)):
             n = int(np.prod(shape))
@@ -873,16 +876,28 @@ def run_euler_case(spec: str):
     import paper_2109_02598_gb300 as pf
     parts = spec.split(":")
     model, shape, steps = parts[0], tuple(int(v) for v in parts[1].split("x"))[::-1], int(parts[2])
-    coeffs = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06),
-              "c": (1.0,) * 5}[model]
-    dt = {"ac": 0.05, "ch": 0.01, "gs": 0.5, "c": 0.005}[model]
-    if model == "gs":
-        x0 = synthetic.gray_scott_init(shape, seed=3, n_seeds=8, side=8)
+    stencil = parts[6] if len(parts) >= 7 else "std"
+    if model == "rd3":  # the three coupled species of the widened-rows companion
+        model, dt = "rd", 0.2
+        coeffs = pf.rd_coeffs(*RD3)
+        n = int(np.prod(shape))
+        x0 = tuple(synthetic.uniform(12, 60 + i, n, 0.05, 0.9).reshape(shape).astype(np.float32)
+                   for i in range(3))
     else:
-        x0 = tuple(0.5 * x for x in synthetic.paper_timing_init("c" if model == "c" else "ac", shape))
+        coeffs = {"ac": (1.0, 1.0), "ch": (1.0, 1.0, 1.0), "gs": (0.2, 0.1, 0.04, 0.06),
+                  "c": (1.0,) * 5}[model]
+        dt = {"ac": 0.05, "ch": 0.01, "gs": 0.5, "c": 0.005}[model]
+        if model == "gs":
+            x0 = synthetic.gray_scott_init(shape, seed=3, n_seeds=8, side=8)
+        else:
+            x0 = tuple(0.5 * x for x in
+                       synthetic.paper_timing_init("c" if model == "c" else "ac", shape))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g = pf.Grid(shape, len(x0), stream=stream).set_model(model, coeffs, dt).write_fields(x0)
+        g = pf.Grid(shape, len(x0), stream=stream)
+        if stencil != "std":
+            g.set_stencil(stencil)
+        g.set_model(model, coeffs, dt).write_fields(x0)
         if len(parts) >= 6:
             g.set_tuning(int(parts[3]), int(parts[4]), int(parts[5]))
         else:
@@ -921,7 +936,7 @@ def main():
     ap.add_argument("--spectral", metavar="MODEL:NXxNY[xNZ]:STEPS[:ENGINE]",
                     help="time one spectral-solver case alone (e.g. c:512x512:200:cufft) "
                          "and print its JSON line instead of the bench line")
-    ap.add_argument("--euler", metavar="MODEL:NXxNY[xNZ]:STEPS[:TX:TY:K]",
+    ap.add_argument("--euler", metavar="MODEL:NXxNY[xNZ]:STEPS[:TX:TY:K[:STENCIL]]",
                     help="time one forward-Euler case alone (autotuned unless a tuning is "
                          "given; e.g. ac:128x128:1000) and print its JSON line")
     ap.add_argument("--adjoint", metavar="N:STEPS",
