@@ -171,8 +171,9 @@ int pf_reduce(pf_grid_t g, int what, int field, double* out);
 /* Choose the Laplacian stencil of the step (PF_STENCIL_*; Sec. 2.2.2 lists these among the
  * stencil families). Model B and Model C apply it twice. The tuning returns to the default
  * for the stencil. The isotropic and fourth-order stencils run with 2D tiles 64x16 or
- * 128x32 (k <= 2) and with the general 3D kernel (k = 1); the batch and the adjoint use the
- * standard stencil. Errors: PF_ERR_INVALID_ARG (unknown stencil; fourth order in 3D;
+ * 128x32 (k <= 2) and with the general 3D kernel (k = 1); the isotropic 9-point stencil also
+ * runs on the 2D strip kernel for Allen-Cahn and Gray-Scott (k = 1, 2 or 4); the batch and
+ * the adjoint use the standard stencil. Errors: PF_ERR_INVALID_ARG (unknown stencil; fourth order in 3D;
  * 27-point in 2D),
  * PF_ERR_UNSTABLE_DT (the current dt exceeds the bound for the new stencil; nothing changed). */
 int pf_set_stencil(pf_grid_t g, int stencil);

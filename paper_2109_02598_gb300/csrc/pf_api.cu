@@ -741,8 +741,8 @@ int pf_set_tuning(pf_grid_t g, int tile_x, int tile_y, int k_steps) {
     const bool ok = g->dim == 2 ? fe2d_stencil_supported(g->stencil, t, kk)
                                 : ((t == 0 || t == 1) && kk == 1);
     if (!ok)
-      return invalid("this stencil runs with 2D tiles 64x16 or 128x32 and k <= 2, or 3D tiles "
-                     "32x16 or 64x8 and k = 1");
+      return invalid("this stencil runs with 2D tiles 64x16 or 128x32 and k <= 2 (the 9-point "
+                     "one also on the strip kernel), or 3D tiles 32x16 or 64x8 and k = 1");
   }
   if (g->dim == 3 && tile == kTileBox3D) {
     if (!(g->model_set && fe3d_box_supported(g->model, k_steps > 0 ? k_steps : 1, grid_geom(g))))
